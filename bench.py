@@ -1,0 +1,302 @@
+"""Benchmark: samples/s at fixed fidelity on the 4x7-grid / 14-cycle workload.
+
+One step = one pass of the sampling hot path over one group of T = 256 batches of
+2^6 amplitudes: Philox batch draws, batch selectors, every pairwise contraction of the
+sliced network over the slice set (2^10 slices at fidelity 1), the FP64 slice sum,
+p = |a|^2 / F and the warp rejection sampler.  Every step recomputes every tensor
+(nothing is carried between steps).  Inputs/intermediates exceed L2 (the dominant
+operands are GiB-sized) and L2 is also flushed between timed steps.
+
+    python bench.py [--gpus N --steps K --warmup W] [--impl reference]
+
+Prints one JSON line (rank 0).  Under torchrun each rank runs independent batch
+groups (replicas, weak scaling); the timing is the max over ranks.
+"""
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+WORKLOAD = dict(rows=4, cols=7, cycles=14, seed=0, n_sliced=10, n_open=6, log2_batches=8)
+METRIC = "samples/s at fixed fidelity"
+FFMA_PEAK_NOTE = "152 SMs x 128 FP32 lanes x 2 FLOP x 2070 MHz"
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--fidelity", type=float, default=1.0)
+    ap.add_argument("--trials", type=int, default=256)
+    ap.add_argument("--seed", type=int, default=2024)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    return ap.parse_args()
+
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+def peaks():
+    try:
+        return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except Exception:
+        return {}
+
+
+class Clocks:
+    """nvidia-smi sampling of SM clocks and throttle reasons during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device_index):
+        self.dev = device_index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        try:
+            fd, self.path = tempfile.mkstemp(suffix=".csv")
+            os.close(fd)
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.dev), "--query-gpu=" + self.FIELDS, "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        out = {"sm_mhz": None, "sm_max_mhz": None, "reasons": []}
+        if not self.proc:
+            return out
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            parts = [x.strip() for x in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+            except ValueError:
+                continue
+            for nm, val in zip(names, parts[5:9]):
+                if val.lower().startswith("active"):
+                    reasons.add(nm)
+        os.unlink(self.path)
+        if sm:
+            out = {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(smax), "reasons": sorted(reasons),
+                   "samples": len(sm)}
+        return out
+
+
+# ---------------------------------------------------------------- oracle baseline
+
+def oracle_step(circ, openq, T, seed, t0, alpha=2.0):
+    """The oracle on one step of the workload: the FP64 state vector (the whole circuit),
+    then the Sec. II.A step on T batches with the same Philox draws.  Returns accepted."""
+    import numpy as np
+    import oracle
+    psi = oracle.simulate(circ)
+    p = np.abs(psi) ** 2
+    del psi
+    b_bits = circ.n_qubits - len(openq)
+    js = oracle.batch_draws(seed, T, b_bits, t0=t0)
+    pb = np.ascontiguousarray(oracle.batch_amplitudes(p, circ.n_qubits, openq, js))
+    acc, _pick = oracle.sample_batches(pb, b_bits, alpha, seed, t0=t0)
+    return int(acc.sum())
+
+
+def cpu_cores():
+    try:
+        return len(os.sched_getaffinity(0))
+    except Exception:
+        return os.cpu_count() or 1
+
+
+def run_reference(args):
+    rank, world, _ = dist_env()
+    if rank != 0:
+        return
+    from paper_2112_15083_gb300 import circuits as cg
+    import oracle
+    oracle.lib()
+    w = WORKLOAD
+    circ = cg.sycamore_grid(w["rows"], w["cols"], w["cycles"], seed=w["seed"])
+    openq = cg.default_open_qubits(w["rows"], w["cols"], w["n_open"])
+    T = 1 << w["log2_batches"]
+    for i in range(args.warmup):
+        oracle_step(circ, openq, T, args.seed, i * T)
+    t = time.perf_counter()
+    acc = 0
+    for k in range(args.steps):
+        acc += oracle_step(circ, openq, T, args.seed, (args.warmup + k) * T)
+    dt = time.perf_counter() - t
+    val = acc / dt
+    cores = cpu_cores()
+    line = {
+        "impl": "reference", "metric": METRIC, "value": val, "unit": "samples/s", "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * dt / max(1, args.steps),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": workload_config(args),
+        "cpu_baseline": {"value": val, "unit": "samples/s", "cores": cores, "kind": "oracle",
+                         "sample": "per step: FP64 state vector of the 28-qubit circuit + the sampler on %d batches" % T},
+        "e2e": {"value": val, "unit": "samples/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+def workload_config(args):
+    w = WORKLOAD
+    return {"workload": "grid4x7_m14: 28-qubit 4x7 Sycamore-style ABCD circuit, 14 cycles, fSim(pi/2,pi/6); "
+                        "10 sliced legs (1024 slices); 256 batches of 64 bitstrings per step",
+            "qubits": 28, "cycles": w["cycles"], "sliced_legs": w["n_sliced"], "batches_per_step": 1 << w["log2_batches"],
+            "batch_size": 64, "fidelity_target": args.fidelity, "alpha": 2.0, "order_trials": args.trials,
+            "l2": "flushed between timed steps; dominant operands exceed L2"}
+
+
+# ---------------------------------------------------------------- our path
+
+def run_ours(args):
+    import numpy as np
+    import torch
+    import __graft_entry__
+    rank, world, local = dist_env()
+    torch.cuda.set_device(local)
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    __graft_entry__.build()
+    import paper_2112_15083_gb300 as P
+    from paper_2112_15083_gb300 import circuits as cg
+    w = WORKLOAD
+    circ = cg.sycamore_grid(w["rows"], w["cols"], w["cycles"], seed=w["seed"])
+    openq = cg.default_open_qubits(w["rows"], w["cols"], w["n_open"])
+    C = P.circuit_load(circ.serialize())
+    plan = P.plan(C, openq, n_auto_sliced=w["n_sliced"], log2_batches=w["log2_batches"], order_trials=args.trials,
+                  order_seed=0, hbm_budget_bytes=200e9)
+    info = plan.info()
+    slices, F = plan.select(args.fidelity)
+    T = 1 << w["log2_batches"]
+    dev = torch.device("cuda", local)
+    acc = [torch.empty(T, dtype=torch.uint8, device=dev) for _ in range(args.steps)]
+    bits = [torch.empty(T, dtype=torch.int64, device=dev) for _ in range(args.steps)]
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
+    base_t = rank * (1 << 40)
+    seed = args.seed
+    for i in range(args.warmup):
+        plan.sample_step(slices, F, seed, base_t + i * T, accept=acc[0], bits=bits[0])
+    torch.cuda.synchronize()
+    clocks = Clocks(local)
+    ev0 = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    ev1 = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    plan.trace(True)
+    if world > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+    clocks.start()
+    for k in range(args.steps):
+        flush.zero_()
+        ev0[k].record()
+        plan.sample_step(slices, F, seed, base_t + (args.warmup + k) * T, accept=acc[k], bits=bits[k])
+        ev1[k].record()
+    torch.cuda.synchronize()
+    if world > 1:
+        torch.distributed.barrier()
+    clk = clocks.stop()
+    step_ms = [ev0[k].elapsed_time(ev1[k]) for k in range(args.steps)]
+    tot_ms = sum(step_ms)
+    trace = plan.trace_read()
+    plan.trace(False)
+    accepted = int(sum(int(a.sum().item()) for a in acc))
+    if world > 1:
+        t = torch.tensor([tot_ms, float(accepted)], dtype=torch.float64, device=dev)
+        mx = t.clone()
+        torch.distributed.all_reduce(mx, op=torch.distributed.ReduceOp.MAX)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.SUM)
+        tot_ms_max, accepted_all = float(mx[0]), float(t[1])
+    else:
+        tot_ms_max, accepted_all = tot_ms, float(accepted)
+    value = accepted_all / (tot_ms_max / 1e3)
+    flops_step = sum(s["flops_per_launch"] for s in trace)
+
+    # dominant kernel from the live per-step events
+    dom = max(trace, key=lambda s: s["ms"])
+    dom_ms = dom["ms"] / max(1, dom["launches"])
+    pk = peaks()
+    ffma_peak = 152 * 128 * 2 * 2.07e9 / 1e12
+    roofline = {"bound": "alu", "achieved": dom["flops_per_launch"] / (dom_ms / 1e3) / 1e12, "peak": ffma_peak,
+                "unit": "TFLOP/s", "traffic": None}
+    roofline["frac"] = roofline["achieved"] / roofline["peak"]
+    roofline["kernel"] = "cgemm_tile %d (bat,m,n,k bits = %d,%d,%d,%d; %d versions)" % (
+        dom["kernel"], dom["nbat"], dom["nm"], dom["nn"], dom["nk"], dom["nver"])
+    roofline["share_of_step"] = dom["ms"] / max(1e-9, sum(s["ms"] for s in trace))
+    roofline["peak_source"] = "derived: " + FFMA_PEAK_NOTE + " (FP32 FFMA, complex64 path)"
+
+    # end to end through the public API with host buffers (one tn_sample call per step)
+    e2e = None
+    if rank == 0:
+        n_per = T // 2
+        torch.cuda.synchronize()
+        t = time.perf_counter()
+        got = 0
+        groups = 0
+        for k in range(args.steps):
+            b, st = plan.sample(args.fidelity, n_per, seed=seed + 1 + k)
+            got += len(b)
+            groups += (st["steps"] + T - 1) // T
+        dt = time.perf_counter() - t
+        e2e = {"value": got / dt, "unit": "samples/s", "h2d_bytes_per_step": 0,
+               "d2h_bytes_per_step": int(groups * T * (1 + 8 + 8) / args.steps + n_per * 8),
+               "api": "tn_sample(host bitstrings), %d samples per call" % n_per}
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        os.environ.setdefault("OMP_NUM_THREADS", str(cpu_cores()))
+        t = time.perf_counter()
+        a = oracle_step(circ, openq, T, seed, 0)
+        dt = time.perf_counter() - t
+        cpu = {"value": a / dt, "unit": "samples/s", "cores": int(os.environ["OMP_NUM_THREADS"]), "kind": "oracle",
+               "sample": "one step: FP64 state vector of the 28-qubit circuit + the sampler on %d batches "
+                         "(%d accepted in %.1f s)" % (T, a, dt)}
+
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": "samples/s", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": tot_ms_max / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "c64 (fp32 FFMA), fp64 slice sum/sampler",
+            "data": "synthetic", "config": workload_config(args),
+            "fidelity": F, "contraction_tflops": flops_step * args.steps / (tot_ms / 1e3) / 1e12,
+            "flops_per_step": flops_step, "plan": info, "clocks": clk, "roofline": roofline,
+            "cpu_baseline": cpu, "e2e": e2e,
+            "gpu_launches": args.steps * (len(trace) + 4),
+        }
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        torch.distributed.destroy_process_group()
+
+
+if __name__ == "__main__":
+    a = parse()
+    if a.impl == "reference":
+        run_reference(a)
+    else:
+        run_ours(a)

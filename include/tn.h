@@ -1,0 +1,261 @@
+/*
+ * tn.h — C-ABI of the GB300 sliced-contraction sampler (libtn.so).
+ *
+ * Method: arXiv:2112.15083, "Classical Sampling of Random Quantum Circuits with
+ * Bounded Fidelity".  Batches of 2^|A| amplitudes of a random circuit are computed by
+ * contracting its tensor network once per slice (an assignment of the sliced legs)
+ * and summing over a chosen set of slices only (Sec. I.C); the slices are chosen by
+ * their norms R[i] = ||psi_i||^2 (Sec. I.A-B, App. B Alg. 1-2); bitstrings are drawn
+ * from the batches by modified frugal rejection sampling (Sec. II.A).
+ *
+ * Conventions shared by every entry point:
+ *  - Return codes: TN_OK (0) or a negative TN_E* code.  tn_strerror() names a code;
+ *    tn_last_error() gives a detail message for the calling thread's last failure.
+ *  - Qubit q of a bitstring is bit q of a uint64 (so at most 64 qubits).
+ *  - Wire segments ("vertices", the tensor legs of App. B): single-qubit gates are
+ *    merged into the preceding two-qubit gate on their wire (leading ones into the
+ *    |0> input), so segment (q, s) is the wire of qubit q just before its (s+1)-th
+ *    two-qubit gate, and s = (two-qubit gates on q) is the circuit output of q.
+ *    Only internal segments (1 <= s < two-qubit gates on q) can be sliced.
+ *  - Open qubits A (the batch, N_A = 2^|A|) are given in an order: bit r of the
+ *    in-batch index i is qubit open[r].  Closed qubits B are the others in ascending
+ *    order: bit c of a closed pattern j is the c-th closed qubit.
+ *  - A slice is a uint64 whose bit e is the value of the e-th sliced edge of the plan.
+ *  - Complex numbers are interleaved (re, im) pairs of doubles.
+ *  - The caller owns every array it passes; the plan copies what it keeps.  The plan
+ *    owns its device memory (see tn_plan_opts.alloc) and enqueues work on
+ *    tn_plan_opts.stream; calls return after that work has finished.
+ *  - Not thread-safe per plan: one call at a time per plan handle.
+ */
+#ifndef TN_H
+#define TN_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define TN_OK 0
+#define TN_EINVAL (-1)       /* bad argument, circuit, order or slice set */
+#define TN_ENOMEM (-2)       /* host or device allocation failed, or the HBM budget is exceeded */
+#define TN_ETIMEOUT (-3)     /* a bounded device-side wait gave up */
+#define TN_EDEVICE (-4)      /* CUDA error (no device, launch failure, ...) */
+#define TN_EUNSUPPORTED (-5) /* valid request outside what this build implements */
+
+/* Precision of the pairwise contractions (north-star "split precision"). */
+#define TN_PREC_C64 0    /* complex64 operands, FP32 FFMA accumulation */
+#define TN_PREC_BF16X2 1 /* hi+lo bf16 split operands on tcgen05, FP32 accumulation */
+#define TN_PREC_FP16X2 2 /* hi+lo fp16 split operands (scaled) on tcgen05, FP32 accumulation */
+
+/* Flags for buffers passed to tn_contract / tn_sample. */
+#define TN_DEVICE_BUFFERS 1 /* closed_bits / amps / bitstrings are device pointers */
+
+typedef struct tn_circuit_s *tn_circuit_h;
+typedef struct tn_plan_s *tn_plan_h;
+
+typedef struct {
+    int32_t qubit;
+    int32_t segment;
+} tn_edge;
+
+/* Device memory provider.  alloc returns NULL on failure; both run on the host
+ * thread that made the call.  A NULL alloc means cudaMallocAsync/cudaFreeAsync on
+ * the plan's stream. */
+typedef void *(*tn_alloc_fn)(size_t bytes, void *stream, void *ctx);
+typedef void (*tn_free_fn)(void *ptr, size_t bytes, void *stream, void *ctx);
+
+typedef struct {
+    int32_t precision;       /* TN_PREC_* */
+    int32_t log2_batches;    /* batches contracted together: T = 2^log2_batches (0..16) */
+    uint64_t order_seed;     /* seed of the randomised greedy contraction order */
+    int32_t order_trials;    /* greedy trials (best estimated time wins); <= 0: 64 */
+    int32_t n_auto_sliced;   /* when sliced == NULL: how many edges the planner slices */
+    double hbm_budget_bytes; /* device working-set limit per call; <= 0: 64 GiB */
+    void *stream;            /* cudaStream_t; NULL = legacy default stream */
+    tn_alloc_fn alloc;       /* optional device allocator */
+    tn_free_fn free;
+    void *alloc_ctx;
+} tn_plan_opts;
+
+/* Fill opts with the defaults above (C64, T = 256, seed 0, 64 trials, 64 GiB). */
+void tn_plan_opts_default(tn_plan_opts *opts);
+
+/* Parse a serialized circuit: b"RQC1", uint32 n_qubits, uint32 n_gates, then per gate
+ * uint32 arity (1|2), uint32 q0, uint32 q1 (0xFFFFFFFF if arity 1) and (2^arity)^2
+ * complex128 matrix entries, row-major; a two-qubit basis index is 2*bit(q0)+bit(q1).
+ * (The circuit C of Sec. I.A; gates are the tuples (l, A, q) of App. B.)
+ * Errors: TN_EINVAL on a malformed buffer or more than 64 qubits. */
+int tn_circuit_load(const void *buf, size_t len, tn_circuit_h *out);
+void tn_circuit_destroy(tn_circuit_h c);
+
+/*
+ * Build a contraction plan: the tensor network of C with the open qubits' output legs
+ * left open and the closed ones bound to a batch-indexed selector, a contraction tree
+ * (Sec. I, "contraction tree"), the sliced legs I (Sec. I, "sliced variables") and a
+ * compiled list of pairwise contractions, each a batched complex GEMM whose output is
+ * written in the layout its consumer reads.
+ *
+ *  order        NULL, or 2*(n_leaves-1) int32 giving the contraction tree as SSA pairs:
+ *               leaves are the merged two-qubit gates in circuit order, then one leaf
+ *               per qubit without two-qubit gates; each pair creates the next id.
+ *  sliced       NULL (the planner picks opts->n_auto_sliced edges) or n_sliced internal
+ *               wire segments, n_sliced <= 62.
+ *  open_qubits  n_open distinct qubits (n_open <= 16); the batch size is 2^n_open.
+ * Errors: TN_EINVAL (bad order / segment / qubit), TN_ENOMEM, TN_EDEVICE.
+ */
+int tn_plan(tn_circuit_h c, const int32_t *order, int32_t n_order, const tn_edge *sliced,
+            int32_t n_sliced, const int32_t *open_qubits, int32_t n_open,
+            const tn_plan_opts *opts, tn_plan_h *out);
+void tn_plan_destroy(tn_plan_h p);
+
+typedef struct {
+    int32_t n_qubits, n_open, n_closed, log2_batches;
+    int32_t n_leaves, n_steps, n_sliced;
+    int32_t log2_max_tensor;     /* largest per-slice intermediate (elements, log2) */
+    double flops_per_slice;      /* 8 * sum over steps of prod(dims), one slice, one group */
+    double flops_all_slices;     /* same, summed with reuse over all 2^n_sliced slices */
+} tn_plan_info;
+
+int tn_plan_get_info(tn_plan_h p, tn_plan_info *info);
+/*
+ * Host-only planning (no device work), for inspection and tests: runs the same planner
+ * as tn_plan and fills info; if steps != NULL, writes up to cap_steps rows of five
+ * int32 per step (batch bits, m bits, n bits, k bits, log2 versions over all slices);
+ * if sliced_out != NULL, writes up to cap_sliced sliced edges in slice-bit order.
+ */
+int tn_plan_host(tn_circuit_h c, const int32_t *order, int32_t n_order, const tn_edge *sliced,
+                 int32_t n_sliced, const int32_t *open_qubits, int32_t n_open,
+                 const tn_plan_opts *opts, tn_plan_info *info, int32_t *steps, int32_t cap_steps,
+                 tn_edge *sliced_out, int32_t cap_sliced);
+
+/*
+ * App. B Alg. 2 SlicedVertexSelect(C, I, k) on the host: greedy choice of S in I, each
+ * step taking the candidate u outside S and L'_C(S) that minimises |L'_C(S + {u})|
+ * (ties: first in I), then dropping from S the vertices u depends on.  Vertices are wire
+ * segments; s_index receives positions into I of S in (qubit, segment) order.
+ */
+int tn_sliced_vertex_select(tn_circuit_h c, const tn_edge *I, int32_t n_I, int32_t k,
+                            int32_t *s_index, int32_t *k_out);
+
+/* The plan's sliced edges I in slice-bit order (cap entries at most). */
+int tn_plan_sliced_edges(tn_plan_h p, tn_edge *out, int32_t cap, int32_t *n_out);
+
+/*
+ * Partial-slice norms (Sec. I.A, App. B Alg. 1 steps 1-3): S = SlicedVertexSelect(C, I,
+ * k0) with k0 = ceil(3 - log2 f) (Alg. 2), C1 = union of the lightcones of S, and
+ * R[i] = <0|C1* delta_{S=i} C1|0> = ||psi_i||^2 for i in {0,1}^k, computed on the GPU
+ * by contracting the network C1 (x) C1* with the S legs identified (Fig. 1), in FP64.
+ *  s_index  out, k entries: positions of S within the plan's sliced edges (ascending);
+ *           bit t of i is S[t].
+ *  R        out, host, cap_R >= 2^k doubles.
+ * Errors: TN_EINVAL (f outside (0,1], cap too small), TN_EDEVICE.
+ */
+int tn_partial_norms(tn_plan_h p, double f, int32_t *s_index, int32_t *k, double *R,
+                     int64_t cap_R);
+
+/*
+ * Slice cut (Alg. 1 steps 4-5) on the GPU: sort R descending (ties: index ascending),
+ * sum in that order in FP64, keep the minimal prefix whose sum reaches f (all of it if
+ * rounding keeps the total below f).  R: host array of 2^k doubles.  X: out, host,
+ * the kept indices in sorted order (cap 2^k); F: the kept sum.  k <= 20.
+ */
+int tn_slice_cut(const double *R, int32_t k, double f, void *stream, int32_t *X,
+                 int32_t *n_x, double *F);
+
+/*
+ * Slice selection for fidelity f (Alg. 1): tn_partial_norms + tn_slice_cut, then the
+ * slice set X x {0,1}^{|I|-k} (Sec. I.C step 1) written to slices (cap entries).  When
+ * f >= 1 every slice is kept and F = 1.  n_slices receives the set size even if cap is
+ * too small (then TN_EINVAL).
+ */
+int tn_select(tn_plan_h p, double f, uint64_t *slices, int64_t cap, int64_t *n_slices,
+              double *F);
+
+/*
+ * Amplitudes of n_batches batches summed over a slice set (Sec. I.C step 1; no
+ * normalisation): amps[t*2^n_open + i] = sum over slices s of <i, closed_bits[t]|C_s|0>,
+ * C_s the network with the sliced legs fixed by s.  Slices are summed in FP64 in the
+ * given order.  Slices must be distinct; closed_bits holds one pattern per batch.
+ *  flags & TN_DEVICE_BUFFERS: closed_bits and amps are device pointers, else host.
+ * Errors: TN_EINVAL (duplicate or out-of-range slice), TN_ENOMEM (budget), TN_EDEVICE.
+ */
+int tn_contract(tn_plan_h p, const uint64_t *slices, int64_t n_slices, const uint64_t *closed_bits,
+                int64_t n_batches, double *amps, int32_t flags);
+
+typedef struct {
+    double F;           /* retained fidelity sum_{i in X} R[i] (1 when f >= 1) */
+    double eps_hat;     /* Sec. II.C: eps_J / |J| over the computed batches */
+    int64_t steps;      /* batches computed (|J|) */
+    int64_t accepted;   /* accepted batches (>= N unless max steps reached) */
+    int64_t n_slices;   /* size of the contracted slice set */
+    double flops;       /* algorithmic FLOPs of the contractions (8 * complex MACs) */
+} tn_sample_stats;
+
+/*
+ * Sampling with fidelity (Sec. II.A): select slices for f_target (Alg. 1), then for
+ * t = 0, 1, ... draw j_t uniformly, contract the batch j_t over the slices, set
+ * p_{i,j} = |a_{i,j}|^2 / F, accept with probability min(1, p_j N_B / alpha) and pick i
+ * with probability p_{i,j}/p_j.  Batches are processed 2^log2_batches at a time until N
+ * are accepted (at most ceil(8 alpha N) + 4096 batches).  Random numbers: Philox4x32-10
+ * with key = seed and counter = (t, stream): stream 0 gives j (low |B| bits of words
+ * 0-1) and u (words 2-3), stream 1 gives v; a 64-bit word w maps to (w >> 11) 2^-53.
+ * Accept iff u*alpha < p_j*N_B.  Requires n_open = 6.
+ *  bitstrings  out, N entries, the accepted strings in t order.
+ *  alpha       > 1 (paper: 2).
+ */
+int tn_sample(tn_plan_h p, double f_target, int64_t N, uint64_t seed, double alpha,
+              uint64_t *bitstrings, int32_t flags, tn_sample_stats *stats);
+
+/*
+ * One sampling step over one batch group (Sec. II.A for t = t0 .. t0 + T - 1, T =
+ * 2^log2_batches): draw j_t (Philox, as in tn_sample), contract the T batches over the
+ * given slice set, set p = |a|^2 / F, run the accept / pick step and write accept[t] (0/1)
+ * and bits[t] (the bitstring (i_t, j_t)).  reuse_stem != 0 skips the contractions that do
+ * not depend on the batch (kept from the previous step on the same slice set).
+ * flags & TN_DEVICE_BUFFERS: accept / bits are device arrays and the call returns without
+ * synchronising the stream; otherwise they are host arrays and the call synchronises.
+ */
+int tn_sample_step(tn_plan_h p, const uint64_t *slices, int64_t n_slices, double F, uint64_t seed,
+                   uint64_t t0, double alpha, int32_t reuse_stem, uint8_t *accept, uint64_t *bits,
+                   int32_t flags);
+
+/* Tracing: when on, every execution records CUDA events around each contraction step
+ * on the plan's stream.  tn_trace_read synchronises and reports, per step, the launches,
+ * the summed device time, and the algorithmic FLOPs (8 per complex multiply-add) and
+ * bytes (operands read + result written, complex64) of one launch. */
+typedef struct {
+    int32_t step;
+    int32_t launches;
+    double ms;
+    double flops_per_launch;
+    double bytes_per_launch;
+    int32_t nbat, nm, nn, nk;
+    int64_t nver;
+    int32_t kernel; /* 0: row kernel, 1..: tile kernel variant */
+} tn_step_trace;
+int tn_trace_enable(tn_plan_h p, int32_t on);
+int tn_trace_read(tn_plan_h p, tn_step_trace *out, int32_t cap, int32_t *n_out);
+
+/*
+ * The sampler step alone (Sec. II.A steps 2-3) on given probabilities: p is a device
+ * array of T*64 doubles (p[t*64 + i] = p_{i,j_t}, batch index t0 + t); writes accept[t]
+ * (0/1) and pick[t] (device arrays).  The batch total and prefix sums use a 32-lane
+ * Kogge-Stone scan of pair sums (offsets 1,2,4,8,16); p_j is the last lane's total; the
+ * pick is the smallest i whose prefix exceeds v*p_j, else the last i with p_i > 0.
+ */
+int tn_rejection_sample(const double *p, int64_t T, int32_t b_bits, double alpha, uint64_t seed,
+                        uint64_t t0, uint8_t *accept, int32_t *pick, void *stream);
+
+/* Batch draws j_t = low b_bits of Philox(seed, t0 + t, stream 0) words 0-1 (device out). */
+int tn_draw_batches(uint64_t seed, uint64_t t0, int64_t T, int32_t b_bits, uint64_t *j,
+                    void *stream);
+
+const char *tn_strerror(int code);
+const char *tn_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* TN_H */

@@ -379,7 +379,7 @@ def batch_draws(seed: int, T: int, b_bits: int, t0: int = 0) -> np.ndarray:
 
 
 def sample(p_model: np.ndarray, n: int, open_qubits, N: int, seed: int, alpha: float = 2.0,
-           max_steps: int | None = None):
+           max_steps: int | None = None, chunk: int = 1024):
     """Modified frugal rejection sampling (Sec. II.A) from a normalised distribution
     p_model over 2^n bitstrings with batches over the 6 open qubits.  Returns
     (samples in step order (first N accepted), steps used, epsilon_hat)."""
@@ -390,7 +390,6 @@ def sample(p_model: np.ndarray, n: int, open_qubits, N: int, seed: int, alpha: f
     out = []
     t = 0
     eps_sum = 0.0
-    chunk = 1024
     limit = max_steps if max_steps is not None else 64 * N + 1024
     while len(out) < N and t < limit:
         T = min(chunk, limit - t)

@@ -1,0 +1,1001 @@
+// libtn executor and C-ABI (see include/tn.h).
+//
+// A plan holds the compiled amplitude network (leaves on the device, a step list) and
+// executes a slice set as follows: every tree node x gets one version per distinct
+// projection of the slice set on the sliced legs below x (so intermediates shared by
+// several slices are computed once); each step is one launch over all versions; the
+// root versions are summed in FP64 in slice order (Sec. I.C).  Leaves holding closed
+// output legs are re-materialised per batch group with the group's closed patterns.
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <numeric>
+#include <unordered_map>
+
+#include "kernels.cuh"
+#include "tn_internal.h"
+
+namespace {
+thread_local std::string g_err;
+}
+void tn_set_error(const std::string &m) { g_err = m; }
+
+#define CK(x)                                                                                   \
+    do {                                                                                        \
+        cudaError_t e_ = (x);                                                                   \
+        if (e_ != cudaSuccess) {                                                                \
+            tn_set_error(std::string("CUDA error: ") + cudaGetErrorString(e_) + " in " #x);     \
+            return TN_EDEVICE;                                                                  \
+        }                                                                                       \
+    } while (0)
+
+#define RC(x)                       \
+    do {                            \
+        int r_ = (x);               \
+        if (r_ != TN_OK) return r_; \
+    } while (0)
+
+namespace {
+
+struct DevMem {
+    tn_alloc_fn alloc = nullptr;
+    tn_free_fn free = nullptr;
+    void *ctx = nullptr;
+    cudaStream_t stream = nullptr;
+    void *get(size_t bytes) {
+        bytes = std::max<size_t>(bytes, 256);
+        void *p = nullptr;
+        if (alloc) p = alloc(bytes, stream, ctx);
+        else if (cudaMallocAsync(&p, bytes, stream) != cudaSuccess) p = nullptr;
+        return p;
+    }
+    void put(void *p, size_t bytes) {
+        if (!p) return;
+        bytes = std::max<size_t>(bytes, 256);
+        if (free) free(p, bytes, stream, ctx);
+        else cudaFreeAsync(p, stream);
+    }
+};
+
+struct DBuf {
+    void *p = nullptr;
+    size_t bytes = 0;
+};
+
+int ensure(DevMem &mem, DBuf &b, size_t bytes) {
+    if (b.p && b.bytes >= bytes) return TN_OK;
+    mem.put(b.p, b.bytes);
+    b.p = nullptr;
+    b.bytes = 0;
+    size_t want = std::max<size_t>(bytes, 256);
+    b.p = mem.get(want);
+    if (!b.p) {
+        tn_set_error("device allocation of " + std::to_string(want) + " bytes failed");
+        return TN_ENOMEM;
+    }
+    b.bytes = want;
+    return TN_OK;
+}
+
+void release(DevMem &mem, DBuf &b) {
+    mem.put(b.p, b.bytes);
+    b.p = nullptr;
+    b.bytes = 0;
+}
+
+// Versions and memory layout of one execution of a compiled network on a slice set.
+struct CallPlan {
+    std::vector<uint64_t> slices;              // key
+    std::vector<long long> nver;               // per node
+    std::vector<size_t> off;                   // arena byte offset per internal node
+    std::vector<size_t> tab_off;               // per step: index of ptrA table in tables
+    size_t root_tab = 0;                       // index of the root table
+    std::vector<const void *> host_tab;        // pointer tables (device addresses)
+    size_t arena_bytes = 0;
+    double flops_all = 0, flops_beta = 0;      // per execution (all steps / beta steps)
+    bool valid = false;
+};
+
+struct CNet {
+    Network net;
+    Tree tree;
+    std::vector<Step> steps;
+    int elem = 8;  // 8: complex64, 16: complex128
+    std::vector<DBuf> leaf_src, leaf_dst;
+    std::vector<int> leaf_codebits;
+    std::vector<std::vector<int>> leaf_sl;  // sliced legs (e) in leg order
+    std::vector<char> leaf_beta;
+    std::vector<tnk::MatDesc> beta_descs;
+    DBuf d_beta_descs;
+    DBuf arena, tables;
+    CallPlan cp;
+    std::vector<int> parent;
+    size_t leaf_bytes = 0;
+    // tracing
+    bool trace = false;
+    std::vector<cudaEvent_t> ev;        // 2 per step
+    std::vector<int> ev_pending;        // per step: events recorded and not yet read
+    std::vector<int> tr_launches;
+    std::vector<double> tr_ms;
+    std::vector<int> tr_kernel;
+};
+
+}  // namespace
+
+struct tn_plan_s {
+    tn_circuit_s circ;
+    Merged mg;
+    tn_plan_opts opts{};
+    DevMem mem;
+    std::vector<tn_edge> I;
+    std::vector<int> open, closed;
+    int log2T = 0;
+    CNet amp;
+    DBuf d_closed, d_amps, d_j, d_acc, d_pick, d_eps, d_bits, d_R, d_X;
+    double budget = 0;
+    // norm cache
+    double norm_f = -1;
+    std::vector<int> norm_S;
+    std::vector<double> norm_R;
+};
+
+// ---------------------------------------------------------------- leaves
+
+namespace {
+
+int setup_leaves(DevMem &mem, CNet &cn) {
+    const int L = (int)cn.net.leaves.size();
+    cn.leaf_src.assign(L, DBuf());
+    cn.leaf_dst.assign(L, DBuf());
+    cn.leaf_codebits.assign(L, 0);
+    cn.leaf_sl.assign(L, {});
+    cn.leaf_beta.assign(L, 0);
+    cn.beta_descs.clear();
+    std::vector<tnk::MatDesc> static_descs;
+    cn.leaf_bytes = 0;
+    for (int i = 0; i < L; i++) {
+        const Leaf &lf = cn.net.leaves[i];
+        const Node &nd = cn.tree.nodes[i];
+        tnk::MatDesc d;
+        std::memset(&d, 0, sizeof(d));
+        std::vector<int> sl, cl, clref;
+        for (size_t l = 0; l < lf.kind.size(); l++) {
+            if (lf.kind[l] == LEG_SLICED) { sl.push_back((int)l); cn.leaf_sl[i].push_back(lf.ref[l]); }
+            if (lf.kind[l] == LEG_CLOSED) { cl.push_back((int)l); clref.push_back(lf.ref[l]); }
+        }
+        if (sl.size() > 8 || cl.size() > 8 || nd.layout.size() > (size_t)tnk::kMaxBits) {
+            tn_set_error("leaf with too many legs");
+            return TN_EUNSUPPORTED;
+        }
+        d.nd = (int)nd.layout.size();
+        d.ncode_bits = (int)sl.size();
+        d.ncl = (int)cl.size();
+        for (int t = 0; t < d.nd; t++) {
+            int id = nd.layout[t];
+            int leg = -1;
+            for (size_t l = 0; l < lf.kind.size(); l++)
+                if (lf.kind[l] == LEG_NET && lf.ref[l] == id) leg = (int)l;
+            if (leg >= 0) d.dst_leg[t] = (int8_t)leg;
+            else if (id >= cn.net.beta_base && id < cn.net.beta_base + cn.net.n_beta) d.dst_leg[t] = (int8_t)(-1 - (id - cn.net.beta_base));
+            else { tn_set_error("leaf layout index not found"); return TN_EINVAL; }
+        }
+        for (size_t u = 0; u < sl.size(); u++) d.sl_leg[u] = (int8_t)sl[u];
+        for (size_t c = 0; c < cl.size(); c++) { d.cl_leg[c] = (int8_t)cl[c]; d.cl_ref[c] = (int16_t)clref[c]; }
+        cn.leaf_codebits[i] = d.ncode_bits;
+        cn.leaf_beta[i] = !cl.empty();
+        size_t src_bytes = lf.data.size() * sizeof(double2);
+        RC(ensure(mem, cn.leaf_src[i], src_bytes));
+        CK(cudaMemcpyAsync(cn.leaf_src[i].p, lf.data.data(), src_bytes, cudaMemcpyHostToDevice, mem.stream));
+        size_t dst_bytes = (size_t(1) << (d.nd + d.ncode_bits)) * cn.elem;
+        RC(ensure(mem, cn.leaf_dst[i], dst_bytes));
+        cn.leaf_bytes += dst_bytes + src_bytes;
+        d.src = static_cast<const double2 *>(cn.leaf_src[i].p);
+        d.dst = cn.leaf_dst[i].p;
+        if (cl.empty()) static_descs.push_back(d);
+        else cn.beta_descs.push_back(d);
+    }
+    // static leaves: materialise once
+    if (!static_descs.empty()) {
+        DBuf tmp;
+        RC(ensure(mem, tmp, static_descs.size() * sizeof(tnk::MatDesc)));
+        CK(cudaMemcpyAsync(tmp.p, static_descs.data(), static_descs.size() * sizeof(tnk::MatDesc),
+                           cudaMemcpyHostToDevice, mem.stream));
+        dim3 grid(4, (unsigned)static_descs.size());
+        if (cn.elem == 8) tnk::materialize<float2><<<grid, 256, 0, mem.stream>>>((const tnk::MatDesc *)tmp.p, nullptr);
+        else tnk::materialize<double2><<<grid, 256, 0, mem.stream>>>((const tnk::MatDesc *)tmp.p, nullptr);
+        CK(cudaGetLastError());
+        CK(cudaStreamSynchronize(mem.stream));
+        release(mem, tmp);
+    }
+    if (!cn.beta_descs.empty()) {
+        RC(ensure(mem, cn.d_beta_descs, cn.beta_descs.size() * sizeof(tnk::MatDesc)));
+        CK(cudaMemcpyAsync(cn.d_beta_descs.p, cn.beta_descs.data(), cn.beta_descs.size() * sizeof(tnk::MatDesc),
+                           cudaMemcpyHostToDevice, mem.stream));
+    }
+    CK(cudaStreamSynchronize(mem.stream));
+    cn.parent.assign(cn.tree.nodes.size(), -1);
+    for (size_t i = 0; i < cn.tree.nodes.size(); i++)
+        for (int c : cn.tree.nodes[i].ch)
+            if (c >= 0) cn.parent[c] = (int)i;
+    return TN_OK;
+}
+
+void free_cnet(DevMem &mem, CNet &cn) {
+    for (auto &b : cn.leaf_src) release(mem, b);
+    for (auto &b : cn.leaf_dst) release(mem, b);
+    release(mem, cn.d_beta_descs);
+    release(mem, cn.arena);
+    release(mem, cn.tables);
+    for (auto &x : cn.ev) cudaEventDestroy(x);
+    cn.ev.clear();
+}
+
+inline uint64_t leaf_code(uint64_t w, const std::vector<int> &sl) {
+    uint64_t code = 0;
+    for (size_t u = 0; u < sl.size(); u++) code |= ((w >> sl[u]) & 1ull) << u;
+    return code;
+}
+
+// Versions, arena offsets and pointer tables for a slice set.
+int prepare_call(DevMem &mem, CNet &cn, const std::vector<uint64_t> &slices, double budget) {
+    if (cn.cp.valid && cn.cp.slices == slices) return TN_OK;
+    CallPlan cp;
+    cp.slices = slices;
+    const auto &nodes = cn.tree.nodes;
+    const int NN = (int)nodes.size();
+    std::vector<std::vector<uint64_t>> vals(NN);
+    std::vector<std::unordered_map<uint64_t, int>> index(NN);
+    cp.nver.assign(NN, 0);
+    for (int x = 0; x < NN; x++) {
+        const uint64_t D = nodes[x].dep;
+        for (uint64_t s : slices) {
+            uint64_t w = s & D;
+            if (index[x].emplace(w, (int)vals[x].size()).second) vals[x].push_back(w);
+        }
+        cp.nver[x] = (long long)vals[x].size();
+    }
+    // arena: first fit, children released after their parent's step; beta-free
+    // nodes consumed by beta steps stay alive (reused by later batch groups)
+    auto tensor_bytes = [&](int x) {
+        return (size_t)cp.nver[x] * (size_t(1) << nodes[x].idx.count()) * (size_t)cn.elem;
+    };
+    struct Blk { size_t off, len; };
+    std::vector<Blk> freel;
+    size_t top = 0;
+    auto alloc = [&](size_t len) {
+        len = (len + 255) & ~size_t(255);
+        for (size_t i = 0; i < freel.size(); i++)
+            if (freel[i].len >= len) {
+                size_t o = freel[i].off;
+                freel[i].off += len;
+                freel[i].len -= len;
+                if (!freel[i].len) freel.erase(freel.begin() + i);
+                return o;
+            }
+        size_t o = top;
+        top += len;
+        return o;
+    };
+    auto dealloc = [&](size_t off, size_t len) {
+        len = (len + 255) & ~size_t(255);
+        freel.push_back({off, len});
+        std::sort(freel.begin(), freel.end(), [](const Blk &a, const Blk &b) { return a.off < b.off; });
+        std::vector<Blk> merged;
+        for (auto &b : freel) {
+            if (!merged.empty() && merged.back().off + merged.back().len == b.off) merged.back().len += b.len;
+            else merged.push_back(b);
+        }
+        if (!merged.empty() && merged.back().off + merged.back().len == top) { top = merged.back().off; merged.pop_back(); }
+        freel.swap(merged);
+    };
+    cp.off.assign(NN, 0);
+    size_t peak = 0;
+    for (const Step &s : cn.steps) {
+        cp.off[s.c] = alloc(tensor_bytes(s.c));
+        peak = std::max(peak, top);
+        for (int ch : {s.a, s.b}) {
+            if (nodes[ch].ch[0] < 0) continue;
+            bool persistent = !nodes[ch].beta && nodes[s.c].beta;
+            if (!persistent) dealloc(cp.off[ch], tensor_bytes(ch));
+        }
+    }
+    cp.arena_bytes = std::max<size_t>(peak, 256);
+    if ((double)cp.arena_bytes + (double)cn.leaf_bytes > budget) {
+        tn_set_error("working set of " + std::to_string(cp.arena_bytes) + " bytes exceeds the HBM budget");
+        return TN_ENOMEM;
+    }
+    RC(ensure(mem, cn.arena, cp.arena_bytes));
+    // pointer tables
+    auto base_of = [&](int x, uint64_t w) -> const void * {
+        if (nodes[x].ch[0] < 0) {
+            uint64_t code = leaf_code(w, cn.leaf_sl[x]);
+            size_t sz = (size_t(1) << nodes[x].layout.size()) * cn.elem;
+            return static_cast<const char *>(cn.leaf_dst[x].p) + code * sz;
+        }
+        size_t sz = (size_t(1) << nodes[x].idx.count()) * cn.elem;
+        return static_cast<const char *>(cn.arena.p) + cp.off[x] + (size_t)index[x].at(w) * sz;
+    };
+    cp.host_tab.clear();
+    cp.tab_off.clear();
+    cp.flops_all = cp.flops_beta = 0;
+    for (const Step &s : cn.steps) {
+        cp.tab_off.push_back(cp.host_tab.size());
+        const uint64_t Da = nodes[s.a].dep, Db = nodes[s.b].dep;
+        for (uint64_t w : vals[s.c]) cp.host_tab.push_back(base_of(s.a, w & Da));
+        for (uint64_t w : vals[s.c]) cp.host_tab.push_back(base_of(s.b, w & Db));
+        double fl = s.flops_per_version * (double)cp.nver[s.c];
+        cp.flops_all += fl;
+        if (nodes[s.c].beta) cp.flops_beta += fl;
+    }
+    cp.root_tab = cp.host_tab.size();
+    const int root = cn.tree.root;
+    for (uint64_t s : slices) cp.host_tab.push_back(base_of(root, s & nodes[root].dep));
+    RC(ensure(mem, cn.tables, cp.host_tab.size() * sizeof(void *)));
+    CK(cudaMemcpyAsync(cn.tables.p, cp.host_tab.data(), cp.host_tab.size() * sizeof(void *),
+                       cudaMemcpyHostToDevice, mem.stream));
+    CK(cudaStreamSynchronize(mem.stream));
+    cp.valid = true;
+    cn.cp = std::move(cp);
+    return TN_OK;
+}
+
+template <typename T>
+int launch_step(CNet &cn, const Step &s, cudaStream_t st) {
+    const CallPlan &cp = cn.cp;
+    const auto &nodes = cn.tree.nodes;
+    tnk::GemmParams p;
+    std::memset(&p, 0, sizeof(p));
+    const void *const *tab = static_cast<const void *const *>(cn.tables.p);
+    p.ptrA = tab + cp.tab_off[&s - cn.steps.data()];
+    p.nver = cp.nver[s.c];
+    p.ptrB = p.ptrA + p.nver;
+    p.C = static_cast<char *>(cn.arena.p) + cp.off[s.c];
+    p.c_vstride = 1LL << nodes[s.c].idx.count();
+    p.lm = s.nm;
+    p.ln = s.nn;
+    p.lk = s.nk;
+    p.lbat = s.nbat;
+    if (s.nbat + s.nm + s.nn > tnk::kMaxBits) { tn_set_error("step too large"); return TN_EUNSUPPORTED; }
+    for (int i = 0; i < s.nbat; i++) p.pos_bat[i] = s.pos_bat[i];
+    for (int i = 0; i < s.nm; i++) p.pos_m[i] = s.pos_m[i];
+    for (int i = 0; i < s.nn; i++) p.pos_n[i] = s.pos_n[i];
+    const size_t si = &s - cn.steps.data();
+    if (s.nn <= 4 && s.nk <= 6) {
+        if (cn.trace) cn.tr_kernel[si] = 0;
+        long long rows = p.nver << (p.lbat + p.lm);
+        unsigned blocks = (unsigned)((rows + 255) / 256);
+        switch (s.nn) {
+            case 0: tnk::cgemm_row<T, 1><<<blocks, 256, 0, st>>>(p); break;
+            case 1: tnk::cgemm_row<T, 2><<<blocks, 256, 0, st>>>(p); break;
+            case 2: tnk::cgemm_row<T, 4><<<blocks, 256, 0, st>>>(p); break;
+            case 3: tnk::cgemm_row<T, 8><<<blocks, 256, 0, st>>>(p); break;
+            default: tnk::cgemm_row<T, 16><<<blocks, 256, 0, st>>>(p); break;
+        }
+    } else {
+        auto launch = [&](auto kern, int TM, int TN, int nthreads) {
+            if (cn.trace) cn.tr_kernel[si] = TM * 1000 + TN;
+            int ltm = std::min(s.nm, __builtin_ctz(TM)), ltn = std::min(s.nn, __builtin_ctz(TN));
+            long long blocks = p.nver << (s.nbat + (s.nm - ltm) + (s.nn - ltn));
+            kern<<<(unsigned)blocks, nthreads, 0, st>>>(p);
+        };
+        constexpr int TK = sizeof(T) == 8 ? 16 : 8;
+        if (s.nm >= 7 && s.nn >= 6) launch(tnk::cgemm_tile<T, 128, 64, TK, 8, 4>, 128, 64, 256);
+        else if (s.nm >= 6 && s.nn >= 6) launch(tnk::cgemm_tile<T, 64, 64, TK, 4, 4>, 64, 64, 256);
+        else if (s.nm >= 7 && s.nn >= 5) launch(tnk::cgemm_tile<T, 128, 32, TK, 8, 2>, 128, 32, 256);
+        else if (s.nm >= 6 && s.nn >= 5) launch(tnk::cgemm_tile<T, 64, 32, TK, 4, 2>, 64, 32, 256);
+        else if (s.nn >= 5) launch(tnk::cgemm_tile<T, 32, 32, TK, 2, 2>, 32, 32, 256);
+        else launch(tnk::cgemm_tile<T, 128, 16, TK, 4, 2>, 128, 16, 256);
+    }
+    CK(cudaGetLastError());
+    return TN_OK;
+}
+
+// One execution of a compiled network: beta leaves, steps, FP64 slice sum into out.
+int execute(CNet &cn, const uint64_t *d_closed, bool skip_beta_free, double2 *out, cudaStream_t st) {
+    if (!cn.beta_descs.empty()) {
+        dim3 grid(8, (unsigned)cn.beta_descs.size());
+        if (cn.elem == 8) tnk::materialize<float2><<<grid, 256, 0, st>>>((const tnk::MatDesc *)cn.d_beta_descs.p, d_closed);
+        else tnk::materialize<double2><<<grid, 256, 0, st>>>((const tnk::MatDesc *)cn.d_beta_descs.p, d_closed);
+        CK(cudaGetLastError());
+    }
+    for (const Step &s : cn.steps) {
+        if (skip_beta_free && !cn.tree.nodes[s.c].beta) continue;
+        const size_t si = &s - cn.steps.data();
+        if (cn.trace) {
+            if (cn.ev_pending[si]) {  // fold the previous measurement in before reusing the events
+                float ms = 0;
+                CK(cudaEventSynchronize(cn.ev[2 * si + 1]));
+                CK(cudaEventElapsedTime(&ms, cn.ev[2 * si], cn.ev[2 * si + 1]));
+                cn.tr_ms[si] += ms;
+                cn.tr_launches[si]++;
+                cn.ev_pending[si] = 0;
+            }
+            CK(cudaEventRecord(cn.ev[2 * si], st));
+        }
+        if (cn.elem == 8) RC(launch_step<float2>(cn, s, st));
+        else RC(launch_step<double2>(cn, s, st));
+        if (cn.trace) {
+            CK(cudaEventRecord(cn.ev[2 * si + 1], st));
+            cn.ev_pending[si] = 1;
+        }
+    }
+    const int root = cn.tree.root;
+    long long nelem = 1LL << cn.tree.nodes[root].layout.size();
+    const void *const *rt = static_cast<const void *const *>(cn.tables.p) + cn.cp.root_tab;
+    unsigned blocks = (unsigned)((nelem + 255) / 256);
+    if (cn.elem == 8) tnk::slice_sum<float2><<<blocks, 256, 0, st>>>(rt, (long long)cn.cp.slices.size(), nelem, out);
+    else tnk::slice_sum<double2><<<blocks, 256, 0, st>>>(rt, (long long)cn.cp.slices.size(), nelem, out);
+    CK(cudaGetLastError());
+    return TN_OK;
+}
+
+int build_cnet(const Merged &mg, CNet &cn, const tn_plan_opts &o, const int32_t *order, int n_order,
+               DevMem &mem, int elem) {
+    (void)mg;
+    cn.elem = elem;
+    RC(tn_tree_and_compile(cn.net, o, order, n_order, nullptr, cn.tree, cn.steps));
+    return setup_leaves(mem, cn);
+}
+
+}  // namespace
+
+// ---------------------------------------------------------------- C-ABI
+
+extern "C" {
+
+const char *tn_last_error(void) { return g_err.c_str(); }
+
+const char *tn_strerror(int code) {
+    switch (code) {
+        case TN_OK: return "ok";
+        case TN_EINVAL: return "invalid argument";
+        case TN_ENOMEM: return "out of memory or HBM budget exceeded";
+        case TN_ETIMEOUT: return "device wait timed out";
+        case TN_EDEVICE: return "CUDA device error";
+        case TN_EUNSUPPORTED: return "unsupported request";
+        default: return "unknown error";
+    }
+}
+
+void tn_plan_opts_default(tn_plan_opts *o) {
+    std::memset(o, 0, sizeof(*o));
+    o->precision = TN_PREC_C64;
+    o->log2_batches = 8;
+    o->order_seed = 0;
+    o->order_trials = 64;
+    o->n_auto_sliced = 0;
+    o->hbm_budget_bytes = 64.0 * (1ull << 30);
+}
+
+int tn_circuit_load(const void *buf, size_t len, tn_circuit_h *out) {
+    if (!out) { tn_set_error("null output handle"); return TN_EINVAL; }
+    *out = nullptr;
+    auto *c = new (std::nothrow) tn_circuit_s;
+    if (!c) return TN_ENOMEM;
+    int rc = tn_parse_circuit(buf, len, c);
+    if (rc != TN_OK) { delete c; return rc; }
+    *out = c;
+    return TN_OK;
+}
+
+void tn_circuit_destroy(tn_circuit_h c) { delete c; }
+
+int tn_plan(tn_circuit_h c, const int32_t *order, int32_t n_order, const tn_edge *sliced, int32_t n_sliced,
+            const int32_t *open_qubits, int32_t n_open, const tn_plan_opts *opts, tn_plan_h *out) {
+    if (!c || !out || (n_open > 0 && !open_qubits) || n_open < 0 || n_open > 16) {
+        tn_set_error("tn_plan: bad arguments (need circuit, output handle, 0 <= n_open <= 16)");
+        return TN_EINVAL;
+    }
+    *out = nullptr;
+    tn_plan_opts o;
+    if (opts) o = *opts;
+    else tn_plan_opts_default(&o);
+    if (o.log2_batches < 0 || o.log2_batches > 16) { tn_set_error("log2_batches must be in [0,16]"); return TN_EINVAL; }
+    if (o.precision != TN_PREC_C64) {
+        tn_set_error("tn_plan: this build implements the complex64 path only");
+        return TN_EUNSUPPORTED;
+    }
+    if (sliced && (n_sliced < 0 || n_sliced > 62)) { tn_set_error("n_sliced must be in [0,62]"); return TN_EINVAL; }
+    if (!sliced && (o.n_auto_sliced < 0 || o.n_auto_sliced > 62)) { tn_set_error("n_auto_sliced in [0,62]"); return TN_EINVAL; }
+    int ndev = 0;
+    if (cudaGetDeviceCount(&ndev) != cudaSuccess || ndev == 0) { tn_set_error("no CUDA device"); return TN_EDEVICE; }
+    auto *p = new (std::nothrow) tn_plan_s;
+    if (!p) return TN_ENOMEM;
+    p->circ = *c;
+    p->opts = o;
+    p->mem.alloc = o.alloc;
+    p->mem.free = o.free;
+    p->mem.ctx = o.alloc_ctx;
+    p->mem.stream = static_cast<cudaStream_t>(o.stream);
+    p->budget = o.hbm_budget_bytes > 0 ? o.hbm_budget_bytes : 64.0 * (1ull << 30);
+    tn_merge(p->circ, p->mg);
+    p->open.assign(open_qubits, open_qubits + n_open);
+    p->log2T = o.log2_batches;
+    auto fail = [&](int rc) {
+        free_cnet(p->mem, p->amp);
+        delete p;
+        return rc;
+    };
+    int rc = tn_plan_build_host(p->mg, o, order, n_order, sliced, n_sliced, p->open, p->I, p->amp.net,
+                                p->amp.tree, p->amp.steps, p->closed);
+    if (rc) return fail(rc);
+    if (p->closed.empty()) p->log2T = 0;
+    p->amp.elem = 8;
+    rc = setup_leaves(p->mem, p->amp);
+    if (rc) return fail(rc);
+    *out = p;
+    return TN_OK;
+}
+
+void tn_plan_destroy(tn_plan_h p) {
+    if (!p) return;
+    free_cnet(p->mem, p->amp);
+    for (DBuf *b : {&p->d_closed, &p->d_amps, &p->d_j, &p->d_acc, &p->d_pick, &p->d_eps, &p->d_bits, &p->d_R, &p->d_X})
+        release(p->mem, *b);
+    cudaStreamSynchronize(p->mem.stream);
+    delete p;
+}
+
+static void fill_info(const Merged &mg, const std::vector<int> &open, const std::vector<int> &closed, int log2T,
+                      const std::vector<tn_edge> &I, const Network &net, const Tree &tree,
+                      const std::vector<Step> &steps, tn_plan_info *info) {
+    std::memset(info, 0, sizeof(*info));
+    info->n_qubits = mg.n;
+    info->n_open = (int)open.size();
+    info->n_closed = (int)closed.size();
+    info->log2_batches = closed.empty() ? 0 : log2T;
+    info->n_leaves = (int)net.leaves.size();
+    info->n_steps = (int)steps.size();
+    info->n_sliced = (int)I.size();
+    int mx = 0;
+    double fl1 = 0;
+    for (auto &nd : tree.nodes) mx = std::max(mx, nd.idx.count());
+    for (auto &s : steps) fl1 += s.flops_per_version;
+    info->log2_max_tensor = mx;
+    info->flops_per_slice = fl1;
+    info->flops_all_slices = tn_tree_cost(net, tree).flops;
+}
+
+int tn_plan_host(tn_circuit_h c, const int32_t *order, int32_t n_order, const tn_edge *sliced, int32_t n_sliced,
+                 const int32_t *open_qubits, int32_t n_open, const tn_plan_opts *opts, tn_plan_info *info,
+                 int32_t *steps_out, int32_t cap_steps, tn_edge *sliced_out, int32_t cap_sliced) {
+    if (!c || !info || (n_open > 0 && !open_qubits) || n_open < 0 || n_open > 16) {
+        tn_set_error("tn_plan_host: bad arguments");
+        return TN_EINVAL;
+    }
+    tn_plan_opts o;
+    if (opts) o = *opts;
+    else tn_plan_opts_default(&o);
+    Merged mg;
+    tn_merge(*c, mg);
+    std::vector<int> open(open_qubits, open_qubits + n_open), closed;
+    std::vector<tn_edge> I;
+    Network net;
+    Tree tree;
+    std::vector<Step> steps;
+    RC(tn_plan_build_host(mg, o, order, n_order, sliced, n_sliced, open, I, net, tree, steps, closed));
+    fill_info(mg, open, closed, o.log2_batches, I, net, tree, steps, info);
+    if (steps_out)
+        for (int i = 0; i < (int)steps.size() && i < cap_steps; i++) {
+            const Step &s = steps[i];
+            int32_t *r = steps_out + 5 * i;
+            r[0] = s.nbat; r[1] = s.nm; r[2] = s.nn; r[3] = s.nk;
+            r[4] = __builtin_popcountll(tree.nodes[s.c].dep);
+        }
+    if (sliced_out)
+        for (int i = 0; i < (int)I.size() && i < cap_sliced; i++) sliced_out[i] = I[i];
+    return TN_OK;
+}
+
+int tn_sliced_vertex_select(tn_circuit_h c, const tn_edge *I, int32_t n_I, int32_t k, int32_t *s_index,
+                            int32_t *k_out) {
+    if (!c || (n_I > 0 && !I) || !k_out || k < 0) { tn_set_error("tn_sliced_vertex_select: bad arguments"); return TN_EINVAL; }
+    Merged mg;
+    tn_merge(*c, mg);
+    std::vector<tn_edge> Iv(I, I + n_I);
+    for (auto &e : Iv)
+        if (e.qubit < 0 || e.qubit >= mg.n || e.segment < 0 || e.segment > mg.n2q[e.qubit]) {
+            tn_set_error("tn_sliced_vertex_select: vertex out of range");
+            return TN_EINVAL;
+        }
+    std::vector<int> S = tn_sliced_vertex_select(mg, Iv, k);
+    *k_out = (int32_t)S.size();
+    if (s_index)
+        for (size_t t = 0; t < S.size(); t++) s_index[t] = S[t];
+    return TN_OK;
+}
+
+int tn_plan_get_info(tn_plan_h p, tn_plan_info *info) {
+    if (!p || !info) { tn_set_error("null argument"); return TN_EINVAL; }
+    fill_info(p->mg, p->open, p->closed, p->log2T, p->I, p->amp.net, p->amp.tree, p->amp.steps, info);
+    return TN_OK;
+}
+
+int tn_plan_sliced_edges(tn_plan_h p, tn_edge *out, int32_t cap, int32_t *n_out) {
+    if (!p || !n_out) { tn_set_error("null argument"); return TN_EINVAL; }
+    *n_out = (int32_t)p->I.size();
+    if (out)
+        for (int i = 0; i < (int)p->I.size() && i < cap; i++) out[i] = p->I[i];
+    return TN_OK;
+}
+
+int tn_contract(tn_plan_h p, const uint64_t *slices, int64_t n_slices, const uint64_t *closed_bits, int64_t n_batches,
+                double *amps, int32_t flags) {
+    if (!p || !slices || n_slices <= 0 || !amps || n_batches <= 0 || (!closed_bits && !p->closed.empty())) {
+        tn_set_error("tn_contract: bad arguments");
+        return TN_EINVAL;
+    }
+    const int nI = (int)p->I.size();
+    std::vector<uint64_t> sl(slices, slices + n_slices);
+    {
+        std::vector<uint64_t> sorted = sl;
+        std::sort(sorted.begin(), sorted.end());
+        if (std::adjacent_find(sorted.begin(), sorted.end()) != sorted.end()) { tn_set_error("duplicate slice"); return TN_EINVAL; }
+        if (nI < 64 && sorted.back() >> nI) { tn_set_error("slice sets bits beyond the sliced edges"); return TN_EINVAL; }
+    }
+    cudaStream_t st = p->mem.stream;
+    RC(prepare_call(p->mem, p->amp, sl, p->budget));
+    const long long T = 1LL << p->log2T;
+    const int nopen = (int)p->open.size();
+    const long long NA = 1LL << nopen;
+    RC(ensure(p->mem, p->d_closed, T * sizeof(uint64_t)));
+    RC(ensure(p->mem, p->d_amps, T * NA * sizeof(double2)));
+    const bool dev = flags & TN_DEVICE_BUFFERS;
+    for (long long g0 = 0; g0 < n_batches; g0 += T) {
+        long long nb = std::min<long long>(T, n_batches - g0);
+        CK(cudaMemsetAsync(p->d_closed.p, 0, T * sizeof(uint64_t), st));
+        if (!p->closed.empty())
+            CK(cudaMemcpyAsync(p->d_closed.p, closed_bits + g0, nb * sizeof(uint64_t),
+                               dev ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, st));
+        RC(execute(p->amp, static_cast<const uint64_t *>(p->d_closed.p), g0 > 0, static_cast<double2 *>(p->d_amps.p), st));
+        CK(cudaMemcpyAsync(amps + 2 * g0 * NA, p->d_amps.p, nb * NA * sizeof(double2),
+                           dev ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, st));
+    }
+    CK(cudaStreamSynchronize(st));
+    return TN_OK;
+}
+
+int tn_partial_norms(tn_plan_h p, double f, int32_t *s_index, int32_t *k_out, double *R, int64_t cap_R) {
+    if (!p || !(f > 0.0 && f <= 1.0) || !k_out) { tn_set_error("tn_partial_norms: bad arguments"); return TN_EINVAL; }
+    const int k0 = (int)std::ceil(3.0 - std::log2(f));
+    std::vector<int> spos = tn_sliced_vertex_select(p->mg, p->I, k0);
+    const int k = (int)spos.size();
+    *k_out = k;
+    if (s_index)
+        for (int t = 0; t < k; t++) s_index[t] = spos[t];
+    if (R && cap_R < (int64_t(1) << k)) { tn_set_error("R capacity below 2^k"); return TN_EINVAL; }
+    if (k > 20) { tn_set_error("k above 20"); return TN_EUNSUPPORTED; }
+    std::vector<double> Rh(size_t(1) << k, 0.0);
+    if (k == 0) Rh[0] = 1.0;
+    else {
+        std::vector<tn_edge> S;
+        for (int e : spos) S.push_back(p->I[e]);
+        CNet cn;
+        int rc = tn_build_norm_network(p->mg, S, cn.net);
+        if (rc) return rc;
+        rc = build_cnet(p->mg, cn, p->opts, nullptr, 0, p->mem, 16);
+        if (rc) { free_cnet(p->mem, cn); return rc; }
+        rc = prepare_call(p->mem, cn, {0ull}, p->budget);
+        if (rc) { free_cnet(p->mem, cn); return rc; }
+        DBuf out;
+        rc = ensure(p->mem, out, (size_t(1) << k) * sizeof(double2));
+        if (!rc) rc = execute(cn, nullptr, false, static_cast<double2 *>(out.p), p->mem.stream);
+        std::vector<double2> tmp(size_t(1) << k);
+        if (!rc && cudaMemcpyAsync(tmp.data(), out.p, tmp.size() * sizeof(double2), cudaMemcpyDeviceToHost,
+                                   p->mem.stream) != cudaSuccess) rc = TN_EDEVICE;
+        if (!rc && cudaStreamSynchronize(p->mem.stream) != cudaSuccess) rc = TN_EDEVICE;
+        release(p->mem, out);
+        free_cnet(p->mem, cn);
+        cudaStreamSynchronize(p->mem.stream);
+        if (rc) { if (rc == TN_EDEVICE) tn_set_error("norm network execution failed"); return rc; }
+        for (size_t i = 0; i < tmp.size(); i++) Rh[i] = tmp[i].x;
+    }
+    if (R) std::copy(Rh.begin(), Rh.end(), R);
+    p->norm_f = f;
+    p->norm_S = spos;
+    p->norm_R = Rh;
+    return TN_OK;
+}
+
+int tn_slice_cut(const double *R, int32_t k, double f, void *stream, int32_t *X, int32_t *n_x, double *F) {
+    if (!R || !X || !n_x || !F || k < 0 || k > 12) { tn_set_error("tn_slice_cut: bad arguments (k <= 12)"); return TN_EINVAL; }
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    const int n = 1 << k;
+    void *dR = nullptr, *dX = nullptr, *dn = nullptr, *dF = nullptr;
+    CK(cudaMallocAsync(&dR, n * sizeof(double), st));
+    CK(cudaMallocAsync(&dX, n * sizeof(int32_t), st));
+    CK(cudaMallocAsync(&dn, sizeof(int32_t), st));
+    CK(cudaMallocAsync(&dF, sizeof(double), st));
+    CK(cudaMemcpyAsync(dR, R, n * sizeof(double), cudaMemcpyHostToDevice, st));
+    size_t smem = (size_t)n * (sizeof(double) + sizeof(int));
+    tnk::slice_cut<<<1, 256, smem, st>>>((const double *)dR, k, f, (int32_t *)dX, (int32_t *)dn, (double *)dF);
+    CK(cudaGetLastError());
+    CK(cudaMemcpyAsync(n_x, dn, sizeof(int32_t), cudaMemcpyDeviceToHost, st));
+    CK(cudaMemcpyAsync(F, dF, sizeof(double), cudaMemcpyDeviceToHost, st));
+    CK(cudaStreamSynchronize(st));
+    CK(cudaMemcpyAsync(X, dX, (size_t)(*n_x) * sizeof(int32_t), cudaMemcpyDeviceToHost, st));
+    CK(cudaFreeAsync(dR, st));
+    CK(cudaFreeAsync(dX, st));
+    CK(cudaFreeAsync(dn, st));
+    CK(cudaFreeAsync(dF, st));
+    CK(cudaStreamSynchronize(st));
+    return TN_OK;
+}
+
+int tn_select(tn_plan_h p, double f, uint64_t *slices, int64_t cap, int64_t *n_slices, double *F) {
+    if (!p || !n_slices || !F || !(f > 0.0)) { tn_set_error("tn_select: bad arguments"); return TN_EINVAL; }
+    const int nI = (int)p->I.size();
+    if (nI > 40) { tn_set_error("tn_select: more than 40 sliced edges"); return TN_EUNSUPPORTED; }
+    std::vector<uint64_t> out;
+    if (f >= 1.0) {
+        *F = 1.0;
+        for (uint64_t s = 0; s < (1ull << nI); s++) out.push_back(s);
+    } else {
+        int32_t k = 0;
+        std::vector<int32_t> spos(64);
+        std::vector<double> R;
+        if (p->norm_f == f) { spos = p->norm_S; k = (int)spos.size(); R = p->norm_R; }
+        else {
+            int k0 = (int)std::ceil(3.0 - std::log2(f));
+            R.resize(size_t(1) << std::min(k0, 20));
+            RC(tn_partial_norms(p, f, spos.data(), &k, R.data(), (int64_t)R.size()));
+            R.resize(size_t(1) << k);
+            spos.resize(k);
+        }
+        std::vector<int32_t> X(size_t(1) << k);
+        int32_t nx = 0;
+        RC(tn_slice_cut(R.data(), k, f, p->mem.stream, X.data(), &nx, F));
+        // X x {0,1}^{|I|-k}: free bits are the sliced edges outside S
+        std::vector<int> freeb;
+        for (int e = 0; e < nI; e++)
+            if (std::find(spos.begin(), spos.end(), e) == spos.end()) freeb.push_back(e);
+        for (int a = 0; a < nx; a++) {
+            uint64_t base = 0;
+            for (int t = 0; t < k; t++) base |= (uint64_t)((X[a] >> t) & 1) << spos[t];
+            for (uint64_t r = 0; r < (1ull << freeb.size()); r++) {
+                uint64_t s = base;
+                for (size_t u = 0; u < freeb.size(); u++) s |= ((r >> u) & 1ull) << freeb[u];
+                out.push_back(s);
+            }
+        }
+    }
+    *n_slices = (int64_t)out.size();
+    if (slices) {
+        if (cap < (int64_t)out.size()) { tn_set_error("tn_select: capacity below the slice-set size"); return TN_EINVAL; }
+        std::copy(out.begin(), out.end(), slices);
+    }
+    return TN_OK;
+}
+
+int tn_draw_batches(uint64_t seed, uint64_t t0, int64_t T, int32_t b_bits, uint64_t *j, void *stream) {
+    if (!j || T < 0 || b_bits < 0 || b_bits > 64) { tn_set_error("tn_draw_batches: bad arguments"); return TN_EINVAL; }
+    if (T == 0) return TN_OK;
+    tnk::draw_batches<<<(unsigned)((T + 255) / 256), 256, 0, static_cast<cudaStream_t>(stream)>>>(seed, t0, T, b_bits, j);
+    CK(cudaGetLastError());
+    CK(cudaStreamSynchronize(static_cast<cudaStream_t>(stream)));
+    return TN_OK;
+}
+
+int tn_rejection_sample(const double *p, int64_t T, int32_t b_bits, double alpha, uint64_t seed, uint64_t t0,
+                        uint8_t *accept, int32_t *pick, void *stream) {
+    if (!p || !accept || !pick || T < 0 || b_bits < 0 || b_bits > 58 || !(alpha > 0)) {
+        tn_set_error("tn_rejection_sample: bad arguments");
+        return TN_EINVAL;
+    }
+    if (T == 0) return TN_OK;
+    tnk::SampleParams sp;
+    std::memset(&sp, 0, sizeof(sp));
+    sp.p = p;
+    sp.T = T;
+    sp.b_bits = b_bits;
+    sp.alpha = alpha;
+    sp.seed = seed;
+    sp.t0 = t0;
+    sp.accept = accept;
+    sp.pick = pick;
+    tnk::sampler<<<(unsigned)((T * 32 + 255) / 256), 256, 0, static_cast<cudaStream_t>(stream)>>>(sp);
+    CK(cudaGetLastError());
+    CK(cudaStreamSynchronize(static_cast<cudaStream_t>(stream)));
+    return TN_OK;
+}
+
+int tn_trace_enable(tn_plan_h p, int32_t on) {
+    if (!p) { tn_set_error("null plan"); return TN_EINVAL; }
+    CNet &cn = p->amp;
+    const size_t ns = cn.steps.size();
+    if (on && cn.ev.empty()) {
+        cn.ev.resize(2 * ns);
+        for (auto &x : cn.ev) CK(cudaEventCreate(&x));
+    }
+    cn.ev_pending.assign(ns, 0);
+    cn.tr_launches.assign(ns, 0);
+    cn.tr_ms.assign(ns, 0.0);
+    cn.tr_kernel.assign(ns, -1);
+    cn.trace = on != 0;
+    return TN_OK;
+}
+
+int tn_trace_read(tn_plan_h p, tn_step_trace *out, int32_t cap, int32_t *n_out) {
+    if (!p || !n_out) { tn_set_error("null argument"); return TN_EINVAL; }
+    CNet &cn = p->amp;
+    const int ns = (int)cn.steps.size();
+    *n_out = ns;
+    if (!cn.trace) return TN_OK;
+    CK(cudaStreamSynchronize(p->mem.stream));
+    for (int si = 0; si < ns; si++)
+        if (cn.ev_pending[si]) {
+            float ms = 0;
+            CK(cudaEventElapsedTime(&ms, cn.ev[2 * si], cn.ev[2 * si + 1]));
+            cn.tr_ms[si] += ms;
+            cn.tr_launches[si]++;
+            cn.ev_pending[si] = 0;
+        }
+    const auto &nodes = cn.tree.nodes;
+    for (int si = 0; si < ns && si < cap && out; si++) {
+        const Step &s = cn.steps[si];
+        tn_step_trace &t = out[si];
+        std::memset(&t, 0, sizeof(t));
+        t.step = si;
+        t.launches = cn.tr_launches[si];
+        t.ms = cn.tr_ms[si];
+        long long nv = cn.cp.valid ? cn.cp.nver[s.c] : 1;
+        t.nver = nv;
+        t.flops_per_launch = s.flops_per_version * (double)nv;
+        auto vbytes = [&](int x) {
+            long long v = cn.cp.valid ? cn.cp.nver[x] : 1;
+            int bits = nodes[x].ch[0] < 0 ? (int)nodes[x].layout.size() : nodes[x].idx.count();
+            return 8.0 * std::ldexp(1.0, bits) * (double)v;
+        };
+        t.bytes_per_launch = vbytes(s.a) + vbytes(s.b) + vbytes(s.c);
+        t.nbat = s.nbat;
+        t.nm = s.nm;
+        t.nn = s.nn;
+        t.nk = s.nk;
+        t.kernel = cn.tr_kernel[si];
+    }
+    return TN_OK;
+}
+
+int tn_sample_step(tn_plan_h p, const uint64_t *slices, int64_t n_slices, double F, uint64_t seed, uint64_t t0,
+                   double alpha, int32_t reuse_stem, uint8_t *accept, uint64_t *bits, int32_t flags) {
+    if (!p || !slices || n_slices <= 0 || !accept || !bits || !(alpha > 1.0) || !(F > 0.0)) {
+        tn_set_error("tn_sample_step: bad arguments");
+        return TN_EINVAL;
+    }
+    if (p->open.size() != 6) { tn_set_error("tn_sample_step: needs 6 open qubits"); return TN_EUNSUPPORTED; }
+    std::vector<uint64_t> sl(slices, slices + n_slices);
+    RC(prepare_call(p->mem, p->amp, sl, p->budget));
+    cudaStream_t st = p->mem.stream;
+    const long long T = 1LL << p->log2T;
+    const int b_bits = (int)p->closed.size();
+    RC(ensure(p->mem, p->d_j, T * sizeof(uint64_t)));
+    RC(ensure(p->mem, p->d_amps, T * 64 * sizeof(double2)));
+    RC(ensure(p->mem, p->d_pick, T * sizeof(int32_t)));
+    const bool dev = flags & TN_DEVICE_BUFFERS;
+    if (!dev) {
+        RC(ensure(p->mem, p->d_acc, T));
+        RC(ensure(p->mem, p->d_bits, T * sizeof(uint64_t)));
+    }
+    tnk::draw_batches<<<(unsigned)((T + 255) / 256), 256, 0, st>>>(seed, t0, T, b_bits, static_cast<uint64_t *>(p->d_j.p));
+    CK(cudaGetLastError());
+    RC(execute(p->amp, static_cast<const uint64_t *>(p->d_j.p), reuse_stem != 0, static_cast<double2 *>(p->d_amps.p), st));
+    tnk::SampleParams sp;
+    std::memset(&sp, 0, sizeof(sp));
+    sp.amps = static_cast<const double2 *>(p->d_amps.p);
+    sp.invF_num = F;
+    sp.T = T;
+    sp.b_bits = b_bits;
+    sp.alpha = alpha;
+    sp.seed = seed;
+    sp.t0 = t0;
+    sp.accept = dev ? accept : static_cast<uint8_t *>(p->d_acc.p);
+    sp.pick = static_cast<int32_t *>(p->d_pick.p);
+    sp.j = static_cast<const uint64_t *>(p->d_j.p);
+    sp.bits = dev ? bits : static_cast<uint64_t *>(p->d_bits.p);
+    sp.n_open = 6;
+    sp.n_closed = b_bits;
+    for (int r = 0; r < 6; r++) sp.open_q[r] = (int8_t)p->open[r];
+    for (int c = 0; c < b_bits; c++) sp.closed_q[c] = (int8_t)p->closed[c];
+    tnk::sampler<<<(unsigned)((T * 32 + 255) / 256), 256, 0, st>>>(sp);
+    CK(cudaGetLastError());
+    if (!dev) {
+        CK(cudaMemcpyAsync(accept, p->d_acc.p, T, cudaMemcpyDeviceToHost, st));
+        CK(cudaMemcpyAsync(bits, p->d_bits.p, T * sizeof(uint64_t), cudaMemcpyDeviceToHost, st));
+        CK(cudaStreamSynchronize(st));
+    }
+    return TN_OK;
+}
+
+int tn_sample(tn_plan_h p, double f_target, int64_t N, uint64_t seed, double alpha, uint64_t *bitstrings,
+              int32_t flags, tn_sample_stats *stats) {
+    if (!p || N < 0 || !bitstrings || !(alpha > 1.0) || !(f_target > 0.0)) {
+        tn_set_error("tn_sample: bad arguments (alpha > 1, f_target > 0)");
+        return TN_EINVAL;
+    }
+    if (p->open.size() != 6) { tn_set_error("tn_sample: needs 6 open qubits (batches of 64)"); return TN_EUNSUPPORTED; }
+    tn_sample_stats st_local;
+    std::memset(&st_local, 0, sizeof(st_local));
+    int64_t nsl = 0;
+    double F = 1.0;
+    RC(tn_select(p, f_target, nullptr, 0, &nsl, &F));
+    std::vector<uint64_t> sl((size_t)nsl);
+    RC(tn_select(p, f_target, sl.data(), nsl, &nsl, &F));
+    st_local.F = F;
+    st_local.n_slices = nsl;
+    cudaStream_t st = p->mem.stream;
+    RC(prepare_call(p->mem, p->amp, sl, p->budget));
+    const long long T = 1LL << p->log2T;
+    const int b_bits = (int)p->closed.size();
+    RC(ensure(p->mem, p->d_j, T * sizeof(uint64_t)));
+    RC(ensure(p->mem, p->d_amps, T * 64 * sizeof(double2)));
+    RC(ensure(p->mem, p->d_acc, T));
+    RC(ensure(p->mem, p->d_pick, T * sizeof(int32_t)));
+    RC(ensure(p->mem, p->d_eps, T * sizeof(double)));
+    RC(ensure(p->mem, p->d_bits, T * sizeof(uint64_t)));
+    std::vector<uint8_t> h_acc(T);
+    std::vector<uint64_t> h_bits(T);
+    std::vector<double> h_eps(T);
+    std::vector<uint64_t> result;
+    result.reserve((size_t)N);
+    const int64_t max_steps = (int64_t)std::ceil(8.0 * alpha * (double)N) + 4096;
+    int64_t t = 0;
+    double eps_sum = 0;
+    int group = 0;
+    tnk::SampleParams sp;
+    std::memset(&sp, 0, sizeof(sp));
+    sp.amps = static_cast<const double2 *>(p->d_amps.p);
+    sp.invF_num = F;
+    sp.T = T;
+    sp.b_bits = b_bits;
+    sp.alpha = alpha;
+    sp.seed = seed;
+    sp.accept = static_cast<uint8_t *>(p->d_acc.p);
+    sp.pick = static_cast<int32_t *>(p->d_pick.p);
+    sp.eps = static_cast<double *>(p->d_eps.p);
+    sp.j = static_cast<const uint64_t *>(p->d_j.p);
+    sp.bits = static_cast<uint64_t *>(p->d_bits.p);
+    sp.n_open = 6;
+    sp.n_closed = b_bits;
+    for (int r = 0; r < 6; r++) sp.open_q[r] = (int8_t)p->open[r];
+    for (int c = 0; c < b_bits; c++) sp.closed_q[c] = (int8_t)p->closed[c];
+    while ((int64_t)result.size() < N && t < max_steps) {
+        tnk::draw_batches<<<(unsigned)((T + 255) / 256), 256, 0, st>>>(seed, (uint64_t)t, T, b_bits,
+                                                                         static_cast<uint64_t *>(p->d_j.p));
+        CK(cudaGetLastError());
+        RC(execute(p->amp, static_cast<const uint64_t *>(p->d_j.p), group > 0, static_cast<double2 *>(p->d_amps.p), st));
+        sp.t0 = (uint64_t)t;
+        tnk::sampler<<<(unsigned)((T * 32 + 255) / 256), 256, 0, st>>>(sp);
+        CK(cudaGetLastError());
+        CK(cudaMemcpyAsync(h_acc.data(), p->d_acc.p, T, cudaMemcpyDeviceToHost, st));
+        CK(cudaMemcpyAsync(h_bits.data(), p->d_bits.p, T * sizeof(uint64_t), cudaMemcpyDeviceToHost, st));
+        CK(cudaMemcpyAsync(h_eps.data(), p->d_eps.p, T * sizeof(double), cudaMemcpyDeviceToHost, st));
+        CK(cudaStreamSynchronize(st));
+        const long long take = std::min<long long>(T, max_steps - t);
+        for (long long i = 0; i < take; i++) {
+            eps_sum += h_eps[i];
+            if (h_acc[i]) {
+                st_local.accepted++;
+                if ((int64_t)result.size() < N) result.push_back(h_bits[i]);
+            }
+        }
+        st_local.flops += group == 0 ? p->amp.cp.flops_all : p->amp.cp.flops_beta;
+        t += take;
+        group++;
+    }
+    st_local.steps = t;
+    st_local.eps_hat = t > 0 ? eps_sum / (double)t : 0.0;
+    if (flags & TN_DEVICE_BUFFERS) {
+        CK(cudaMemcpyAsync(bitstrings, result.data(), result.size() * sizeof(uint64_t), cudaMemcpyHostToDevice, st));
+        CK(cudaStreamSynchronize(st));
+    } else {
+        std::copy(result.begin(), result.end(), bitstrings);
+    }
+    if (stats) *stats = st_local;
+    if ((int64_t)result.size() < N) {
+        tn_set_error("tn_sample: step limit reached before N accepted samples");
+        return TN_EINVAL;
+    }
+    return TN_OK;
+}
+
+}  // extern "C"

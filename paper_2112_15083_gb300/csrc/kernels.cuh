@@ -1,0 +1,372 @@
+// Device kernels of libtn (sm_103a).
+//
+//  * cgemm_row / cgemm_tile: one pairwise contraction step (Sec. I, contraction tree;
+//    the per-slice work of Sec. I.C) as a batched complex GEMM
+//        C[v][bat][m][n] = sum_k A[v][bat][m][k] * B[v][bat][n][k]
+//    over versions v (slice assignments of the sliced legs the operands depend on),
+//    with the permutation of the result fused into the epilogue: element (bat, m, n)
+//    goes to bit-scattered address pos_bat(bat) + pos_m(m) + pos_n(n).
+//  * materialize: writes leaf tensors in the layout their consumer reads, fixing the
+//    sliced legs (one copy per slice value) and binding closed output legs to the
+//    batch pattern (the batch-indexed selector <b_B|).
+//  * slice_sum: FP64 sum over the slice set in slice order (Sec. I.C step 1).
+//  * draw / sampler: Philox4x32-10 draws and the modified frugal rejection step
+//    (Sec. II.A), one warp per batch of 64.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace tnk {
+
+constexpr int kMaxBits = 40;
+
+struct GemmParams {
+    const void *const *ptrA;  // per C-version operand base
+    const void *const *ptrB;
+    void *C;                  // C base (version v at C + v * c_vstride)
+    long long c_vstride;      // elements
+    long long nver;
+    int lm, ln, lk, lbat;     // log2 of M, N, K, BAT
+    int8_t pos_bat[kMaxBits], pos_m[kMaxBits], pos_n[kMaxBits];
+};
+
+__device__ __forceinline__ long long scatter_bits(long long x, const int8_t *pos, int nbits) {
+    long long off = 0;
+#pragma unroll 4
+    for (int i = 0; i < nbits; i++) off |= ((x >> i) & 1LL) << pos[i];
+    return off;
+}
+
+__device__ __forceinline__ float2 cfma(float2 a, float2 b, float2 c) {
+    c.x = fmaf(a.x, b.x, c.x);
+    c.x = fmaf(-a.y, b.y, c.x);
+    c.y = fmaf(a.x, b.y, c.y);
+    c.y = fmaf(a.y, b.x, c.y);
+    return c;
+}
+__device__ __forceinline__ double2 cfma(double2 a, double2 b, double2 c) {
+    c.x = fma(a.x, b.x, c.x);
+    c.x = fma(-a.y, b.y, c.x);
+    c.y = fma(a.x, b.y, c.y);
+    c.y = fma(a.y, b.x, c.y);
+    return c;
+}
+template <typename T> __device__ __forceinline__ T czero();
+template <> __device__ __forceinline__ float2 czero<float2>() { return make_float2(0.f, 0.f); }
+template <> __device__ __forceinline__ double2 czero<double2>() { return make_double2(0.0, 0.0); }
+
+// One thread per output row (v, bat, m); all N (<= 16) columns in registers.  For the
+// gate-absorption steps (small N and K), which are bound by HBM bandwidth.
+template <typename T, int N>
+__global__ void __launch_bounds__(256) cgemm_row(GemmParams p) {
+    const long long rows = p.nver << (p.lbat + p.lm);
+    const long long row = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (row >= rows) return;
+    const long long M = 1LL << p.lm;
+    const long long m = row & (M - 1);
+    const long long bat = (row >> p.lm) & ((1LL << p.lbat) - 1);
+    const long long v = row >> (p.lm + p.lbat);
+    const int K = 1 << p.lk;
+    const T *A = static_cast<const T *>(p.ptrA[v]) + (((bat << p.lm) | m) << p.lk);
+    const T *B = static_cast<const T *>(p.ptrB[v]) + (bat << (p.ln + p.lk));
+    T acc[N];
+#pragma unroll
+    for (int n = 0; n < N; n++) acc[n] = czero<T>();
+    for (int k = 0; k < K; k++) {
+        T a = A[k];
+#pragma unroll
+        for (int n = 0; n < N; n++) acc[n] = cfma(a, __ldg(&B[(n << p.lk) + k]), acc[n]);
+    }
+    T *C = static_cast<T *>(p.C) + v * p.c_vstride + scatter_bits(bat, p.pos_bat, p.lbat) +
+           scatter_bits(m, p.pos_m, p.lm);
+#pragma unroll
+    for (int n = 0; n < N; n++) C[scatter_bits(n, p.pos_n, p.ln)] = acc[n];
+}
+
+// Shared-memory tiled kernel: TM x TN output tile, K in chunks of TK, each thread an
+// RM x RN register tile (rows contiguous, columns strided by TN/RN for coalescing).
+template <typename T, int TM, int TN, int TK, int RM, int RN>
+__global__ void __launch_bounds__((TM / RM) * (TN / RN)) cgemm_tile(GemmParams p) {
+    constexpr int NTX = TN / RN, NTY = TM / RM, NT = NTX * NTY;
+    __shared__ T As[TK][TM + 1];
+    __shared__ T Bs[TK][TN + 1];
+    const int tid = threadIdx.x;
+    const int tx = tid % NTX, ty = tid / NTX;
+    const long long M = 1LL << p.lm, N = 1LL << p.ln;
+    const int K = 1 << p.lk;
+    const int ltm = p.lm > 0 ? min(p.lm, __ffs(TM) - 1) : 0;
+    const int ltn = p.ln > 0 ? min(p.ln, __ffs(TN) - 1) : 0;
+    const int ltiles_m = p.lm - ltm, ltiles_n = p.ln - ltn;
+    long long bid = blockIdx.x;
+    const long long tn_i = bid & ((1LL << ltiles_n) - 1);
+    bid >>= ltiles_n;
+    const long long tm_i = bid & ((1LL << ltiles_m) - 1);
+    bid >>= ltiles_m;
+    const long long bat = bid & ((1LL << p.lbat) - 1);
+    const long long v = bid >> p.lbat;
+    if (v >= p.nver) return;
+    const long long m0 = tm_i * TM, n0 = tn_i * TN;
+    const int mrows = (int)min((long long)TM, M - m0), ncols = (int)min((long long)TN, N - n0);
+    const T *A = static_cast<const T *>(p.ptrA[v]) + (((bat << p.lm) | m0) << p.lk);
+    const T *B = static_cast<const T *>(p.ptrB[v]) + (((bat << p.ln) | n0) << p.lk);
+    T acc[RM][RN];
+#pragma unroll
+    for (int i = 0; i < RM; i++)
+#pragma unroll
+        for (int j = 0; j < RN; j++) acc[i][j] = czero<T>();
+    const int kt = min(TK, K);
+    const int lkt = __ffs(kt) - 1;
+    for (int k0 = 0; k0 < K; k0 += kt) {
+        for (int e = tid; e < (TM << lkt); e += NT) {
+            int r = e >> lkt, c = e & (kt - 1);
+            As[c][r] = r < mrows ? A[((long long)r << p.lk) + k0 + c] : czero<T>();
+        }
+        for (int e = tid; e < (TN << lkt); e += NT) {
+            int r = e >> lkt, c = e & (kt - 1);
+            Bs[c][r] = r < ncols ? B[((long long)r << p.lk) + k0 + c] : czero<T>();
+        }
+        __syncthreads();
+        for (int kk = 0; kk < kt; kk++) {
+            T a[RM], b[RN];
+#pragma unroll
+            for (int i = 0; i < RM; i++) a[i] = As[kk][ty * RM + i];
+#pragma unroll
+            for (int j = 0; j < RN; j++) b[j] = Bs[kk][tx + j * NTX];
+#pragma unroll
+            for (int i = 0; i < RM; i++)
+#pragma unroll
+                for (int j = 0; j < RN; j++) acc[i][j] = cfma(a[i], b[j], acc[i][j]);
+        }
+        __syncthreads();
+    }
+    T *C = static_cast<T *>(p.C) + v * p.c_vstride + scatter_bits(bat, p.pos_bat, p.lbat);
+    long long offn[RN];
+#pragma unroll
+    for (int j = 0; j < RN; j++) offn[j] = scatter_bits(n0 + tx + j * NTX, p.pos_n, p.ln);
+#pragma unroll
+    for (int i = 0; i < RM; i++) {
+        const int r = ty * RM + i;
+        if (r >= mrows) continue;
+        const long long offm = scatter_bits(m0 + r, p.pos_m, p.lm);
+#pragma unroll
+        for (int j = 0; j < RN; j++)
+            if (tx + j * NTX < ncols) C[offm + offn[j]] = acc[i][j];
+    }
+}
+
+// ---------------------------------------------------------------- leaves
+
+struct MatDesc {
+    const double2 *src;  // full leaf tensor, data index = sum_t value(leg t) << t
+    void *dst;           // [code][2^nd] in the consumer's layout
+    int nd;              // destination bits
+    int ncode_bits;      // sliced legs of the leaf
+    int ncl;             // closed legs
+    int8_t dst_leg[kMaxBits];  // >= 0: source leg position; < 0: beta bit (-1 - t)
+    int8_t sl_leg[8];          // code bit u -> source leg position
+    int8_t cl_leg[8];          // closed leg -> source leg position
+    int16_t cl_ref[8];         // closed leg -> closed-qubit position c
+};
+
+// grid.y = leaf; threads over (code, element).  closed_bits[beta] gives the batch
+// pattern (bit c = closed qubit c); may be null when no leaf has closed legs.
+template <typename T>
+__global__ void materialize(const MatDesc *descs, const uint64_t *closed_bits) {
+    const MatDesc d = descs[blockIdx.y];
+    const long long total = 1LL << (d.nd + d.ncode_bits);
+    for (long long g = (long long)blockIdx.x * blockDim.x + threadIdx.x; g < total;
+         g += (long long)gridDim.x * blockDim.x) {
+        const long long code = g >> d.nd, e = g & ((1LL << d.nd) - 1);
+        long long src = 0, beta = 0;
+        for (int t = 0; t < d.nd; t++) {
+            const long long bit = (e >> t) & 1;
+            const int L = d.dst_leg[t];
+            if (L >= 0) src |= bit << L;
+            else beta |= bit << (-1 - L);
+        }
+        for (int u = 0; u < d.ncode_bits; u++) src |= ((code >> u) & 1) << d.sl_leg[u];
+        if (d.ncl) {
+            const uint64_t pat = closed_bits[beta];
+            for (int c = 0; c < d.ncl; c++) src |= (long long)((pat >> d.cl_ref[c]) & 1) << d.cl_leg[c];
+        }
+        const double2 x = d.src[src];
+        T *out = static_cast<T *>(d.dst);
+        if constexpr (sizeof(T) == sizeof(float2)) out[g] = make_float2((float)x.x, (float)x.y);
+        else out[g] = x;
+    }
+}
+
+// ---------------------------------------------------------------- slice sum
+
+// out[e] = sum_{v in order} root_v[e], in FP64.
+template <typename T>
+__global__ void slice_sum(const void *const *ptr, long long nver, long long nelem, double2 *out) {
+    const long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= nelem) return;
+    double re = 0.0, im = 0.0;
+    for (long long v = 0; v < nver; v++) {
+        const T x = static_cast<const T *>(ptr[v])[e];
+        re = __dadd_rn(re, (double)x.x);
+        im = __dadd_rn(im, (double)x.y);
+    }
+    out[e] = make_double2(re, im);
+}
+
+// ---------------------------------------------------------------- Philox
+
+// Philox4x32-10 (Salmon, Moraes, Dror, Shaw, SC'11): 10 rounds of two 32x32->64
+// multiplications with key bumps by the Weyl constants.
+__device__ __forceinline__ uint4 philox4x32_10(uint4 c, uint2 k) {
+#pragma unroll
+    for (int r = 0; r < 10; r++) {
+        if (r > 0) {
+            k.x += 0x9E3779B9u;
+            k.y += 0xBB67AE85u;
+        }
+        const uint32_t lo0 = 0xD2511F53u * c.x, hi0 = __umulhi(0xD2511F53u, c.x);
+        const uint32_t lo1 = 0xCD9E8D57u * c.z, hi1 = __umulhi(0xCD9E8D57u, c.z);
+        c = make_uint4(hi1 ^ c.y ^ k.x, lo1, hi0 ^ c.w ^ k.y, lo0);
+    }
+    return c;
+}
+
+__device__ __forceinline__ double u53(uint32_t lo, uint32_t hi) {
+    const uint64_t w = ((uint64_t)hi << 32) | lo;
+    return __dmul_rn((double)(w >> 11), 1.0 / 9007199254740992.0);
+}
+
+__global__ void draw_batches(uint64_t seed, uint64_t t0, long long T, int b_bits, uint64_t *j) {
+    const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= T) return;
+    const uint64_t tt = t0 + (uint64_t)t;
+    const uint4 o = philox4x32_10(make_uint4((uint32_t)tt, (uint32_t)(tt >> 32), 0u, 0u),
+                                  make_uint2((uint32_t)seed, (uint32_t)(seed >> 32)));
+    const uint64_t w = ((uint64_t)o.y << 32) | o.x;
+    j[t] = b_bits >= 64 ? w : (w & ((1ull << b_bits) - 1));
+}
+
+struct SampleParams {
+    const double *p;      // T*64 probabilities, or null (then amps/F)
+    const double2 *amps;  // T*64 amplitudes
+    double invF_num;      // F (p = |a|^2 / F)
+    long long T;
+    int b_bits;
+    double alpha;
+    uint64_t seed, t0;
+    uint8_t *accept;
+    int32_t *pick;
+    double *eps;          // optional: max(0, p_j - alpha/N_B)
+    const uint64_t *j;    // optional: batch patterns (for bitstrings)
+    uint64_t *bits;       // optional: assembled bitstrings
+    int n_open, n_closed;
+    int8_t open_q[16];
+    int8_t closed_q[64];
+};
+
+// One warp per batch (Sec. II.A steps 2-3); lane l holds p_{2l}, p_{2l+1}.
+__global__ void sampler(SampleParams sp) {
+    const long long warp = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int lane = threadIdx.x & 31;
+    if (warp >= sp.T) return;
+    double p0, p1;
+    if (sp.p) {
+        p0 = sp.p[warp * 64 + 2 * lane];
+        p1 = sp.p[warp * 64 + 2 * lane + 1];
+    } else {
+        const double2 a0 = sp.amps[warp * 64 + 2 * lane], a1 = sp.amps[warp * 64 + 2 * lane + 1];
+        p0 = __ddiv_rn(__dadd_rn(__dmul_rn(a0.x, a0.x), __dmul_rn(a0.y, a0.y)), sp.invF_num);
+        p1 = __ddiv_rn(__dadd_rn(__dmul_rn(a1.x, a1.x), __dmul_rn(a1.y, a1.y)), sp.invF_num);
+    }
+    double x = __dadd_rn(p0, p1);
+#pragma unroll
+    for (int off = 1; off < 32; off <<= 1) {
+        const double y = __shfl_up_sync(0xffffffffu, x, off);
+        if (lane >= off) x = __dadd_rn(y, x);
+    }
+    const double pj = __shfl_sync(0xffffffffu, x, 31);
+    double excl = __shfl_up_sync(0xffffffffu, x, 1);
+    if (lane == 0) excl = 0.0;
+    const uint64_t t = sp.t0 + (uint64_t)warp;
+    const uint2 key = make_uint2((uint32_t)sp.seed, (uint32_t)(sp.seed >> 32));
+    const uint4 o0 = philox4x32_10(make_uint4((uint32_t)t, (uint32_t)(t >> 32), 0u, 0u), key);
+    const uint4 o1 = philox4x32_10(make_uint4((uint32_t)t, (uint32_t)(t >> 32), 1u, 0u), key);
+    const double u = u53(o0.z, o0.w), v = u53(o1.x, o1.y);
+    const double NB = ldexp(1.0, sp.b_bits);
+    const bool acc = __dmul_rn(u, sp.alpha) < __dmul_rn(pj, NB);
+    const double tau = __dmul_rn(v, pj);
+    const double c0 = __dadd_rn(excl, p0), c1 = x;
+    const bool h0 = c0 > tau, h1 = c1 > tau;
+    const unsigned hit = __ballot_sync(0xffffffffu, h0 || h1);
+    int pick;
+    if (hit) {
+        const int L = __ffs(hit) - 1;
+        const bool l0 = __shfl_sync(0xffffffffu, h0, L);
+        pick = l0 ? 2 * L : 2 * L + 1;
+    } else {
+        const unsigned nz = __ballot_sync(0xffffffffu, p0 > 0.0 || p1 > 0.0);
+        if (nz) {
+            const int L = 31 - __clz(nz);
+            const bool z1 = __shfl_sync(0xffffffffu, p1 > 0.0, L);
+            pick = z1 ? 2 * L + 1 : 2 * L;
+        } else {
+            pick = 63;
+        }
+    }
+    if (lane == 0) {
+        sp.accept[warp] = acc ? 1 : 0;
+        sp.pick[warp] = pick;
+        if (sp.eps) sp.eps[warp] = fmax(__dadd_rn(pj, -sp.alpha / NB), 0.0);
+        if (sp.bits) {
+            const uint64_t jj = sp.j[warp];
+            uint64_t b = 0;
+            for (int r = 0; r < sp.n_open; r++) b |= (uint64_t)((pick >> r) & 1) << sp.open_q[r];
+            for (int c = 0; c < sp.n_closed; c++) b |= ((jj >> c) & 1ull) << sp.closed_q[c];
+            sp.bits[warp] = b;
+        }
+    }
+}
+
+// ---------------------------------------------------------------- slice cut
+
+// Alg. 1 steps 4-5 for 2^k <= 4096 norms in one block: bitonic sort of (R desc, i asc)
+// in shared memory, then a sequential FP64 prefix in sorted order.
+__global__ void slice_cut(const double *R, int k, double f, int32_t *X, int32_t *n_x, double *F) {
+    extern __shared__ unsigned char smem[];
+    const int n = 1 << k;
+    double *r = reinterpret_cast<double *>(smem);
+    int *idx = reinterpret_cast<int *>(r + n);
+    for (int i = threadIdx.x; i < n; i += blockDim.x) { r[i] = R[i]; idx[i] = i; }
+    __syncthreads();
+    for (int size = 2; size <= n; size <<= 1)
+        for (int stride = size >> 1; stride > 0; stride >>= 1) {
+            for (int i = threadIdx.x; i < n; i += blockDim.x) {
+                const int j = i ^ stride;
+                if (j > i) {
+                    // "before(a, b)": a precedes b in (R descending, index ascending) order
+                    const bool a_first = r[i] > r[j] || (r[i] == r[j] && idx[i] < idx[j]);
+                    const bool up = (i & size) == 0;
+                    if (up != a_first) {
+                        const double tr = r[i]; r[i] = r[j]; r[j] = tr;
+                        const int ti = idx[i]; idx[i] = idx[j]; idx[j] = ti;
+                    }
+                }
+            }
+            __syncthreads();
+        }
+    if (threadIdx.x == 0) {
+        double acc = 0.0;
+        int cnt = n;
+        for (int t = 0; t < n; t++) {
+            acc = __dadd_rn(acc, r[t]);
+            if (acc >= f) { cnt = t + 1; break; }
+        }
+        *n_x = cnt;
+        *F = acc;
+    }
+    __syncthreads();
+    const int cnt = *n_x;
+    for (int t = threadIdx.x; t < cnt; t += blockDim.x) X[t] = idx[t];
+}
+
+}  // namespace tnk

@@ -1,0 +1,155 @@
+// Internal structures of libtn: circuit, tensor network, contraction tree and the
+// compiled step list.  Host-only declarations (shared by planner.cpp and engine.cu).
+#pragma once
+
+#include <cstdint>
+#include <complex>
+#include <string>
+#include <vector>
+
+#include "tn.h"
+
+using cplx = std::complex<double>;
+
+// ------------------------------------------------------------------ errors
+void tn_set_error(const std::string &msg);
+
+// ------------------------------------------------------------------ circuit
+struct TnGate {
+    int arity;
+    int q[2];
+    cplx m[16];  // row-major (2^arity)^2
+};
+
+struct tn_circuit_s {
+    int n = 0;
+    std::vector<TnGate> gates;
+};
+
+int tn_parse_circuit(const void *buf, size_t len, tn_circuit_s *c);
+
+// ------------------------------------------------------------------ index sets
+constexpr int kMaxIdx = 1024;
+struct Bits {
+    uint64_t w[kMaxIdx / 64] = {};
+    void set(int i) { w[i >> 6] |= 1ull << (i & 63); }
+    void clr(int i) { w[i >> 6] &= ~(1ull << (i & 63)); }
+    bool has(int i) const { return (w[i >> 6] >> (i & 63)) & 1; }
+    int count() const {
+        int c = 0;
+        for (auto x : w) c += __builtin_popcountll(x);
+        return c;
+    }
+    Bits operator|(const Bits &o) const { Bits r; for (int i = 0; i < kMaxIdx / 64; i++) r.w[i] = w[i] | o.w[i]; return r; }
+    Bits operator&(const Bits &o) const { Bits r; for (int i = 0; i < kMaxIdx / 64; i++) r.w[i] = w[i] & o.w[i]; return r; }
+    Bits andnot(const Bits &o) const { Bits r; for (int i = 0; i < kMaxIdx / 64; i++) r.w[i] = w[i] & ~o.w[i]; return r; }
+    bool any() const { for (auto x : w) if (x) return true; return false; }
+    std::vector<int> list() const {
+        std::vector<int> out;
+        for (int i = 0; i < kMaxIdx / 64; i++) {
+            uint64_t x = w[i];
+            while (x) { int b = __builtin_ctzll(x); out.push_back(i * 64 + b); x &= x - 1; }
+        }
+        return out;
+    }
+};
+
+// ------------------------------------------------------------------ network
+// Leg kinds of a leaf tensor.
+enum LegKind { LEG_NET = 0, LEG_SLICED = 1, LEG_CLOSED = 2 };
+
+struct Leaf {
+    // data index = sum_t value(leg t) << t
+    std::vector<int> kind;  // LegKind
+    std::vector<int> ref;   // NET: network index id; SLICED: position e in I; CLOSED: closed pos c
+    std::vector<cplx> data; // 2^legs
+};
+
+// A contraction network: leaves, index space, output indices.
+struct Network {
+    int n_idx = 0;                 // network index ids [0, n_idx)
+    std::vector<Leaf> leaves;
+    std::vector<int> out_layout;   // output index ids, LSB first
+    int n_beta = 0;                // beta bits are network ids beta_base .. beta_base+n_beta-1
+    int beta_base = -1;
+    int n_sliced = 0;              // |I|
+    std::vector<int> idx_seg;      // segment id of each network index (-1: beta / other)
+};
+
+// Contraction tree node.
+struct Node {
+    Bits idx;              // network indices of the tensor
+    uint64_t dep = 0;      // sliced edges its subtree depends on (bit e = I[e])
+    int ch[2] = {-1, -1};  // children (internal nodes)
+    int leaf = -1;         // leaf number (leaves)
+    bool beta = false;     // carries beta bits
+    std::vector<int> layout;  // storage order of idx, LSB first (set by the compiler)
+};
+
+// One pairwise contraction: C[v][bat][m][n] = sum_k A[v][bat][m][k] * B[v][bat][n][k].
+struct Step {
+    int c, a, b;                     // node ids, a = row operand
+    int nbat, nm, nn, nk;            // bit counts
+    int8_t pos_bat[64], pos_m[64], pos_n[64];  // bit positions in C's layout
+    double flops_per_version;        // 8 * 2^(nbat+nm+nn+nk)
+};
+
+struct Tree {
+    std::vector<Node> nodes;  // leaves first (node i = leaf i), then internal in SSA order
+    int root = -1;
+};
+
+struct TreeCost {
+    double flops = 0;     // algorithmic FLOPs over all versions
+    double bytes = 0;     // operand + result bytes
+    double time = 0;      // estimated seconds
+    int log2_max = 0;     // largest per-version tensor (log2 elements)
+    double max_versioned = 0;  // largest versioned tensor (elements)
+};
+
+// Planner entry points (planner.cpp).
+struct MergedGate {
+    int qa, qb, sa, sb;
+    cplx M[16];  // index (oa<<3)|(ob<<2)|(ia<<1)|ib
+};
+
+struct Merged {
+    int n = 0;
+    std::vector<MergedGate> gates;
+    std::vector<int> n2q;             // two-qubit gates per qubit
+    std::vector<cplx> input;          // 2 per qubit: leading single-qubit gates applied to |0>
+    std::vector<int> seg_base;        // segment id of (q, s) = seg_base[q] + s
+    int n_seg = 0;
+};
+
+void tn_merge(const tn_circuit_s &c, Merged &mg);
+
+// Alg. 2 on the merged view: returns S as positions into I (sorted by (qubit, segment)).
+std::vector<int> tn_sliced_vertex_select(const Merged &mg, const std::vector<tn_edge> &I, int k);
+// Lightcone union (merged gate ids) of a set of vertices.
+std::vector<int> tn_lightcone(const Merged &mg, const std::vector<tn_edge> &S);
+
+// Network of the amplitude batches: open legs, beta selector leaves, sliced legs.
+int tn_build_amp_network(const Merged &mg, const std::vector<tn_edge> &I, const std::vector<int> &open,
+                         int log2_batches, Network &net, std::vector<int> &closed_qubits);
+// Norm network C1 (x) C1* (Fig. 1) with the S legs identified; output = S legs in S order.
+int tn_build_norm_network(const Merged &mg, const std::vector<tn_edge> &S, Network &net);
+
+// Contraction order and tree compilation.
+void tn_tree_from_leaves(const Network &net, Tree &t);
+int tn_tree_from_ssa(const Network &net, const int32_t *pairs, int n_pairs, Tree &t);
+void tn_greedy_tree(const Network &net, uint64_t seed, int trials, Tree &best, TreeCost &cost);
+TreeCost tn_tree_cost(const Network &net, const Tree &t);
+void tn_recompute_deps(const Network &net, Tree &t);
+std::vector<int> tn_auto_slice(const Merged &mg, Network &net, Tree &t, int n_slice);
+int tn_compile(const Network &net, Tree &t, std::vector<Step> &steps);
+
+// Whole host-side planning: sliced edges (given or auto), the amplitude network, the
+// contraction tree (given SSA order or seeded greedy) and the compiled steps.
+int tn_plan_build_host(const Merged &mg, const tn_plan_opts &o, const int32_t *order, int n_order,
+                       const tn_edge *sliced, int n_sliced, const std::vector<int> &open,
+                       std::vector<tn_edge> &I, Network &net, Tree &tree, std::vector<Step> &steps,
+                       std::vector<int> &closed);
+// Greedy tree of a network (or the SSA order when given) + compile.
+int tn_tree_and_compile(const Network &net, const tn_plan_opts &o, const int32_t *order, int n_order,
+                        const Tree *candidate, Tree &tree, std::vector<Step> &steps);

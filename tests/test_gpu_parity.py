@@ -1,0 +1,279 @@
+"""GPU parity of the CUDA path (through the C-ABI) against the CPU oracle.
+
+Tolerances: complex64 contractions must match the FP64 oracle within
+max|a - a_ref| <= 1e-4 * RMS(a_ref) over every compared amplitude; FP64 paths (norms)
+within 1e-12; integer / index outputs (slice cut, Philox draws, sampler decisions)
+bit-exact given identical inputs.
+"""
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_2112_15083_gb300 import circuits as cg
+
+pytestmark = pytest.mark.gpu
+
+TOL_C64 = 1e-4
+
+
+@pytest.fixture(scope="module", autouse=True)
+def gpu():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import __graft_entry__
+    __graft_entry__.build()
+    torch.cuda.set_device(0)
+    return torch
+
+
+def pkg():
+    import paper_2112_15083_gb300 as p
+    return p
+
+
+def close_c64(got, ref):
+    rms = float(np.sqrt(np.mean(np.abs(ref) ** 2)))
+    err = float(np.abs(got - ref).max())
+    assert err <= TOL_C64 * rms, "max err %.3e > %.1e * rms %.3e" % (err, TOL_C64, rms)
+    return err / rms
+
+
+# ------------------------------------------------------------------ contraction
+
+def test_12q_all_amplitudes_two_slices():
+    """3x4 grid, 8 cycles, all 12 qubits open, 2 sliced legs: all 4096 amplitudes."""
+    P = pkg()
+    circ = cg.sycamore_grid(3, 4, 8, seed=0)
+    C = P.circuit_load(circ.serialize())
+    plan = P.plan(C, list(range(12)), n_auto_sliced=2, log2_batches=0)
+    sl = plan.sliced_edges()
+    assert len(sl) == 2
+    amps = plan.contract(np.arange(4, dtype=np.uint64), [0])
+    psi = oracle.simulate(circ)
+    close_c64(amps[0], psi)
+    for s in range(4):
+        one = plan.contract(np.array([s], np.uint64), [0])
+        ref = oracle.simulate(circ, [(q, g, (s >> e) & 1) for e, (q, g) in enumerate(sl)])
+        close_c64(one[0], ref if np.abs(ref).max() > 0 else psi)
+
+
+@pytest.mark.parametrize("seed", [0, 1])
+def test_haar_batches_ragged_groups_and_slice_subsets(seed):
+    """Generic gates, 3 open qubits, T = 8 per group, 13 batches (two groups, ragged)."""
+    P = pkg()
+    n = 10
+    circ = cg.random_haar(n, 70, seed=seed, p_two=0.75)
+    openq = [7, 1, 4]
+    closed = oracle.closed_of(n, openq)
+    C = P.circuit_load(circ.serialize())
+    plan = P.plan(C, openq, n_auto_sliced=4, log2_batches=3, order_trials=8)
+    sl = plan.sliced_edges()
+    cb = cg.random_closed_bits(13, len(closed), seed=seed + 10)
+    psi = oracle.simulate(circ)
+    amps = plan.contract(np.arange(16, dtype=np.uint64), cb)
+    close_c64(amps, oracle.batch_amplitudes(psi, n, openq, cb))
+    sub = np.array([9, 2, 14, 5], dtype=np.uint64)
+    amps = plan.contract(sub, cb)
+    close_c64(amps, oracle.batch_amplitudes(oracle.sliced_state(circ, sl, sub), n, openq, cb))
+
+
+def test_20q_many_groups_device_buffers(gpu):
+    torch = gpu
+    P = pkg()
+    circ = cg.sycamore_grid(4, 5, 10, seed=2)
+    openq = cg.default_open_qubits(4, 5, 6)
+    C = P.circuit_load(circ.serialize())
+    plan = P.plan(C, openq, n_auto_sliced=6, log2_batches=4, order_trials=16)
+    cb = cg.random_closed_bits(50, 14, seed=5)
+    ref = oracle.batch_amplitudes(oracle.simulate(circ), 20, openq, cb)
+    slices = np.arange(64, dtype=np.uint64)
+    out = plan.contract(slices, torch.from_numpy(cb.astype(np.int64)).cuda())
+    close_c64(out.cpu().numpy(), ref)
+    close_c64(plan.contract(slices, cb), ref)
+
+
+@pytest.fixture(scope="module")
+def grid28():
+    circ = cg.sycamore_grid(4, 7, 14, seed=0)
+    psi = oracle.simulate(circ)
+    return circ, psi
+
+
+def test_28q_256_batches_full_slice_set(grid28):
+    """The 4x7 / 14-cycle workload: 2^10 slices, 256 batches of 64, all amplitudes."""
+    P = pkg()
+    circ, psi = grid28
+    openq = cg.default_open_qubits(4, 7, 6)
+    C = P.circuit_load(circ.serialize())
+    plan = P.plan(C, openq, n_auto_sliced=10, log2_batches=8, order_trials=256)
+    cb = cg.random_closed_bits(256, 22, seed=1)
+    amps = plan.contract(np.arange(1024, dtype=np.uint64), cb)
+    close_c64(amps, oracle.batch_amplitudes(psi, 28, openq, cb))
+
+
+def test_28q_single_slice_sampled(grid28):
+    """One slice at full size, checked against the oracle's projector simulation."""
+    P = pkg()
+    circ, _ = grid28
+    openq = cg.default_open_qubits(4, 7, 6)
+    C = P.circuit_load(circ.serialize())
+    plan = P.plan(C, openq, n_auto_sliced=10, log2_batches=4, order_trials=64)
+    sl = plan.sliced_edges()
+    s = 0b1011001101
+    cb = cg.random_closed_bits(16, 22, seed=7)
+    amps = plan.contract(np.array([s], np.uint64), cb)
+    ref_state = oracle.simulate(circ, [(q, g, (s >> e) & 1) for e, (q, g) in enumerate(sl)])
+    ref = oracle.batch_amplitudes(ref_state, 28, openq, cb)
+    if np.abs(ref).max() > 0:
+        close_c64(amps, ref)
+    else:
+        assert np.abs(amps).max() < 1e-6
+
+
+def test_bad_slices_rejected():
+    P = pkg()
+    circ = cg.sycamore_grid(3, 4, 8, seed=0)
+    C = P.circuit_load(circ.serialize())
+    plan = P.plan(C, list(range(12)), n_auto_sliced=2, log2_batches=0)
+    with pytest.raises(P.TnError) as e:
+        plan.contract(np.array([1, 1], np.uint64), [0])
+    assert e.value.code == P.tn.TN_EINVAL
+    with pytest.raises(P.TnError):
+        plan.contract(np.array([4], np.uint64), [0])  # bit beyond |I|
+
+
+def test_hbm_budget_enforced():
+    P = pkg()
+    circ = cg.sycamore_grid(3, 4, 8, seed=0)
+    C = P.circuit_load(circ.serialize())
+    plan = P.plan(C, list(range(12)), n_auto_sliced=2, log2_batches=0, hbm_budget_bytes=1024.0)
+    with pytest.raises(P.TnError) as e:
+        plan.contract(np.arange(4, dtype=np.uint64), [0])
+    assert e.value.code == P.tn.TN_ENOMEM
+
+
+# ------------------------------------------------------------------ selection
+
+@pytest.mark.parametrize("grid,f", [((3, 4, 8), 0.25), ((4, 5, 12), 1 / 64)])
+def test_partial_norms_fp64(grid, f):
+    P = pkg()
+    circ = cg.sycamore_grid(*grid, seed=0)
+    n = grid[0] * grid[1]
+    view = oracle.MergedView(circ)
+    I = [(q, s) for q in range(n) for s in range(1, view.n2q[q] - 1)]
+    C = P.circuit_load(circ.serialize())
+    plan = P.plan(C, cg.default_open_qubits(grid[0], grid[1], 6), sliced=I[:40], log2_batches=2)
+    S_idx, R = plan.partial_norms(f)
+    S_ref = oracle.sliced_vertex_select(circ, I[:40], oracle.k0_for(f))
+    assert [I[i] for i in S_idx] == S_ref
+    R_ref = oracle.norms(circ, S_ref)
+    assert np.abs(R - R_ref).max() < 1e-12
+    assert abs(R.sum() - 1) < 1e-12
+
+
+@pytest.mark.parametrize("k,f", [(4, 0.3), (10, 0.02), (12, 0.002), (10, 0.999)])
+def test_slice_cut_bit_exact(k, f):
+    P = pkg()
+    rng = np.random.default_rng(k)
+    R = rng.exponential(size=1 << k)
+    R[5] = R[9]  # a tie, broken by index
+    R /= R.sum()
+    X, F = P.slice_cut(R, f)
+    Xr, Fr = oracle.select_slices(R, f)
+    assert list(X) == list(Xr)
+    assert F == Fr
+
+
+def test_select_partial_state_20q():
+    """Alg. 1 end to end (GPU norms + cut), then the partial contraction of Sec. I.C."""
+    P = pkg()
+    circ = cg.sycamore_grid(4, 5, 12, seed=0)
+    view = oracle.MergedView(circ)
+    openq = cg.default_open_qubits(4, 5, 6)
+    C = P.circuit_load(circ.serialize())
+    I = [(q, s) for q in range(20) for s in range(2, view.n2q[q] - 1)][:12]
+    plan = P.plan(C, openq, sliced=I, log2_batches=4, order_trials=16)
+    f = 0.25
+    slices, F = plan.select(f)
+    S_ref, X_ref, F_ref, R_ref = oracle.slice_selection(circ, I, f)
+    assert abs(F - F_ref) < 1e-12
+    k = len(S_ref)
+    assert len(slices) == len(X_ref) << (len(I) - k)
+    cb = cg.random_closed_bits(20, 14, seed=3)
+    amps = plan.contract(slices, cb)
+    ref = oracle.batch_amplitudes(oracle.partial_state(circ, S_ref, X_ref), 20, openq, cb)
+    close_c64(amps, ref)
+
+
+# ------------------------------------------------------------------ sampler
+
+def test_draw_batches_bit_exact():
+    P = pkg()
+    for b_bits in (0, 6, 22, 40):
+        j = P.draw_batches(123, 1000, 3000, b_bits).cpu().numpy().astype(np.uint64)
+        ref = oracle.batch_draws(123, 3000, b_bits, t0=1000)
+        assert np.array_equal(j, ref)
+
+
+def sampler_cases():
+    rng = np.random.default_rng(0)
+    T = 4096
+    p = rng.exponential(size=(T, 64)) / (64 * 2 ** 12)
+    p[0] = 0.0                      # empty batch: never accepted
+    p[1] = 0.0
+    p[1, 17] = 1e-3                 # single mass point
+    p[2, ::2] = 0.0                 # zeros interleaved
+    p[3] *= 50                      # clipped batch (p_j N_B > alpha)
+    p[4, :] = 1.0 / (64 * 4096)     # uniform
+    return p
+
+
+@pytest.mark.parametrize("alpha,seed,t0", [(2.0, 1, 0), (1.5, 99, 123456789), (8.0, 2 ** 63 + 5, 7)])
+def test_sampler_bit_identical(gpu, alpha, seed, t0):
+    torch = gpu
+    P = pkg()
+    p = sampler_cases()
+    acc, pick = P.rejection_sample(torch.from_numpy(p).cuda(), 12, alpha, seed, t0)
+    acc_r, pick_r = oracle.sample_batches(p, 12, alpha, seed, t0=t0)
+    assert np.array_equal(acc.cpu().numpy().astype(bool), acc_r)
+    assert np.array_equal(pick.cpu().numpy(), pick_r)
+    assert not acc_r[0] and pick_r[1] == 17
+
+
+def test_sample_end_to_end_12q():
+    """tn_sample at full fidelity vs the oracle sampler on the exact distribution: the
+    draws use the same Philox streams, so all but near-threshold decisions agree."""
+    P = pkg()
+    circ = cg.sycamore_grid(3, 4, 8, seed=0)
+    openq = cg.default_open_qubits(3, 4, 6)
+    C = P.circuit_load(circ.serialize())
+    plan = P.plan(C, openq, n_auto_sliced=2, log2_batches=6, order_trials=16)
+    N = 2000
+    bits, st = plan.sample(1.0, N, seed=11, alpha=2.0)
+    p = np.abs(oracle.simulate(circ)) ** 2
+    ref, steps, eps_hat = oracle.sample(p, 12, openq, N, seed=11, alpha=2.0, chunk=64)
+    assert st["F"] == 1.0 and st["accepted"] >= N
+    same = np.mean(bits.astype(np.int64) == ref)
+    assert same > 0.99, same
+    assert abs(st["eps_hat"] - eps_hat) < 1e-6
+
+
+@pytest.mark.slow
+def test_sample_xeb_tracks_fidelity_20q():
+    """Sampling at partial fidelity: the linear XEB of the GPU samples ~ F (Table elided)."""
+    P = pkg()
+    circ = cg.sycamore_grid(4, 5, 12, seed=0)
+    view = oracle.MergedView(circ)
+    openq = cg.default_open_qubits(4, 5, 6)
+    C = P.circuit_load(circ.serialize())
+    I = [(q, s) for q in range(20) for s in range(2, view.n2q[q] - 1)][:12]
+    plan = P.plan(C, openq, sliced=I, log2_batches=8, order_trials=16)
+    N = 40000
+    bits, st = plan.sample(0.25, N, seed=5, alpha=2.0)
+    p = np.abs(oracle.simulate(circ)) ** 2
+    xeb = oracle.xeb_of_samples(p, 20, bits.astype(np.int64))
+    sigma = math.sqrt(2.0 / N)  # Porter-Thomas: Var(2^n p) ~ 1 (+ F terms)
+    assert abs(xeb - st["F"]) < 4 * sigma + 0.02 * st["F"], (xeb, st["F"])
