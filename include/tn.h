@@ -121,8 +121,9 @@ typedef struct {
 int tn_plan_get_info(tn_plan_h p, tn_plan_info *info);
 /*
  * Host-only planning (no device work), for inspection and tests: runs the same planner
- * as tn_plan and fills info; if steps != NULL, writes up to cap_steps rows of five
- * int32 per step (batch bits, m bits, n bits, k bits, log2 versions over all slices);
+ * as tn_plan and fills info; if steps != NULL, writes up to cap_steps rows of seven
+ * int32 per step (batch bits, m bits, n bits, k bits, then log2 of the versions of C, A
+ * and B over the full slice set);
  * if sliced_out != NULL, writes up to cap_sliced sliced edges in slice-bit order.
  */
 int tn_plan_host(tn_circuit_h c, const int32_t *order, int32_t n_order, const tn_edge *sliced,

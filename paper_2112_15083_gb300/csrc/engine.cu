@@ -288,18 +288,30 @@ int prepare_call(DevMem &mem, CNet &cn, const std::vector<uint64_t> &slices, dou
         if (!merged.empty() && merged.back().off + merged.back().len == top) { top = merged.back().off; merged.pop_back(); }
         freel.swap(merged);
     };
+    // Stem tensors kept for later batch groups (batch-free, consumed by a batch step)
+    // get a reserved prefix: batch-dependent tensors are rewritten in every group, so
+    // the two must never share memory.
+    std::vector<char> keep(NN, 0);
+    for (const Step &s : cn.steps)
+        for (int ch : {s.a, s.b})
+            if (nodes[ch].ch[0] >= 0 && !nodes[ch].beta && nodes[s.c].beta) keep[ch] = 1;
+    size_t reserved = 0;
     cp.off.assign(NN, 0);
+    for (const Step &s : cn.steps)
+        if (keep[s.c]) {
+            cp.off[s.c] = reserved;
+            reserved += (tensor_bytes(s.c) + 255) & ~size_t(255);
+        }
     size_t peak = 0;
     for (const Step &s : cn.steps) {
-        cp.off[s.c] = alloc(tensor_bytes(s.c));
-        peak = std::max(peak, top);
-        for (int ch : {s.a, s.b}) {
-            if (nodes[ch].ch[0] < 0) continue;
-            bool persistent = !nodes[ch].beta && nodes[s.c].beta;
-            if (!persistent) dealloc(cp.off[ch], tensor_bytes(ch));
+        if (!keep[s.c]) {
+            cp.off[s.c] = reserved + alloc(tensor_bytes(s.c));
+            peak = std::max(peak, top);
         }
+        for (int ch : {s.a, s.b})
+            if (nodes[ch].ch[0] >= 0 && !keep[ch]) dealloc(cp.off[ch] - reserved, tensor_bytes(ch));
     }
-    cp.arena_bytes = std::max<size_t>(peak, 256);
+    cp.arena_bytes = std::max<size_t>(reserved + peak, 256);
     if ((double)cp.arena_bytes + (double)cn.leaf_bytes > budget) {
         tn_set_error("working set of " + std::to_string(cp.arena_bytes) + " bytes exceeds the HBM budget");
         return TN_ENOMEM;
@@ -578,9 +590,11 @@ int tn_plan_host(tn_circuit_h c, const int32_t *order, int32_t n_order, const tn
     if (steps_out)
         for (int i = 0; i < (int)steps.size() && i < cap_steps; i++) {
             const Step &s = steps[i];
-            int32_t *r = steps_out + 5 * i;
+            int32_t *r = steps_out + 7 * i;
             r[0] = s.nbat; r[1] = s.nm; r[2] = s.nn; r[3] = s.nk;
             r[4] = __builtin_popcountll(tree.nodes[s.c].dep);
+            r[5] = __builtin_popcountll(tree.nodes[s.a].dep);
+            r[6] = __builtin_popcountll(tree.nodes[s.b].dep);
         }
     if (sliced_out)
         for (int i = 0; i < (int)I.size() && i < cap_sliced; i++) sliced_out[i] = I[i];

@@ -335,7 +335,8 @@ class Plan:
 
 def plan_host(circuit: Circuit, open_qubits, sliced=None, order=None, log2_batches=8, order_seed=0,
               order_trials=64, n_auto_sliced=0):
-    """Host-only planning (no GPU): (info dict, steps array (n_steps, 5), sliced edges)."""
+    """Host-only planning (no GPU): (info dict, steps array (n_steps, 7), sliced edges).
+    Step row: batch, m, n, k bits, log2 versions of C, A, B."""
     L = lib()
     o = PlanOpts()
     L.tn_plan_opts_default(ctypes.byref(o))
@@ -355,7 +356,7 @@ def plan_host(circuit: Circuit, open_qubits, sliced=None, order=None, log2_batch
     else:
         ord_ptr, n_ord = None, 0
     inf = PlanInfo()
-    steps = np.zeros((4096, 5), dtype=np.int32)
+    steps = np.zeros((4096, 7), dtype=np.int32)
     sl_out = (Edge * 64)()
     rc = L.tn_plan_host(circuit.h, ord_ptr, n_ord, sl_ptr, n_sl, _np_ptr(openq), openq.size, ctypes.byref(o),
                         ctypes.byref(inf), _np_ptr(steps), 4096, ctypes.cast(sl_out, ctypes.c_void_p), 64)

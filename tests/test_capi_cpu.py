@@ -68,7 +68,7 @@ def test_host_plan_counts_and_shapes():
     for q, s in sliced:
         assert 1 <= s < cnt[q]
     # every step's bit classes fit the engine's 40-bit addressing
-    assert (steps[:, 0] + steps[:, 1] + steps[:, 2] <= 40).all()
+    assert steps.shape[1] == 7 and (steps[:, 0] + steps[:, 1] + steps[:, 2] <= 40).all()
 
 
 def test_host_plan_rejects_bad_sliced_edge():

@@ -60,7 +60,7 @@ def test_12q_all_amplitudes_two_slices():
         close_c64(one[0], ref if np.abs(ref).max() > 0 else psi)
 
 
-@pytest.mark.parametrize("seed", [0, 1])
+@pytest.mark.parametrize("seed", [0, 1, 2, 3, 4, 5])
 def test_haar_batches_ragged_groups_and_slice_subsets(seed):
     """Generic gates, 3 open qubits, T = 8 per group, 13 batches (two groups, ragged)."""
     P = pkg()
