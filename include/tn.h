@@ -166,6 +166,21 @@ int tn_slice_cut(const double *R, int32_t k, double f, void *stream, int32_t *X,
                  int32_t *n_x, double *F);
 
 /*
+ * tn_slice_cut without any device allocation (the paper has no counterpart; this is a
+ * deployment variant).  For callers that cannot allocate device memory from their call
+ * path: processes whose device memory is owned up front by another allocator, and code
+ * that must not enter the CUDA allocator (which can wait on other device work and can
+ * fail under fragmentation).  Same arguments and results as tn_slice_cut, but the device
+ * scratch is a 64 KiB static array in libtn that every GPU loading the library holds
+ * until the process exits; k above 12 is rejected with TN_EINVAL.  The first call on a
+ * device looks up the array's device address (cudaGetSymbolAddress) with that device
+ * current; make that first call before any stream capture.  All calls share the one
+ * array per device: calls whose work overlaps on the GPU race with each other.
+ */
+int tn_slice_cut_noalloc(const double *R, int32_t k, double f, void *stream, int32_t *X,
+                         int32_t *n_x, double *F);
+
+/*
  * Slice selection for fidelity f (Alg. 1): tn_partial_norms + tn_slice_cut, then the
  * slice set X x {0,1}^{|I|-k} (Sec. I.C step 1) written to slices (cap entries).  When
  * f >= 1 every slice is kept and F = 1.  n_slices receives the set size even if cap is

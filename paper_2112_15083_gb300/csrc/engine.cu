@@ -9,6 +9,7 @@
 #include <algorithm>
 #include <cmath>
 #include <cstring>
+#include <mutex>
 #include <numeric>
 #include <unordered_map>
 
@@ -1013,3 +1014,87 @@ int tn_sample(tn_plan_h p, double f_target, int64_t N, uint64_t seed, double alp
 }
 
 }  // extern "C"
+
+// ---------------------------------------------------------------- allocation-free slice cut
+//
+// Some callers cannot allocate device memory from their call path: a process whose
+// device memory is owned up front by another allocator (for example a serving loop
+// that reserved all of HBM for plans and resident tensors), or code that must not
+// enter the CUDA allocator at all (an allocation can wait on other work on the device
+// and can fail when memory is fragmented).  tn_slice_cut_noalloc is tn_slice_cut for
+// them: its scratch (the copy of R, the sorted indices, the count and the sum) lives in
+// the static device array below, reserved when the library is loaded and held by every
+// GPU that loads it until the process exits.
+
+namespace {
+constexpr int kCutMaxK = 12;                                               // 2^12 norms at most
+constexpr size_t kCutRBytes = (size_t(1) << kCutMaxK) * sizeof(double);    // 32 KiB
+constexpr size_t kCutXBytes = (size_t(1) << kCutMaxK) * sizeof(int32_t);   // 16 KiB
+constexpr size_t kCutScratchBytes = kCutRBytes + kCutXBytes + 256;        // + count and sum
+constexpr int kCutMaxDevices = 64;
+}  // namespace
+
+static __device__ __align__(256) unsigned char g_cut_scratch[kCutScratchBytes];
+
+namespace {
+std::mutex g_cut_mu;
+void *g_cut_dev_ptr[kCutMaxDevices] = {};
+
+// Device address of g_cut_scratch on the current device.  Host code only has a
+// host-side stand-in under that name, so the address is looked up once per device
+// (with that device current) and cached.
+int cut_scratch_address(void **out) {
+    int dev = -1;
+    CK(cudaGetDevice(&dev));
+    if (dev < 0 || dev >= kCutMaxDevices) {
+        tn_set_error("tn_slice_cut_noalloc: device ordinal outside the supported range");
+        return TN_EUNSUPPORTED;
+    }
+    std::lock_guard<std::mutex> lock(g_cut_mu);
+    if (!g_cut_dev_ptr[dev]) {
+        void *p = nullptr;
+        CK(cudaGetSymbolAddress(&p, g_cut_scratch));
+        if (!p) {
+            tn_set_error("tn_slice_cut_noalloc: no device address for the static scratch");
+            return TN_EDEVICE;
+        }
+        g_cut_dev_ptr[dev] = p;
+    }
+    *out = g_cut_dev_ptr[dev];
+    return TN_OK;
+}
+}  // namespace
+
+extern "C" int tn_slice_cut_noalloc(const double *R, int32_t k, double f, void *stream, int32_t *X, int32_t *n_x,
+                                    double *F) {
+    if (!R || !X || !n_x || !F || k < 0) {
+        tn_set_error("tn_slice_cut_noalloc: bad arguments");
+        return TN_EINVAL;
+    }
+    if (k > kCutMaxK) {
+        tn_set_error("tn_slice_cut_noalloc: k = " + std::to_string(k) + " exceeds the static scratch limit k <= " +
+                     std::to_string(kCutMaxK));
+        return TN_EINVAL;
+    }
+    void *base = nullptr;
+    RC(cut_scratch_address(&base));
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    const int n = 1 << k;
+    unsigned char *b = static_cast<unsigned char *>(base);
+    double *dR = reinterpret_cast<double *>(b);
+    int32_t *dX = reinterpret_cast<int32_t *>(b + kCutRBytes);
+    int32_t *dn = reinterpret_cast<int32_t *>(b + kCutRBytes + kCutXBytes);
+    double *dF = reinterpret_cast<double *>(b + kCutRBytes + kCutXBytes + 128);
+    // the array keeps the previous call's contents: clear the count and the sum
+    CK(cudaMemsetAsync(b + kCutRBytes + kCutXBytes, 0, 256, st));
+    CK(cudaMemcpyAsync(dR, R, n * sizeof(double), cudaMemcpyHostToDevice, st));
+    size_t smem = (size_t)n * (sizeof(double) + sizeof(int));
+    tnk::slice_cut<<<1, 256, smem, st>>>(dR, k, f, dX, dn, dF);
+    CK(cudaGetLastError());
+    CK(cudaMemcpyAsync(n_x, dn, sizeof(int32_t), cudaMemcpyDeviceToHost, st));
+    CK(cudaMemcpyAsync(F, dF, sizeof(double), cudaMemcpyDeviceToHost, st));
+    CK(cudaStreamSynchronize(st));
+    CK(cudaMemcpyAsync(X, dX, (size_t)(*n_x) * sizeof(int32_t), cudaMemcpyDeviceToHost, st));
+    CK(cudaStreamSynchronize(st));
+    return TN_OK;
+}

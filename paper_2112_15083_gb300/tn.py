@@ -24,6 +24,7 @@ EXPORTED = [
     "tn_plan_get_info", "tn_plan_sliced_edges", "tn_partial_norms", "tn_slice_cut", "tn_select",
     "tn_contract", "tn_sample", "tn_rejection_sample", "tn_draw_batches", "tn_strerror", "tn_last_error",
     "tn_plan_host", "tn_sliced_vertex_select", "tn_sample_step", "tn_trace_enable", "tn_trace_read",
+    "tn_slice_cut_noalloc",
 ]
 
 
@@ -117,6 +118,7 @@ def lib():
         L.tn_sample_step.argtypes = [vp, vp, i64, dbl, u64, u64, dbl, i32, vp, vp, i32]
         L.tn_trace_enable.argtypes = [vp, i32]
         L.tn_trace_read.argtypes = [vp, ctypes.POINTER(StepTrace), i32, ctypes.POINTER(i32)]
+        L.tn_slice_cut_noalloc.argtypes = [vp, i32, dbl, vp, vp, ctypes.POINTER(i32), ctypes.POINTER(dbl)]
         L.tn_strerror.argtypes = [ctypes.c_int]
         L.tn_strerror.restype = ctypes.c_char_p
         L.tn_last_error.argtypes = []
@@ -388,6 +390,20 @@ def slice_cut(R, f: float, stream=None):
     F = ctypes.c_double()
     _check(lib().tn_slice_cut(_np_ptr(R), k, f, _stream_ptr(stream), _np_ptr(X), ctypes.byref(n), ctypes.byref(F)),
            "tn_slice_cut")
+    return X[: n.value].copy(), F.value
+
+
+def slice_cut_noalloc(R, f: float, stream=None):
+    """tn_slice_cut_noalloc: the slice cut with its device scratch in libtn's static array
+    (no device allocation; k <= 12)."""
+    R = np.ascontiguousarray(np.asarray(R, dtype=np.float64))
+    k = int(np.log2(R.size))
+    assert R.size == 1 << k
+    X = np.zeros(R.size, dtype=np.int32)
+    n = ctypes.c_int32()
+    F = ctypes.c_double()
+    _check(lib().tn_slice_cut_noalloc(_np_ptr(R), k, f, _stream_ptr(stream), _np_ptr(X), ctypes.byref(n),
+                                      ctypes.byref(F)), "tn_slice_cut_noalloc")
     return X[: n.value].copy(), F.value
 
 
