@@ -250,6 +250,12 @@ def run_ours(args):
         dom["kernel"], dom["nbat"], dom["nm"], dom["nn"], dom["nk"], dom["nver"])
     roofline["share_of_step"] = dom["ms"] / max(1e-9, sum(s["ms"] for s in trace))
     roofline["peak_source"] = "derived: " + FFMA_PEAK_NOTE + " (FP32 FFMA, complex64 path)"
+    top_steps = []
+    for s in sorted(trace, key=lambda s: -s["ms"])[:6]:
+        ms1 = s["ms"] / max(1, s["launches"])
+        top_steps.append({"shape_bits": [s["nbat"], s["nm"], s["nn"], s["nk"]], "kernel": s["kernel"],
+                          "ms": round(ms1, 3), "tflops": round(s["flops_per_launch"] / (ms1 / 1e3) / 1e12, 2),
+                          "gbs": round(s["bytes_per_launch"] / (ms1 / 1e3) / 1e9, 1)})
 
     # end to end through the public API with host buffers (one tn_sample call per step)
     e2e = None
@@ -286,7 +292,7 @@ def run_ours(args):
             "data": "synthetic", "config": workload_config(args),
             "fidelity": F, "contraction_tflops": flops_step * args.steps / (tot_ms / 1e3) / 1e12,
             "flops_per_step": flops_step, "plan": info, "clocks": clk, "roofline": roofline,
-            "cpu_baseline": cpu, "e2e": e2e,
+            "cpu_baseline": cpu, "e2e": e2e, "top_steps": top_steps,
             "gpu_launches": args.steps * (len(trace) + 4),
         }
         print(json.dumps(line), flush=True)

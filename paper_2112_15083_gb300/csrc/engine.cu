@@ -94,6 +94,7 @@ struct CallPlan {
     std::vector<const void *> host_tab;        // pointer tables (device addresses)
     size_t arena_bytes = 0;
     double flops_all = 0, flops_beta = 0;      // per execution (all steps / beta steps)
+    long long root_nver = 0;                   // explicit root versions (slice sum outer loop)
     bool valid = false;
 };
 
@@ -101,6 +102,8 @@ struct CNet {
     Network net;
     Tree tree;
     std::vector<Step> steps;
+    uint64_t E = 0;            // explicit-version sliced legs of the compiled variant
+    bool compiled = false;
     int elem = 8;  // 8: complex64, 16: complex128
     std::vector<DBuf> leaf_src, leaf_dst;
     std::vector<int> leaf_codebits;
@@ -146,6 +149,8 @@ namespace {
 
 int setup_leaves(DevMem &mem, CNet &cn) {
     const int L = (int)cn.net.leaves.size();
+    for (auto &b : cn.leaf_src) release(mem, b);
+    for (auto &b : cn.leaf_dst) release(mem, b);
     cn.leaf_src.assign(L, DBuf());
     cn.leaf_dst.assign(L, DBuf());
     cn.leaf_codebits.assign(L, 0);
@@ -161,7 +166,7 @@ int setup_leaves(DevMem &mem, CNet &cn) {
         std::memset(&d, 0, sizeof(d));
         std::vector<int> sl, cl, clref;
         for (size_t l = 0; l < lf.kind.size(); l++) {
-            if (lf.kind[l] == LEG_SLICED) { sl.push_back((int)l); cn.leaf_sl[i].push_back(lf.ref[l]); }
+            if (lf.kind[l] == LEG_SLICED && ((cn.E >> lf.ref[l]) & 1)) { sl.push_back((int)l); cn.leaf_sl[i].push_back(lf.ref[l]); }
             if (lf.kind[l] == LEG_CLOSED) { cl.push_back((int)l); clref.push_back(lf.ref[l]); }
         }
         if (sl.size() > 8 || cl.size() > 8 || nd.layout.size() > (size_t)tnk::kMaxBits) {
@@ -174,8 +179,11 @@ int setup_leaves(DevMem &mem, CNet &cn) {
         for (int t = 0; t < d.nd; t++) {
             int id = nd.layout[t];
             int leg = -1;
-            for (size_t l = 0; l < lf.kind.size(); l++)
+            const bool vbit = id >= cn.net.n_idx && id < cn.net.n_idx + cn.net.n_sliced;
+            for (size_t l = 0; l < lf.kind.size(); l++) {
                 if (lf.kind[l] == LEG_NET && lf.ref[l] == id) leg = (int)l;
+                if (vbit && lf.kind[l] == LEG_SLICED && lf.ref[l] == id - cn.net.n_idx) leg = (int)l;
+            }
             if (leg >= 0) d.dst_leg[t] = (int8_t)leg;
             else if (id >= cn.net.beta_base && id < cn.net.beta_base + cn.net.n_beta) d.dst_leg[t] = (int8_t)(-1 - (id - cn.net.beta_base));
             else { tn_set_error("leaf layout index not found"); return TN_EINVAL; }
@@ -208,6 +216,7 @@ int setup_leaves(DevMem &mem, CNet &cn) {
         CK(cudaStreamSynchronize(mem.stream));
         release(mem, tmp);
     }
+    cn.cp.valid = false;
     if (!cn.beta_descs.empty()) {
         RC(ensure(mem, cn.d_beta_descs, cn.beta_descs.size() * sizeof(tnk::MatDesc)));
         CK(cudaMemcpyAsync(cn.d_beta_descs.p, cn.beta_descs.data(), cn.beta_descs.size() * sizeof(tnk::MatDesc),
@@ -248,7 +257,7 @@ int prepare_call(DevMem &mem, CNet &cn, const std::vector<uint64_t> &slices, dou
     std::vector<std::unordered_map<uint64_t, int>> index(NN);
     cp.nver.assign(NN, 0);
     for (int x = 0; x < NN; x++) {
-        const uint64_t D = nodes[x].dep;
+        const uint64_t D = nodes[x].dep & cn.E;
         for (uint64_t s : slices) {
             uint64_t w = s & D;
             if (index[x].emplace(w, (int)vals[x].size()).second) vals[x].push_back(w);
@@ -258,7 +267,7 @@ int prepare_call(DevMem &mem, CNet &cn, const std::vector<uint64_t> &slices, dou
     // arena: first fit, children released after their parent's step; beta-free
     // nodes consumed by beta steps stay alive (reused by later batch groups)
     auto tensor_bytes = [&](int x) {
-        return (size_t)cp.nver[x] * (size_t(1) << nodes[x].idx.count()) * (size_t)cn.elem;
+        return (size_t)cp.nver[x] * (size_t(1) << nodes[x].layout.size()) * (size_t)cn.elem;
     };
     struct Blk { size_t off, len; };
     std::vector<Blk> freel;
@@ -325,7 +334,7 @@ int prepare_call(DevMem &mem, CNet &cn, const std::vector<uint64_t> &slices, dou
             size_t sz = (size_t(1) << nodes[x].layout.size()) * cn.elem;
             return static_cast<const char *>(cn.leaf_dst[x].p) + code * sz;
         }
-        size_t sz = (size_t(1) << nodes[x].idx.count()) * cn.elem;
+        size_t sz = (size_t(1) << nodes[x].layout.size()) * cn.elem;
         return static_cast<const char *>(cn.arena.p) + cp.off[x] + (size_t)index[x].at(w) * sz;
     };
     cp.host_tab.clear();
@@ -333,7 +342,7 @@ int prepare_call(DevMem &mem, CNet &cn, const std::vector<uint64_t> &slices, dou
     cp.flops_all = cp.flops_beta = 0;
     for (const Step &s : cn.steps) {
         cp.tab_off.push_back(cp.host_tab.size());
-        const uint64_t Da = nodes[s.a].dep, Db = nodes[s.b].dep;
+        const uint64_t Da = nodes[s.a].dep & cn.E, Db = nodes[s.b].dep & cn.E;
         for (uint64_t w : vals[s.c]) cp.host_tab.push_back(base_of(s.a, w & Da));
         for (uint64_t w : vals[s.c]) cp.host_tab.push_back(base_of(s.b, w & Db));
         double fl = s.flops_per_version * (double)cp.nver[s.c];
@@ -342,7 +351,8 @@ int prepare_call(DevMem &mem, CNet &cn, const std::vector<uint64_t> &slices, dou
     }
     cp.root_tab = cp.host_tab.size();
     const int root = cn.tree.root;
-    for (uint64_t s : slices) cp.host_tab.push_back(base_of(root, s & nodes[root].dep));
+    for (uint64_t w : vals[root]) cp.host_tab.push_back(base_of(root, w));
+    cp.root_nver = (long long)vals[root].size();
     RC(ensure(mem, cn.tables, cp.host_tab.size() * sizeof(void *)));
     CK(cudaMemcpyAsync(cn.tables.p, cp.host_tab.data(), cp.host_tab.size() * sizeof(void *),
                        cudaMemcpyHostToDevice, mem.stream));
@@ -363,7 +373,7 @@ int launch_step(CNet &cn, const Step &s, cudaStream_t st) {
     p.nver = cp.nver[s.c];
     p.ptrB = p.ptrA + p.nver;
     p.C = static_cast<char *>(cn.arena.p) + cp.off[s.c];
-    p.c_vstride = 1LL << nodes[s.c].idx.count();
+    p.c_vstride = 1LL << nodes[s.c].layout.size();
     p.lm = s.nm;
     p.ln = s.nn;
     p.lk = s.nk;
@@ -433,20 +443,52 @@ int execute(CNet &cn, const uint64_t *d_closed, bool skip_beta_free, double2 *ou
         }
     }
     const int root = cn.tree.root;
-    long long nelem = 1LL << cn.tree.nodes[root].layout.size();
+    const int nout = (int)cn.net.out_layout.size();
+    const int nfree = (int)cn.tree.nodes[root].layout.size() - nout;
+    long long nelem = 1LL << nout;
     const void *const *rt = static_cast<const void *const *>(cn.tables.p) + cn.cp.root_tab;
     unsigned blocks = (unsigned)((nelem + 255) / 256);
-    if (cn.elem == 8) tnk::slice_sum<float2><<<blocks, 256, 0, st>>>(rt, (long long)cn.cp.slices.size(), nelem, out);
-    else tnk::slice_sum<double2><<<blocks, 256, 0, st>>>(rt, (long long)cn.cp.slices.size(), nelem, out);
+    if (cn.elem == 8) tnk::slice_sum<float2><<<blocks, 256, 0, st>>>(rt, cn.cp.root_nver, nfree, nout, out);
+    else tnk::slice_sum<double2><<<blocks, 256, 0, st>>>(rt, cn.cp.root_nver, nfree, nout, out);
     CK(cudaGetLastError());
     return TN_OK;
+}
+
+// Compile (and re-materialise the leaves) for explicit-version legs E, if not current.
+int ensure_variant(DevMem &mem, CNet &cn, uint64_t E) {
+    if (cn.compiled && cn.E == E) return TN_OK;
+    RC(tn_compile(cn.net, cn.tree, E, cn.steps));
+    cn.E = E;
+    cn.compiled = true;
+    cn.cp.valid = false;
+    return setup_leaves(mem, cn);
+}
+
+// Sliced legs whose both values appear for every slice of the set (the set is closed
+// under flipping them): those legs become layout bits, the others explicit versions.
+uint64_t explicit_legs(const std::vector<uint64_t> &slices, int nI) {
+    std::unordered_map<uint64_t, char> in;
+    in.reserve(slices.size() * 2);
+    for (uint64_t s : slices) in[s] = 1;
+    uint64_t all = nI >= 64 ? ~0ull : ((1ull << nI) - 1);
+    uint64_t fr = 0;
+    for (int b = 0; b < nI; b++) {
+        bool closed = true;
+        for (uint64_t s : slices)
+            if (!in.count(s ^ (1ull << b))) { closed = false; break; }
+        if (closed) fr |= 1ull << b;
+    }
+    return all & ~fr;
 }
 
 int build_cnet(const Merged &mg, CNet &cn, const tn_plan_opts &o, const int32_t *order, int n_order,
                DevMem &mem, int elem) {
     (void)mg;
     cn.elem = elem;
-    RC(tn_tree_and_compile(cn.net, o, order, n_order, nullptr, cn.tree, cn.steps));
+    uint64_t E0 = 0;
+    RC(tn_tree_and_compile(cn.net, o, order, n_order, nullptr, cn.tree, cn.steps, &E0));
+    cn.E = E0;
+    cn.compiled = true;
     return setup_leaves(mem, cn);
 }
 
@@ -529,11 +571,14 @@ int tn_plan(tn_circuit_h c, const int32_t *order, int32_t n_order, const tn_edge
         delete p;
         return rc;
     };
+    uint64_t E0 = 0;
     int rc = tn_plan_build_host(p->mg, o, order, n_order, sliced, n_sliced, p->open, p->I, p->amp.net,
-                                p->amp.tree, p->amp.steps, p->closed);
+                                p->amp.tree, p->amp.steps, p->closed, &E0);
     if (rc) return fail(rc);
     if (p->closed.empty()) p->log2T = 0;
     p->amp.elem = 8;
+    p->amp.E = E0;
+    p->amp.compiled = true;
     rc = setup_leaves(p->mem, p->amp);
     if (rc) return fail(rc);
     *out = p;
@@ -586,7 +631,7 @@ int tn_plan_host(tn_circuit_h c, const int32_t *order, int32_t n_order, const tn
     Network net;
     Tree tree;
     std::vector<Step> steps;
-    RC(tn_plan_build_host(mg, o, order, n_order, sliced, n_sliced, open, I, net, tree, steps, closed));
+    RC(tn_plan_build_host(mg, o, order, n_order, sliced, n_sliced, open, I, net, tree, steps, closed, nullptr));
     fill_info(mg, open, closed, o.log2_batches, I, net, tree, steps, info);
     if (steps_out)
         for (int i = 0; i < (int)steps.size() && i < cap_steps; i++) {
@@ -649,6 +694,7 @@ int tn_contract(tn_plan_h p, const uint64_t *slices, int64_t n_slices, const uin
         if (nI < 64 && sorted.back() >> nI) { tn_set_error("slice sets bits beyond the sliced edges"); return TN_EINVAL; }
     }
     cudaStream_t st = p->mem.stream;
+    RC(ensure_variant(p->mem, p->amp, explicit_legs(sl, nI)));
     RC(prepare_call(p->mem, p->amp, sl, p->budget));
     const long long T = 1LL << p->log2T;
     const int nopen = (int)p->open.size();
@@ -858,7 +904,7 @@ int tn_trace_read(tn_plan_h p, tn_step_trace *out, int32_t cap, int32_t *n_out) 
         t.flops_per_launch = s.flops_per_version * (double)nv;
         auto vbytes = [&](int x) {
             long long v = cn.cp.valid ? cn.cp.nver[x] : 1;
-            int bits = nodes[x].ch[0] < 0 ? (int)nodes[x].layout.size() : nodes[x].idx.count();
+            int bits = (int)nodes[x].layout.size();
             return 8.0 * std::ldexp(1.0, bits) * (double)v;
         };
         t.bytes_per_launch = vbytes(s.a) + vbytes(s.b) + vbytes(s.c);
@@ -879,7 +925,10 @@ int tn_sample_step(tn_plan_h p, const uint64_t *slices, int64_t n_slices, double
     }
     if (p->open.size() != 6) { tn_set_error("tn_sample_step: needs 6 open qubits"); return TN_EUNSUPPORTED; }
     std::vector<uint64_t> sl(slices, slices + n_slices);
-    RC(prepare_call(p->mem, p->amp, sl, p->budget));
+    if (!(p->amp.cp.valid && p->amp.cp.slices == sl)) {
+        RC(ensure_variant(p->mem, p->amp, explicit_legs(sl, (int)p->I.size())));
+        RC(prepare_call(p->mem, p->amp, sl, p->budget));
+    }
     cudaStream_t st = p->mem.stream;
     const long long T = 1LL << p->log2T;
     const int b_bits = (int)p->closed.size();
@@ -938,7 +987,10 @@ int tn_sample(tn_plan_h p, double f_target, int64_t N, uint64_t seed, double alp
     st_local.F = F;
     st_local.n_slices = nsl;
     cudaStream_t st = p->mem.stream;
-    RC(prepare_call(p->mem, p->amp, sl, p->budget));
+    if (!(p->amp.cp.valid && p->amp.cp.slices == sl)) {
+        RC(ensure_variant(p->mem, p->amp, explicit_legs(sl, (int)p->I.size())));
+        RC(prepare_call(p->mem, p->amp, sl, p->budget));
+    }
     const long long T = 1LL << p->log2T;
     const int b_bits = (int)p->closed.size();
     RC(ensure(p->mem, p->d_j, T * sizeof(uint64_t)));

@@ -199,16 +199,20 @@ __global__ void materialize(const MatDesc *descs, const uint64_t *closed_bits) {
 
 // ---------------------------------------------------------------- slice sum
 
-// out[e] = sum_{v in order} root_v[e], in FP64.
+// out[e] = sum over explicit root versions v (in order) and over the 2^nfree patterns f
+// of the sliced legs carried as layout bits (ascending) of root_v[(f << nout) | e], FP64.
 template <typename T>
-__global__ void slice_sum(const void *const *ptr, long long nver, long long nelem, double2 *out) {
+__global__ void slice_sum(const void *const *ptr, long long nver, int nfree, int nout, double2 *out) {
     const long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    if (e >= nelem) return;
+    if (e >= (1LL << nout)) return;
     double re = 0.0, im = 0.0;
     for (long long v = 0; v < nver; v++) {
-        const T x = static_cast<const T *>(ptr[v])[e];
-        re = __dadd_rn(re, (double)x.x);
-        im = __dadd_rn(im, (double)x.y);
+        const T *r = static_cast<const T *>(ptr[v]);
+        for (long long f = 0; f < (1LL << nfree); f++) {
+            const T x = r[(f << nout) | e];
+            re = __dadd_rn(re, (double)x.x);
+            im = __dadd_rn(im, (double)x.y);
+        }
     }
     out[e] = make_double2(re, im);
 }

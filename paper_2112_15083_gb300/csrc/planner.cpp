@@ -623,8 +623,23 @@ std::vector<int> tn_auto_slice(const Merged &mg, Network &net, Tree &t, int n_sl
 
 // ------------------------------------------------------------------ compiler
 
-int tn_compile(const Network &net, Tree &t, std::vector<Step> &steps) {
+// Layout bits of a node: its network indices plus one bit per sliced leg below it that
+// is not an explicit version (a sliced leg whose values all appear in the slice set
+// is carried like an index that is never summed until the root).
+Bits tn_node_bits(const Network &net, const Node &x, uint64_t E) {
+    Bits b = x.idx;
+    uint64_t fr = x.dep & ~E;
+    while (fr) {
+        int e = __builtin_ctzll(fr);
+        b.set(net.n_idx + e);
+        fr &= fr - 1;
+    }
+    return b;
+}
+
+int tn_compile(const Network &net, Tree &t, uint64_t E, std::vector<Step> &steps) {
     steps.clear();
+    if (net.n_idx + net.n_sliced > kMaxIdx) { tn_set_error("compile: index space too large"); return TN_EUNSUPPORTED; }
     Node &root = t.nodes[t.root];
     // the root's index set must equal the output set
     Bits outb;
@@ -634,16 +649,22 @@ int tn_compile(const Network &net, Tree &t, std::vector<Step> &steps) {
         return TN_EINVAL;
     }
     root.layout = net.out_layout;
+    for (int e = 0; e < net.n_sliced; e++)
+        if (((root.dep & ~E) >> e) & 1) root.layout.push_back(net.n_idx + e);
     for (auto &nd : t.nodes)
-        if (nd.idx.count() > 40) { tn_set_error("compile: tensor with more than 40 index bits"); return TN_EUNSUPPORTED; }
+        if (tn_node_bits(net, nd, E).count() > 40) {
+            tn_set_error("compile: tensor with more than 40 index bits");
+            return TN_EUNSUPPORTED;
+        }
     for (int ci = (int)t.nodes.size() - 1; ci >= 0; ci--) {
         Node &c = t.nodes[ci];
         if (c.ch[0] < 0) continue;
-        if (c.layout.empty() && c.idx.any()) { tn_set_error("compile: node without layout"); return TN_EINVAL; }
         int a = c.ch[0], b = c.ch[1];
-        Bits A = t.nodes[a].idx, B = t.nodes[b].idx;
-        Bits bat = A & B & c.idx, m = (A & c.idx).andnot(B), nn = (B & c.idx).andnot(A), k = (A & B).andnot(c.idx);
-        if (((A | B).andnot(c.idx | k)).any() || (c.idx.andnot(A | B)).any()) {
+        Bits Cb = tn_node_bits(net, c, E);
+        if (c.layout.empty() && Cb.any()) { tn_set_error("compile: node without layout"); return TN_EINVAL; }
+        Bits A = tn_node_bits(net, t.nodes[a], E), B = tn_node_bits(net, t.nodes[b], E);
+        Bits bat = A & B & Cb, m = (A & Cb).andnot(B), nn = (B & Cb).andnot(A), k = (A & B).andnot(Cb);
+        if (((A | B).andnot(Cb | k)).any() || (Cb.andnot(A | B)).any()) {
             tn_set_error("compile: dangling index");
             return TN_EINVAL;
         }
@@ -689,7 +710,6 @@ int tn_compile(const Network &net, Tree &t, std::vector<Step> &steps) {
         lb.insert(lb.end(), vb.begin(), vb.end());
         steps.push_back(s);
     }
-    std::reverse(steps.begin(), steps.end());  // children before parents
     std::sort(steps.begin(), steps.end(), [](const Step &x, const Step &y) { return x.c < y.c; });
     return TN_OK;
 }
@@ -697,7 +717,7 @@ int tn_compile(const Network &net, Tree &t, std::vector<Step> &steps) {
 // ------------------------------------------------------------------ whole plan
 
 int tn_tree_and_compile(const Network &net, const tn_plan_opts &o, const int32_t *order, int n_order,
-                        const Tree *candidate, Tree &tree, std::vector<Step> &steps) {
+                        const Tree *candidate, Tree &tree, std::vector<Step> &steps, uint64_t *E_used) {
     if (order) {
         int rc = tn_tree_from_ssa(net, order, n_order, tree);
         if (rc) return rc;
@@ -711,13 +731,22 @@ int tn_tree_and_compile(const Network &net, const tn_plan_opts &o, const int32_t
             if (cc.time < tc.time) tree = cand;
         }
     }
-    return tn_compile(net, tree, steps);
+    // default variant: every sliced leg as a layout bit (full slice sets); if a tensor
+    // would exceed the addressable bits, every sliced leg is an explicit version instead
+    uint64_t E = 0;
+    int rc = tn_compile(net, tree, E, steps);
+    if (rc == TN_EUNSUPPORTED && net.n_sliced > 0) {
+        E = net.n_sliced >= 64 ? ~0ull : ((1ull << net.n_sliced) - 1);
+        rc = tn_compile(net, tree, E, steps);
+    }
+    if (E_used) *E_used = E;
+    return rc;
 }
 
 int tn_plan_build_host(const Merged &mg, const tn_plan_opts &o, const int32_t *order, int n_order,
                        const tn_edge *sliced, int n_sliced, const std::vector<int> &open,
                        std::vector<tn_edge> &I, Network &net, Tree &tree, std::vector<Step> &steps,
-                       std::vector<int> &closed) {
+                       std::vector<int> &closed, uint64_t *E_used) {
     I.clear();
     Tree t0;
     bool have_t0 = false;
@@ -740,5 +769,5 @@ int tn_plan_build_host(const Merged &mg, const tn_plan_opts &o, const int32_t *o
     }
     int rc = tn_build_amp_network(mg, I, open, o.log2_batches, net, closed);
     if (rc) return rc;
-    return tn_tree_and_compile(net, o, order, n_order, have_t0 ? &t0 : nullptr, tree, steps);
+    return tn_tree_and_compile(net, o, order, n_order, have_t0 ? &t0 : nullptr, tree, steps, E_used);
 }

@@ -142,14 +142,17 @@ void tn_greedy_tree(const Network &net, uint64_t seed, int trials, Tree &best, T
 TreeCost tn_tree_cost(const Network &net, const Tree &t);
 void tn_recompute_deps(const Network &net, Tree &t);
 std::vector<int> tn_auto_slice(const Merged &mg, Network &net, Tree &t, int n_slice);
-int tn_compile(const Network &net, Tree &t, std::vector<Step> &steps);
+// Compile with explicit-version legs E (bit e = I[e]); every other sliced leg below a
+// node is one more layout bit of that node (never summed until the root).
+int tn_compile(const Network &net, Tree &t, uint64_t E, std::vector<Step> &steps);
+Bits tn_node_bits(const Network &net, const Node &x, uint64_t E);
 
 // Whole host-side planning: sliced edges (given or auto), the amplitude network, the
 // contraction tree (given SSA order or seeded greedy) and the compiled steps.
 int tn_plan_build_host(const Merged &mg, const tn_plan_opts &o, const int32_t *order, int n_order,
                        const tn_edge *sliced, int n_sliced, const std::vector<int> &open,
                        std::vector<tn_edge> &I, Network &net, Tree &tree, std::vector<Step> &steps,
-                       std::vector<int> &closed);
+                       std::vector<int> &closed, uint64_t *E_used);
 // Greedy tree of a network (or the SSA order when given) + compile.
 int tn_tree_and_compile(const Network &net, const tn_plan_opts &o, const int32_t *order, int n_order,
-                        const Tree *candidate, Tree &tree, std::vector<Step> &steps);
+                        const Tree *candidate, Tree &tree, std::vector<Step> &steps, uint64_t *E_used);
