@@ -39,6 +39,7 @@ def parse():
     ap.add_argument("--trials", type=int, default=256)
     ap.add_argument("--seed", type=int, default=2024)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--precision", default="bf16x2", choices=["c64", "bf16x2"])
     return ap.parse_args()
 
 
@@ -170,6 +171,7 @@ def workload_config(args):
                         "10 sliced legs (1024 slices); 256 batches of 64 bitstrings per step",
             "qubits": 28, "cycles": w["cycles"], "sliced_legs": w["n_sliced"], "batches_per_step": 1 << w["log2_batches"],
             "batch_size": 64, "fidelity_target": args.fidelity, "alpha": 2.0, "order_trials": args.trials,
+            "precision": getattr(args, "precision", "c64"),
             "l2": "flushed between timed steps; dominant operands exceed L2"}
 
 
@@ -191,8 +193,9 @@ def run_ours(args):
     circ = cg.sycamore_grid(w["rows"], w["cols"], w["cycles"], seed=w["seed"])
     openq = cg.default_open_qubits(w["rows"], w["cols"], w["n_open"])
     C = P.circuit_load(circ.serialize())
+    prec = {"c64": P.tn.PREC_C64, "bf16x2": P.tn.PREC_BF16X2}[args.precision]
     plan = P.plan(C, openq, n_auto_sliced=w["n_sliced"], log2_batches=w["log2_batches"], order_trials=args.trials,
-                  order_seed=0, hbm_budget_bytes=200e9)
+                  order_seed=0, hbm_budget_bytes=200e9, precision=prec)
     info = plan.info()
     slices, F = plan.select(args.fidelity)
     T = 1 << w["log2_batches"]
@@ -242,14 +245,24 @@ def run_ours(args):
     dom = max(trace, key=lambda s: s["ms"])
     dom_ms = dom["ms"] / max(1, dom["launches"])
     pk = peaks()
-    ffma_peak = 152 * 128 * 2 * 2.07e9 / 1e12
-    roofline = {"bound": "alu", "achieved": dom["flops_per_launch"] / (dom_ms / 1e3) / 1e12, "peak": ffma_peak,
-                "unit": "TFLOP/s", "traffic": None}
-    roofline["frac"] = roofline["achieved"] / roofline["peak"]
-    roofline["kernel"] = "cgemm_tile %d (bat,m,n,k bits = %d,%d,%d,%d; %d versions)" % (
-        dom["kernel"], dom["nbat"], dom["nm"], dom["nn"], dom["nk"], dom["nver"])
+    alg = dom["flops_per_launch"] / (dom_ms / 1e3) / 1e12
+    if dom["kernel"] == 9128:
+        # tensor-core step: algorithmic complex FLOPs (8 per complex MAC) against the
+        # measured dense bf16 peak; the split path issues 3x that on the tensor pipe
+        peak = pk.get("bf16_tflops", 1900.0)
+        roofline = {"bound": "tensor", "achieved": alg, "peak": peak, "unit": "TFLOP/s", "traffic": None,
+                    "frac": alg / peak, "tensor_pipe_tflops": 3 * alg, "tensor_pipe_frac": 3 * alg / peak,
+                    "peak_source": "measured bf16 dense burst (MEASURED_PEAKS.json)" if "bf16_tflops" in pk
+                    else "fallback 1.9 PFLOP/s",
+                    "kernel": "tc_cgemm<128,3> split bf16 hi+lo (bat,m,n,k bits = %d,%d,%d,%d)" % (
+                        dom["nbat"], dom["nm"], dom["nn"], dom["nk"])}
+    else:
+        ffma_peak = 152 * 128 * 2 * 2.07e9 / 1e12
+        roofline = {"bound": "alu", "achieved": alg, "peak": ffma_peak, "unit": "TFLOP/s", "traffic": None,
+                    "frac": alg / ffma_peak, "peak_source": "derived: " + FFMA_PEAK_NOTE + " (FP32 FFMA, complex64 path)",
+                    "kernel": "cgemm_tile %d (bat,m,n,k bits = %d,%d,%d,%d)" % (
+                        dom["kernel"], dom["nbat"], dom["nm"], dom["nn"], dom["nk"])}
     roofline["share_of_step"] = dom["ms"] / max(1e-9, sum(s["ms"] for s in trace))
-    roofline["peak_source"] = "derived: " + FFMA_PEAK_NOTE + " (FP32 FFMA, complex64 path)"
     top_steps = []
     for s in sorted(trace, key=lambda s: -s["ms"])[:6]:
         ms1 = s["ms"] / max(1, s["launches"])
@@ -288,7 +301,9 @@ def run_ours(args):
         line = {
             "metric": METRIC, "value": value, "unit": "samples/s", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": tot_ms_max / args.steps, "higher_is_better": True,
-            "scaling": "weak", "vs_baseline": None, "dtype": "c64 (fp32 FFMA), fp64 slice sum/sampler",
+            "scaling": "weak", "vs_baseline": None,
+            "dtype": ("bf16x2 split hi+lo on tcgen05, fp32 accumulation (small steps c64 FFMA); fp64 slice sum/sampler"
+                      if args.precision == "bf16x2" else "c64 (fp32 FFMA), fp64 slice sum/sampler"),
             "data": "synthetic", "config": workload_config(args),
             "fidelity": F, "contraction_tflops": flops_step * args.steps / (tot_ms / 1e3) / 1e12,
             "flops_per_step": flops_step, "plan": info, "clocks": clk, "roofline": roofline,

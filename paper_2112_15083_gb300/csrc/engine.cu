@@ -13,7 +13,10 @@
 #include <numeric>
 #include <unordered_map>
 
+#include <cudaTypedefs.h>
+
 #include "kernels.cuh"
+#include "tc.cuh"
 #include "tn_internal.h"
 
 namespace {
@@ -95,6 +98,8 @@ struct CallPlan {
     size_t arena_bytes = 0;
     double flops_all = 0, flops_beta = 0;      // per execution (all steps / beta steps)
     long long root_nver = 0;                   // explicit root versions (slice sum outer loop)
+    std::vector<size_t> map_off;               // per step: first tensor map (2 per version)
+    std::vector<CUtensorMap> maps;
     bool valid = false;
 };
 
@@ -104,6 +109,12 @@ struct CNet {
     std::vector<Step> steps;
     uint64_t E = 0;            // explicit-version sliced legs of the compiled variant
     bool compiled = false;
+    int prec = TN_PREC_C64;    // precision mode of the tensor-core steps
+    std::vector<int> fmt;      // per node: storage format (tnk::OutFmt)
+    std::vector<float> scale;  // per node: stored value = true value * scale
+    std::vector<char> use_tc;  // per step: tcgen05 kernel
+    DBuf err;                  // device error word of the bounded waits
+    int *d_err = nullptr;
     int elem = 8;  // 8: complex64, 16: complex128
     std::vector<DBuf> leaf_src, leaf_dst;
     std::vector<int> leaf_codebits;
@@ -147,8 +158,84 @@ struct tn_plan_s {
 
 namespace {
 
+int num_sms() {
+    static int n = 0;
+    if (!n) {
+        int dev = 0;
+        cudaGetDevice(&dev);
+        if (cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || n <= 0) n = 148;
+    }
+    return n;
+}
+
+// Tensor-core eligibility of a step: K >= 16 (TMA row pitch >= 32 B, one MMA K step)
+// and both output dimensions >= 64 (the tile is 128 x 128).
+bool tc_step(const Step &s) { return tn_tc_shape(s.nm, s.nn, s.nk); }
+
+// Storage format of every node = what its consumer reads.
+void assign_formats(CNet &cn) {
+    const int NN = (int)cn.tree.nodes.size();
+    cn.fmt.assign(NN, tnk::OUT_C64);
+    cn.scale.assign(NN, 1.0f);
+    cn.use_tc.assign(cn.steps.size(), 0);
+    if (cn.elem != 8 || cn.prec == TN_PREC_C64) return;
+    const int split = cn.prec == TN_PREC_FP16X2 ? tnk::OUT_SPLIT_FP16 : tnk::OUT_SPLIT_BF16;
+    for (size_t i = 0; i < cn.steps.size(); i++) {
+        const Step &s = cn.steps[i];
+        if (!tc_step(s)) continue;
+        cn.use_tc[i] = 1;
+        cn.fmt[s.a] = split;
+        cn.fmt[s.b] = split;
+    }
+}
+
+PFN_cuTensorMapEncodeTiled_v12000 g_encode = nullptr;
+
+int get_encoder() {
+    if (g_encode) return TN_OK;
+    cudaDriverEntryPointQueryResult q;
+    void *fn = nullptr;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000, cudaEnableDefault, &q) != cudaSuccess ||
+        !fn) {
+        tn_set_error("cuTensorMapEncodeTiled is not available from the driver");
+        return TN_EDEVICE;
+    }
+    g_encode = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(fn);
+    return TN_OK;
+}
+
+// 3-D map of a split operand: [4 * BAT planes][rows][K] of 2-byte elements, tiles of
+// 32 (K) x 128 rows, 64-byte swizzle; out-of-range rows/columns read as zero.
+int encode_operand(CUtensorMap *m, const void *base, int lk, int lrows, int lbat, bool fp16) {
+    RC(get_encoder());
+    cuuint64_t dims[3] = {(cuuint64_t)1 << lk, (cuuint64_t)1 << lrows, (cuuint64_t)4 << lbat};
+    cuuint64_t strides[2] = {((cuuint64_t)1 << lk) * 2, ((cuuint64_t)1 << (lk + lrows)) * 2};
+    cuuint32_t box[3] = {(cuuint32_t)tnk::kTcBK, 128, 1};
+    cuuint32_t es[3] = {1, 1, 1};
+    CUresult r = g_encode(m, fp16 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT16 : CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 3,
+                          const_cast<void *>(base), dims, strides, box, es, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                          CU_TENSOR_MAP_SWIZZLE_64B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                          CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    if (r != CUDA_SUCCESS) {
+        tn_set_error("cuTensorMapEncodeTiled failed (" + std::to_string((int)r) + ")");
+        return TN_EDEVICE;
+    }
+    return TN_OK;
+}
+
 int setup_leaves(DevMem &mem, CNet &cn) {
     const int L = (int)cn.net.leaves.size();
+    if (!cn.err.p) {
+        RC(ensure(mem, cn.err, sizeof(int)));
+        CK(cudaMemsetAsync(cn.err.p, 0, sizeof(int), mem.stream));
+        cn.d_err = static_cast<int *>(cn.err.p);
+    }
+    static bool smem_set = false;
+    if (!smem_set) {
+        CK(cudaFuncSetAttribute(tnk::tc_cgemm<128, 3>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                tnk::TcSmem<128, 3>::kBytes));
+        smem_set = true;
+    }
     for (auto &b : cn.leaf_src) release(mem, b);
     for (auto &b : cn.leaf_dst) release(mem, b);
     cn.leaf_src.assign(L, DBuf());
@@ -200,6 +287,8 @@ int setup_leaves(DevMem &mem, CNet &cn) {
         cn.leaf_bytes += dst_bytes + src_bytes;
         d.src = static_cast<const double2 *>(cn.leaf_src[i].p);
         d.dst = cn.leaf_dst[i].p;
+        d.fmt = cn.elem == 8 ? cn.fmt[i] : tnk::OUT_C64;
+        d.scale = cn.scale[i];
         if (cl.empty()) static_descs.push_back(d);
         else cn.beta_descs.push_back(d);
     }
@@ -236,6 +325,8 @@ void free_cnet(DevMem &mem, CNet &cn) {
     release(mem, cn.d_beta_descs);
     release(mem, cn.arena);
     release(mem, cn.tables);
+    release(mem, cn.err);
+    cn.d_err = nullptr;
     for (auto &x : cn.ev) cudaEventDestroy(x);
     cn.ev.clear();
 }
@@ -353,6 +444,23 @@ int prepare_call(DevMem &mem, CNet &cn, const std::vector<uint64_t> &slices, dou
     const int root = cn.tree.root;
     for (uint64_t w : vals[root]) cp.host_tab.push_back(base_of(root, w));
     cp.root_nver = (long long)vals[root].size();
+    // tensor maps of the tensor-core steps (A and B of every explicit version)
+    cp.map_off.assign(cn.steps.size(), 0);
+    cp.maps.clear();
+    for (size_t i = 0; i < cn.steps.size(); i++) {
+        if (cn.use_tc.empty() || !cn.use_tc[i]) continue;
+        const Step &s = cn.steps[i];
+        cp.map_off[i] = cp.maps.size();
+        const long long nv = cp.nver[s.c];
+        const bool f16 = cn.fmt[s.a] == tnk::OUT_SPLIT_FP16;
+        for (long long v = 0; v < nv; v++) {
+            CUtensorMap ma, mb;
+            RC(encode_operand(&ma, cp.host_tab[cp.tab_off[i] + v], s.nk, s.nm, s.nbat, f16));
+            RC(encode_operand(&mb, cp.host_tab[cp.tab_off[i] + nv + v], s.nk, s.nn, s.nbat, f16));
+            cp.maps.push_back(ma);
+            cp.maps.push_back(mb);
+        }
+    }
     RC(ensure(mem, cn.tables, cp.host_tab.size() * sizeof(void *)));
     CK(cudaMemcpyAsync(cn.tables.p, cp.host_tab.data(), cp.host_tab.size() * sizeof(void *),
                        cudaMemcpyHostToDevice, mem.stream));
@@ -383,6 +491,38 @@ int launch_step(CNet &cn, const Step &s, cudaStream_t st) {
     for (int i = 0; i < s.nm; i++) p.pos_m[i] = s.pos_m[i];
     for (int i = 0; i < s.nn; i++) p.pos_n[i] = s.pos_n[i];
     const size_t si = &s - cn.steps.data();
+    p.out_fmt = cn.fmt[s.c];
+    p.out_scale = cn.scale[s.c] / (cn.scale[s.a] * cn.scale[s.b]);
+    if constexpr (sizeof(T) == sizeof(float2)) {
+        if (!cn.use_tc.empty() && cn.use_tc[si]) {
+            if (cn.trace) cn.tr_kernel[si] = 9128;
+            tnk::TcParams tp;
+            std::memset(&tp, 0, sizeof(tp));
+            tp.lm = s.nm;
+            tp.ln = s.nn;
+            tp.lk = s.nk;
+            tp.lbat = s.nbat;
+            tp.out_fmt = p.out_fmt;
+            tp.in_fp16 = cn.fmt[s.a] == tnk::OUT_SPLIT_FP16;
+            tp.out_scale = p.out_scale;
+            tp.err = cn.d_err;
+            tp.c_plane = p.c_vstride;
+            for (int i = 0; i < s.nbat; i++) tp.pos_bat[i] = s.pos_bat[i];
+            for (int i = 0; i < s.nm; i++) tp.pos_m[i] = s.pos_m[i];
+            for (int i = 0; i < s.nn; i++) tp.pos_n[i] = s.pos_n[i];
+            using Lay = tnk::TcSmem<128, 3>;
+            const int ltm = std::min(s.nm, 7), ltn = std::min(s.nn, 7);
+            const long long tiles = 1LL << (s.nbat + (s.nm - ltm) + (s.nn - ltn));
+            const long long blocks = std::min<long long>(tiles, num_sms());
+            for (long long v = 0; v < p.nver; v++) {
+                tp.C = static_cast<char *>(p.C) + v * p.c_vstride * 8;
+                const CUtensorMap *m = &cp.maps[cp.map_off[si] + 2 * v];
+                tnk::tc_cgemm<128, 3><<<(unsigned)blocks, tnk::kTcThreads, Lay::kBytes, st>>>(m[0], m[1], tp);
+            }
+            CK(cudaGetLastError());
+            return TN_OK;
+        }
+    }
     if (s.nn <= 4 && s.nk <= 6) {
         if (cn.trace) cn.tr_kernel[si] = 0;
         long long rows = p.nver << (p.lbat + p.lm);
@@ -457,10 +597,11 @@ int execute(CNet &cn, const uint64_t *d_closed, bool skip_beta_free, double2 *ou
 // Compile (and re-materialise the leaves) for explicit-version legs E, if not current.
 int ensure_variant(DevMem &mem, CNet &cn, uint64_t E) {
     if (cn.compiled && cn.E == E) return TN_OK;
-    RC(tn_compile(cn.net, cn.tree, E, cn.steps));
+    RC(tn_compile(cn.net, cn.tree, E, cn.steps, cn.elem == 8 && cn.prec != TN_PREC_C64));
     cn.E = E;
     cn.compiled = true;
     cn.cp.valid = false;
+    assign_formats(cn);
     return setup_leaves(mem, cn);
 }
 
@@ -481,6 +622,20 @@ uint64_t explicit_legs(const std::vector<uint64_t> &slices, int nI) {
     return all & ~fr;
 }
 
+// After a synchronising call: a bounded device wait that gave up is reported once.
+int check_err(CNet &cn, cudaStream_t st) {
+    if (!cn.d_err) return TN_OK;
+    int h = 0;
+    CK(cudaMemcpyAsync(&h, cn.d_err, sizeof(int), cudaMemcpyDeviceToHost, st));
+    CK(cudaStreamSynchronize(st));
+    if (h) {
+        CK(cudaMemsetAsync(cn.d_err, 0, sizeof(int), st));
+        tn_set_error("a bounded device-side wait gave up (tensor-core step)");
+        return TN_ETIMEOUT;
+    }
+    return TN_OK;
+}
+
 int build_cnet(const Merged &mg, CNet &cn, const tn_plan_opts &o, const int32_t *order, int n_order,
                DevMem &mem, int elem) {
     (void)mg;
@@ -489,6 +644,7 @@ int build_cnet(const Merged &mg, CNet &cn, const tn_plan_opts &o, const int32_t 
     RC(tn_tree_and_compile(cn.net, o, order, n_order, nullptr, cn.tree, cn.steps, &E0));
     cn.E = E0;
     cn.compiled = true;
+    assign_formats(cn);
     return setup_leaves(mem, cn);
 }
 
@@ -546,9 +702,10 @@ int tn_plan(tn_circuit_h c, const int32_t *order, int32_t n_order, const tn_edge
     if (opts) o = *opts;
     else tn_plan_opts_default(&o);
     if (o.log2_batches < 0 || o.log2_batches > 16) { tn_set_error("log2_batches must be in [0,16]"); return TN_EINVAL; }
-    if (o.precision != TN_PREC_C64) {
-        tn_set_error("tn_plan: this build implements the complex64 path only");
-        return TN_EUNSUPPORTED;
+    if (o.precision != TN_PREC_C64 && o.precision != TN_PREC_BF16X2) {
+        tn_set_error(o.precision == TN_PREC_FP16X2 ? "tn_plan: the fp16 split path is not built yet"
+                                                    : "tn_plan: unknown precision");
+        return o.precision == TN_PREC_FP16X2 ? TN_EUNSUPPORTED : TN_EINVAL;
     }
     if (sliced && (n_sliced < 0 || n_sliced > 62)) { tn_set_error("n_sliced must be in [0,62]"); return TN_EINVAL; }
     if (!sliced && (o.n_auto_sliced < 0 || o.n_auto_sliced > 62)) { tn_set_error("n_auto_sliced in [0,62]"); return TN_EINVAL; }
@@ -579,6 +736,8 @@ int tn_plan(tn_circuit_h c, const int32_t *order, int32_t n_order, const tn_edge
     p->amp.elem = 8;
     p->amp.E = E0;
     p->amp.compiled = true;
+    p->amp.prec = o.precision;
+    assign_formats(p->amp);
     rc = setup_leaves(p->mem, p->amp);
     if (rc) return fail(rc);
     *out = p;
@@ -713,7 +872,7 @@ int tn_contract(tn_plan_h p, const uint64_t *slices, int64_t n_slices, const uin
                            dev ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, st));
     }
     CK(cudaStreamSynchronize(st));
-    return TN_OK;
+    return check_err(p->amp, st);
 }
 
 int tn_partial_norms(tn_plan_h p, double f, int32_t *s_index, int32_t *k_out, double *R, int64_t cap_R) {
@@ -966,6 +1125,7 @@ int tn_sample_step(tn_plan_h p, const uint64_t *slices, int64_t n_slices, double
         CK(cudaMemcpyAsync(accept, p->d_acc.p, T, cudaMemcpyDeviceToHost, st));
         CK(cudaMemcpyAsync(bits, p->d_bits.p, T * sizeof(uint64_t), cudaMemcpyDeviceToHost, st));
         CK(cudaStreamSynchronize(st));
+        RC(check_err(p->amp, st));
     }
     return TN_OK;
 }
@@ -1058,6 +1218,7 @@ int tn_sample(tn_plan_h p, double f_target, int64_t N, uint64_t seed, double alp
         std::copy(result.begin(), result.end(), bitstrings);
     }
     if (stats) *stats = st_local;
+    RC(check_err(p->amp, st));
     if ((int64_t)result.size() < N) {
         tn_set_error("tn_sample: step limit reached before N accepted samples");
         return TN_EINVAL;

@@ -14,6 +14,8 @@
 //    (Sec. II.A), one warp per batch of 64.
 #pragma once
 
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -21,15 +23,60 @@ namespace tnk {
 
 constexpr int kMaxBits = 40;
 
+// Storage formats of a tensor (chosen by the kernel that reads it): interleaved
+// complex64, or four planes (re_hi, re_lo, im_hi, im_lo) of bf16 / fp16 with x = hi + lo,
+// plane stride = the tensor's element count.  Both use 8 bytes per element.
+enum OutFmt { OUT_C64 = 0, OUT_SPLIT_BF16 = 1, OUT_SPLIT_FP16 = 2 };
+
 struct GemmParams {
     const void *const *ptrA;  // per C-version operand base
     const void *const *ptrB;
-    void *C;                  // C base (version v at C + v * c_vstride)
+    void *C;                  // C base (version v at C + v * c_vstride elements)
     long long c_vstride;      // elements
     long long nver;
     int lm, ln, lk, lbat;     // log2 of M, N, K, BAT
+    int out_fmt;              // OutFmt of C
+    float out_scale;          // multiplier applied before storing
     int8_t pos_bat[kMaxBits], pos_m[kMaxBits], pos_n[kMaxBits];
 };
+
+// Split x into hi + lo in the operand type and store both parts at plane stride.
+__device__ __forceinline__ void store_split(void *base, long long plane, long long off, float2 x, bool fp16) {
+    if (fp16) {
+        __half *h = static_cast<__half *>(base);
+        const __half rh = __float2half_rn(x.x), ih = __float2half_rn(x.y);
+        h[off] = rh;
+        h[plane + off] = __float2half_rn(x.x - __half2float(rh));
+        h[2 * plane + off] = ih;
+        h[3 * plane + off] = __float2half_rn(x.y - __half2float(ih));
+    } else {
+        __nv_bfloat16 *h = static_cast<__nv_bfloat16 *>(base);
+        const __nv_bfloat16 rh = __float2bfloat16_rn(x.x), ih = __float2bfloat16_rn(x.y);
+        h[off] = rh;
+        h[plane + off] = __float2bfloat16_rn(x.x - __bfloat162float(rh));
+        h[2 * plane + off] = ih;
+        h[3 * plane + off] = __float2bfloat16_rn(x.y - __bfloat162float(ih));
+    }
+}
+
+// Store one complex64 result of version v in C's format.
+__device__ __forceinline__ void store_c(const GemmParams &p, long long v, long long off, float2 x) {
+    x.x *= p.out_scale;
+    x.y *= p.out_scale;
+    if (p.out_fmt == OUT_C64) {
+        static_cast<float2 *>(p.C)[v * p.c_vstride + off] = x;
+    } else {
+        unsigned short *base = static_cast<unsigned short *>(p.C) + 4 * v * p.c_vstride;
+        store_split(base, p.c_vstride, off, x, p.out_fmt == OUT_SPLIT_FP16);
+    }
+}
+template <typename T> __device__ __forceinline__ void store_c_t(const GemmParams &p, long long v, long long off, T x);
+template <> __device__ __forceinline__ void store_c_t<float2>(const GemmParams &p, long long v, long long off, float2 x) {
+    store_c(p, v, off, x);
+}
+template <> __device__ __forceinline__ void store_c_t<double2>(const GemmParams &p, long long v, long long off, double2 x) {
+    static_cast<double2 *>(p.C)[v * p.c_vstride + off] = x;
+}
 
 __device__ __forceinline__ long long scatter_bits(long long x, const int8_t *pos, int nbits) {
     long long off = 0;
@@ -78,10 +125,9 @@ __global__ void __launch_bounds__(256) cgemm_row(GemmParams p) {
 #pragma unroll
         for (int n = 0; n < N; n++) acc[n] = cfma(a, __ldg(&B[(n << p.lk) + k]), acc[n]);
     }
-    T *C = static_cast<T *>(p.C) + v * p.c_vstride + scatter_bits(bat, p.pos_bat, p.lbat) +
-           scatter_bits(m, p.pos_m, p.lm);
+    const long long cb = scatter_bits(bat, p.pos_bat, p.lbat) + scatter_bits(m, p.pos_m, p.lm);
 #pragma unroll
-    for (int n = 0; n < N; n++) C[scatter_bits(n, p.pos_n, p.ln)] = acc[n];
+    for (int n = 0; n < N; n++) store_c_t<T>(p, v, cb + scatter_bits(n, p.pos_n, p.ln), acc[n]);
 }
 
 // Shared-memory tiled kernel: TM x TN output tile, K in chunks of TK, each thread an
@@ -140,7 +186,7 @@ __global__ void __launch_bounds__((TM / RM) * (TN / RN)) cgemm_tile(GemmParams p
         }
         __syncthreads();
     }
-    T *C = static_cast<T *>(p.C) + v * p.c_vstride + scatter_bits(bat, p.pos_bat, p.lbat);
+    const long long cb = scatter_bits(bat, p.pos_bat, p.lbat);
     long long offn[RN];
 #pragma unroll
     for (int j = 0; j < RN; j++) offn[j] = scatter_bits(n0 + tx + j * NTX, p.pos_n, p.ln);
@@ -148,10 +194,10 @@ __global__ void __launch_bounds__((TM / RM) * (TN / RN)) cgemm_tile(GemmParams p
     for (int i = 0; i < RM; i++) {
         const int r = ty * RM + i;
         if (r >= mrows) continue;
-        const long long offm = scatter_bits(m0 + r, p.pos_m, p.lm);
+        const long long offm = cb + scatter_bits(m0 + r, p.pos_m, p.lm);
 #pragma unroll
         for (int j = 0; j < RN; j++)
-            if (tx + j * NTX < ncols) C[offm + offn[j]] = acc[i][j];
+            if (tx + j * NTX < ncols) store_c_t<T>(p, v, offm + offn[j], acc[i][j]);
     }
 }
 
@@ -159,7 +205,9 @@ __global__ void __launch_bounds__((TM / RM) * (TN / RN)) cgemm_tile(GemmParams p
 
 struct MatDesc {
     const double2 *src;  // full leaf tensor, data index = sum_t value(leg t) << t
-    void *dst;           // [code][2^nd] in the consumer's layout
+    void *dst;           // [code][2^nd] in the consumer's layout and format
+    int fmt;             // OutFmt (complex64 leaves only; complex128 when T = double2)
+    float scale;         // multiplier (split fp16 range scaling)
     int nd;              // destination bits
     int ncode_bits;      // sliced legs of the leaf
     int ncl;             // closed legs
@@ -191,9 +239,18 @@ __global__ void materialize(const MatDesc *descs, const uint64_t *closed_bits) {
             for (int c = 0; c < d.ncl; c++) src |= (long long)((pat >> d.cl_ref[c]) & 1) << d.cl_leg[c];
         }
         const double2 x = d.src[src];
-        T *out = static_cast<T *>(d.dst);
-        if constexpr (sizeof(T) == sizeof(float2)) out[g] = make_float2((float)x.x, (float)x.y);
-        else out[g] = x;
+        if constexpr (sizeof(T) == sizeof(float2)) {
+            const float2 y = make_float2((float)(x.x * d.scale), (float)(x.y * d.scale));
+            if (d.fmt == OUT_C64) {
+                static_cast<float2 *>(d.dst)[g] = y;
+            } else {
+                const long long ne = 1LL << d.nd;
+                unsigned short *base = static_cast<unsigned short *>(d.dst) + 4 * code * ne;
+                store_split(base, ne, e, y, d.fmt == OUT_SPLIT_FP16);
+            }
+        } else {
+            static_cast<T *>(d.dst)[g] = x;
+        }
     }
 }
 

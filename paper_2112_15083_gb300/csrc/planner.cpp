@@ -637,7 +637,7 @@ Bits tn_node_bits(const Network &net, const Node &x, uint64_t E) {
     return b;
 }
 
-int tn_compile(const Network &net, Tree &t, uint64_t E, std::vector<Step> &steps) {
+int tn_compile(const Network &net, Tree &t, uint64_t E, std::vector<Step> &steps, bool tc_roles) {
     steps.clear();
     if (net.n_idx + net.n_sliced > kMaxIdx) { tn_set_error("compile: index space too large"); return TN_EUNSUPPORTED; }
     Node &root = t.nodes[t.root];
@@ -668,10 +668,18 @@ int tn_compile(const Network &net, Tree &t, uint64_t E, std::vector<Step> &steps
             tn_set_error("compile: dangling index");
             return TN_EINVAL;
         }
-        // the operand holding C's lowest m/n bit becomes the column operand (coalesced stores)
-        for (int id : c.layout) {
-            if (m.has(id)) { std::swap(a, b); std::swap(m, nn); break; }
-            if (nn.has(id)) break;
+        // the operand holding most of C's lowest layout positions takes the side the
+        // epilogue walks across threads (consecutive threads -> consecutive addresses):
+        // columns for the FFMA kernels, rows for the tensor-core kernel
+        const bool rows_side = tc_roles && tn_tc_shape(m.count(), nn.count(), k.count());
+        {
+            int cm = 0, cn = 0, first = 0;
+            for (size_t q = 0; q < c.layout.size() && q < 5; q++) {
+                if (m.has(c.layout[q])) { cm++; if (!first) first = 1; }
+                if (nn.has(c.layout[q])) { cn++; if (!first) first = 2; }
+            }
+            const bool m_low = cm > cn || (cm == cn && first == 1);
+            if (m_low != rows_side) { std::swap(a, b); std::swap(m, nn); }
         }
         auto in_c_order = [&](const Bits &s) {
             std::vector<int> v;
@@ -680,6 +688,32 @@ int tn_compile(const Network &net, Tree &t, uint64_t E, std::vector<Step> &steps
             return v;
         };
         std::vector<int> vb = in_c_order(bat), vm = in_c_order(m), vn = in_c_order(nn), vk = k.list();
+        // k bits are the lowest layout bits of both operands: group them by the child of
+        // the larger internal operand they come from (larger group first), so that
+        // operand's producer writes long contiguous runs along one of its sides
+        {
+            int x = -1;
+            double best = -1;
+            for (int o : {a, b})
+                if (t.nodes[o].ch[0] >= 0) {
+                    double sz = std::ldexp(1.0, tn_node_bits(net, t.nodes[o], E).count());
+                    if (sz > best) { best = sz; x = o; }
+                }
+            if (x >= 0) {
+                Bits X1 = tn_node_bits(net, t.nodes[t.nodes[x].ch[0]], E), X2 = tn_node_bits(net, t.nodes[t.nodes[x].ch[1]], E);
+                std::vector<int> g1, g2, g3;
+                for (int id : vk) {
+                    if (X1.has(id) && !X2.has(id)) g1.push_back(id);
+                    else if (X2.has(id) && !X1.has(id)) g2.push_back(id);
+                    else g3.push_back(id);
+                }
+                if (g2.size() > g1.size()) std::swap(g1, g2);
+                vk.clear();
+                vk.insert(vk.end(), g1.begin(), g1.end());
+                vk.insert(vk.end(), g2.begin(), g2.end());
+                vk.insert(vk.end(), g3.begin(), g3.end());
+            }
+        }
         auto pos_in_c = [&](int id) {
             for (size_t p = 0; p < c.layout.size(); p++)
                 if (c.layout[p] == id) return (int)p;
@@ -717,7 +751,8 @@ int tn_compile(const Network &net, Tree &t, uint64_t E, std::vector<Step> &steps
 // ------------------------------------------------------------------ whole plan
 
 int tn_tree_and_compile(const Network &net, const tn_plan_opts &o, const int32_t *order, int n_order,
-                        const Tree *candidate, Tree &tree, std::vector<Step> &steps, uint64_t *E_used) {
+                        const Tree *candidate, Tree &tree, std::vector<Step> &steps, uint64_t *E_used,
+                        bool tc_roles) {
     if (order) {
         int rc = tn_tree_from_ssa(net, order, n_order, tree);
         if (rc) return rc;
@@ -734,10 +769,10 @@ int tn_tree_and_compile(const Network &net, const tn_plan_opts &o, const int32_t
     // default variant: every sliced leg as a layout bit (full slice sets); if a tensor
     // would exceed the addressable bits, every sliced leg is an explicit version instead
     uint64_t E = 0;
-    int rc = tn_compile(net, tree, E, steps);
+    int rc = tn_compile(net, tree, E, steps, tc_roles);
     if (rc == TN_EUNSUPPORTED && net.n_sliced > 0) {
         E = net.n_sliced >= 64 ? ~0ull : ((1ull << net.n_sliced) - 1);
-        rc = tn_compile(net, tree, E, steps);
+        rc = tn_compile(net, tree, E, steps, tc_roles);
     }
     if (E_used) *E_used = E;
     return rc;
@@ -769,5 +804,6 @@ int tn_plan_build_host(const Merged &mg, const tn_plan_opts &o, const int32_t *o
     }
     int rc = tn_build_amp_network(mg, I, open, o.log2_batches, net, closed);
     if (rc) return rc;
-    return tn_tree_and_compile(net, o, order, n_order, have_t0 ? &t0 : nullptr, tree, steps, E_used);
+    return tn_tree_and_compile(net, o, order, n_order, have_t0 ? &t0 : nullptr, tree, steps, E_used,
+                               o.precision != TN_PREC_C64);
 }

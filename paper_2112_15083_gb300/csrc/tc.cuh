@@ -1,0 +1,350 @@
+// tcgen05 split-precision complex GEMM (sm_103a) for the contraction steps.
+//
+// C[bat][m][n] = sum_k A[bat][m][k] * B[bat][n][k] with A and B stored as four planes
+// (re_hi, re_lo, im_hi, im_lo) of bf16 or fp16, plane-major: plane p of batch b is the
+// row-major [rows][K] matrix at plane index p * BAT + b.  With x = hi + lo the complex
+// product keeps hi*hi + hi*lo + lo*hi of each real product:
+//   Cr = Ar Br - Ai Bi,  Ci = Ar Bi + Ai Br,
+// i.e. 12 tensor-core MMAs per K slice accumulated in FP32 in two TMEM accumulators
+// (Cr, Ci); the subtracted products use the descriptor's negate-A bit.
+//
+// One CTA computes a 128 x BN tile: warp 0 / lane 0 streams the 8 operand plane tiles
+// of each 32-wide K slice with 3-D TMA (64-byte swizzle) into a 3-stage ring, warp 1 /
+// lane 0 issues the MMAs and releases ring slots with tcgen05.commit, and all four
+// warps read the accumulators back with tcgen05.ld (warp w owns TMEM lanes 32w..32w+31,
+// i.e. tile rows) and store in the consumer's format through the bit-scatter epilogue.
+// Every mbarrier wait is bounded: on timeout the CTA sets *err, stops, waits (bounded)
+// for work it already issued, frees its TMEM and returns.
+#pragma once
+
+#include <cuda.h>
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
+#include <stdint.h>
+
+#include "kernels.cuh"
+
+namespace tnk {
+
+constexpr int kTcBM = 128;
+constexpr int kTcBK = 32;      // K elements per ring slot (64 bytes per row: 64B swizzle)
+
+struct TcParams {
+    void *C;                 // output base (this launch's version)
+    long long c_plane;       // split output: elements per plane
+    int lm, ln, lk, lbat;
+    int out_fmt;
+    int in_fp16;             // operands are fp16 (else bf16)
+    float out_scale;         // multiply results by this before storing
+    int *err;                // set to 1 if a bounded wait gives up
+    int8_t pos_bat[kMaxBits], pos_m[kMaxBits], pos_n[kMaxBits];
+};
+
+__device__ __forceinline__ uint32_t smem_u32(const void *p) {
+    return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+
+__device__ __forceinline__ void mbar_init(uint32_t bar, uint32_t count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(count) : "memory");
+}
+
+__device__ __forceinline__ void mbar_expect_tx(uint32_t bar, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes) : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try(uint32_t bar, uint32_t parity) {
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(bar), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+
+// Bounded wait: gives up after ~limit cycles or when another role has aborted.
+__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, volatile int *abort_flag,
+                                          long long limit) {
+    const long long t0 = clock64();
+    for (int it = 0;; ++it) {
+        if (mbar_try(bar, parity)) return true;
+        if ((it & 63) == 63) {
+            if (*abort_flag) return false;
+            if (clock64() - t0 > limit) {
+                *abort_flag = 1;
+                return false;
+            }
+        }
+    }
+}
+
+// Bounded wait that ignores the abort flag (used to drain work already issued).
+__device__ __forceinline__ bool mbar_drain(uint32_t bar, uint32_t parity, long long limit) {
+    const long long t0 = clock64();
+    for (;;) {
+        if (mbar_try(bar, parity)) return true;
+        if (clock64() - t0 > limit) return false;
+    }
+}
+
+__device__ __forceinline__ void tma_load_3d(uint32_t dst, const CUtensorMap *map, int c0, int c1, int c2,
+                                            uint32_t bar) {
+    asm volatile(
+        "cp.async.bulk.tensor.3d.shared::cluster.global.tile.mbarrier::complete_tx::bytes "
+        "[%0], [%1, {%2, %3, %4}], [%5];" ::"r"(dst),
+        "l"(reinterpret_cast<uint64_t>(map)), "r"(c0), "r"(c1), "r"(c2), "r"(bar)
+        : "memory");
+}
+
+// Shared-memory matrix descriptor: K-major tile, 64-byte swizzle, 8-row groups 512 B
+// apart (rows are 64 bytes), start address advanced by 32 B per 16-element K step.
+__device__ __forceinline__ uint64_t smem_desc_sw64(uint32_t addr) {
+    uint64_t d = 0;
+    d |= (uint64_t)((addr & 0x3FFFF) >> 4);
+    d |= (uint64_t)1 << 16;            // leading byte offset (unused for swizzled K-major)
+    d |= (uint64_t)(512 >> 4) << 32;   // stride byte offset: 8 rows x 64 B
+    d |= (uint64_t)1 << 46;            // descriptor version
+    d |= (uint64_t)4 << 61;            // 64-byte swizzle
+    return d;
+}
+
+// Instruction descriptor, kind::f16: D = F32, A/B = BF16 (1) or F16 (0), K-major both,
+// N >> 3 at bit 17, M >> 4 at bit 24, optional negation of A.
+__device__ __forceinline__ uint32_t idesc_f16(int n, bool fp16, bool neg_a) {
+    uint32_t ab = fp16 ? 0u : 1u;
+    return (1u << 4) | (ab << 7) | (ab << 10) | ((neg_a ? 1u : 0u) << 13) | ((uint32_t)(n >> 3) << 17) |
+           ((uint32_t)(kTcBM >> 4) << 24);
+}
+
+__device__ __forceinline__ void mma_f16(uint32_t tmem_d, uint64_t adesc, uint64_t bdesc, uint32_t idesc,
+                                        uint32_t accumulate) {
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "setp.ne.b32 p, %4, 0;\n\t"
+        "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(tmem_d),
+        "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate)
+        : "memory");
+}
+
+__device__ __forceinline__ void mma_commit(uint32_t bar) {
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar)
+                 : "memory");
+}
+
+__device__ __forceinline__ void tmem_ld16(uint32_t taddr, float *v) {
+    uint32_t r[16];
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x16.b32 "
+        "{%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+          "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+        : "r"(taddr));
+    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+    for (int i = 0; i < 16; i++) v[i] = __uint_as_float(r[i]);
+}
+
+template <int BN, int STAGES>
+struct TcSmem {
+    static constexpr int kAPlane = kTcBM * kTcBK * 2;  // bytes per A plane tile
+    static constexpr int kBPlane = BN * kTcBK * 2;
+    static constexpr int kStage = 4 * kAPlane + 4 * kBPlane;
+    static constexpr int kBytes = STAGES * kStage + 1024 /*barriers*/ + 1024 /*alignment*/;
+};
+
+constexpr int kTcThreads = 192;  // warp 0: TMA, warp 1: MMA, warps 2-5: epilogue
+
+// Persistent kernel: CTA c processes tiles c, c + gridDim.x, ...  Tile order: N tiles
+// fastest, then M tiles, then batch (CTAs running together share the A row panel).
+// TMEM holds two accumulator pairs (Cr | Ci for BN columns each) so the epilogue of
+// one tile overlaps the MMAs of the next.
+template <int BN, int STAGES>
+__global__ void __launch_bounds__(kTcThreads, 1)
+    tc_cgemm(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB, TcParams p) {
+    using L = TcSmem<BN, STAGES>;
+    extern __shared__ unsigned char smem_raw[];
+    unsigned char *smem = reinterpret_cast<unsigned char *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+    unsigned char *ctl = smem + STAGES * L::kStage;
+    uint64_t *full = reinterpret_cast<uint64_t *>(ctl);
+    uint64_t *empty = full + STAGES;
+    uint64_t *acc_full = empty + STAGES;  // [2]: MMA -> epilogue
+    uint64_t *acc_empty = acc_full + 2;   // [2]: epilogue -> MMA
+    uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(acc_empty + 2);
+    volatile int *abort_flag = reinterpret_cast<volatile int *>(tmem_slot + 1);
+
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int ltm = min(p.lm, 7), ltn = min(p.ln, __ffs(BN) - 1);
+    const int lt_n = p.ln - ltn, lt_m = p.lm - ltm;
+    const long long ntiles = 1LL << (p.lbat + lt_m + lt_n);
+    const int BAT = 1 << p.lbat;
+    const int K = 1 << p.lk;
+    const int nkb = (K + kTcBK - 1) / kTcBK;
+    constexpr uint32_t kCols = 4 * BN;  // two accumulator pairs
+    const long long kLimit = 4000000000LL;
+
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < STAGES; s++) {
+            mbar_init(smem_u32(&full[s]), 1);
+            mbar_init(smem_u32(&empty[s]), 1);
+        }
+        for (int b = 0; b < 2; b++) {
+            mbar_init(smem_u32(&acc_full[b]), 1);
+            mbar_init(smem_u32(&acc_empty[b]), 4);  // one arrive per epilogue warp
+        }
+        *abort_flag = 0;
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    }
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tmem_slot)),
+                     "r"(kCols)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    const uint32_t tmem = *tmem_slot;
+
+    long long issued = 0;  // producer: ring slots issued
+    if (warp == 0) {
+        if (lane == 0) {
+            long long slot = 0;
+            bool ok = true;
+            for (long long t = blockIdx.x; t < ntiles && ok; t += gridDim.x) {
+                const int tn_i = (int)(t & ((1LL << lt_n) - 1));
+                const int tm_i = (int)((t >> lt_n) & ((1LL << lt_m) - 1));
+                const int bat = (int)(t >> (lt_n + lt_m));
+                for (int kb = 0; kb < nkb; kb++, slot++) {
+                    const int s = (int)(slot % STAGES);
+                    if (slot >= STAGES &&
+                        !mbar_wait(smem_u32(&empty[s]), (uint32_t)(((slot / STAGES) & 1) ^ 1), abort_flag, kLimit)) {
+                        ok = false;
+                        break;
+                    }
+                    const uint32_t fb = smem_u32(&full[s]);
+                    mbar_expect_tx(fb, L::kStage);
+                    unsigned char *st = smem + s * L::kStage;
+                    for (int pl = 0; pl < 4; pl++) {
+                        tma_load_3d(smem_u32(st + pl * L::kAPlane), &tmA, kb * kTcBK, tm_i * kTcBM, pl * BAT + bat, fb);
+                        tma_load_3d(smem_u32(st + 4 * L::kAPlane + pl * L::kBPlane), &tmB, kb * kTcBK, tn_i * BN,
+                                    pl * BAT + bat, fb);
+                    }
+                    issued = slot + 1;
+                }
+            }
+        }
+    } else if (warp == 1) {
+        if (lane == 0) {
+            // products (A plane, B plane, accumulator 0 = Cr / 1 = Ci, negate A);
+            // planes: 0 re_hi, 1 re_lo, 2 im_hi, 3 im_lo
+            const int8_t pa[12] = {0, 0, 1, 2, 2, 3, 0, 0, 1, 2, 2, 3};
+            const int8_t pb[12] = {0, 1, 0, 2, 3, 2, 2, 3, 2, 0, 1, 0};
+            const int8_t acc[12] = {0, 0, 0, 0, 0, 0, 1, 1, 1, 1, 1, 1};
+            const int8_t neg[12] = {0, 0, 0, 1, 1, 1, 0, 0, 0, 0, 0, 0};
+            const uint32_t id_pos = idesc_f16(BN, p.in_fp16, false), id_neg = idesc_f16(BN, p.in_fp16, true);
+            long long slot = 0;
+            int it = 0, last_b = -1;
+            uint32_t last_par = 0;
+            bool ok = true;
+            for (long long t = blockIdx.x; t < ntiles && ok; t += gridDim.x, it++) {
+                const int b = it & 1;
+                if (it >= 2 &&
+                    !mbar_wait(smem_u32(&acc_empty[b]), (uint32_t)(((it >> 1) & 1) ^ 1), abort_flag, kLimit)) {
+                    ok = false;
+                    break;
+                }
+                asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+                const uint32_t dcol = tmem + (uint32_t)(b * 2 * BN);
+                for (int kb = 0; kb < nkb; kb++, slot++) {
+                    const int s = (int)(slot % STAGES);
+                    if (!mbar_wait(smem_u32(&full[s]), (uint32_t)((slot / STAGES) & 1), abort_flag, kLimit)) {
+                        ok = false;
+                        break;
+                    }
+                    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+                    const uint32_t st = smem_u32(smem + s * L::kStage);
+#pragma unroll
+                    for (int kk = 0; kk < kTcBK / 16; kk++) {
+#pragma unroll
+                        for (int q = 0; q < 12; q++) {
+                            const uint64_t ad = smem_desc_sw64(st + pa[q] * L::kAPlane + kk * 32);
+                            const uint64_t bd = smem_desc_sw64(st + 4 * L::kAPlane + pb[q] * L::kBPlane + kk * 32);
+                            const uint32_t accum = (kb == 0 && kk == 0 && (q == 0 || q == 6)) ? 0u : 1u;
+                            mma_f16(dcol + (acc[q] ? BN : 0), ad, bd, neg[q] ? id_neg : id_pos, accum);
+                        }
+                    }
+                    mma_commit(smem_u32(&empty[s]));
+                }
+                mma_commit(smem_u32(&acc_full[b]));  // also after an abort: flushes issued MMAs
+                last_b = b;
+                last_par = (uint32_t)((it >> 1) & 1);
+            }
+            // after an abort, MMAs may still be running: drain them before TMEM is freed
+            if (*abort_flag && last_b >= 0) mbar_drain(smem_u32(&acc_full[last_b]), last_par, kLimit);
+        }
+    } else {
+        // epilogue warps 2..5: TMEM lane quarter = warp % 4 = tile rows 32*(warp%4)..
+        const int quarter = warp & 3;
+        const int row = 32 * quarter + lane;
+        const long long M = 1LL << p.lm, N = 1LL << p.ln;
+        // scatter(n0 + c0 + j) = scatter(n0 + c0) + scatter(j) for j < 16 (disjoint bits)
+        const int lo_bits = min(p.ln, 4);
+        long long lo[16];
+#pragma unroll
+        for (int j = 0; j < 16; j++) lo[j] = scatter_bits(j, p.pos_n, lo_bits);
+        int it = 0;
+        for (long long t = blockIdx.x; t < ntiles; t += gridDim.x, it++) {
+            const int b = it & 1;
+            if (!mbar_wait(smem_u32(&acc_full[b]), (uint32_t)((it >> 1) & 1), abort_flag, kLimit)) break;
+            asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+            const int tn_i = (int)(t & ((1LL << lt_n) - 1));
+            const int tm_i = (int)((t >> lt_n) & ((1LL << lt_m) - 1));
+            const int bat = (int)(t >> (lt_n + lt_m));
+            const long long m = (long long)tm_i * kTcBM + row;
+            const long long cbase = scatter_bits(bat, p.pos_bat, p.lbat) + (m < M ? scatter_bits(m, p.pos_m, p.lm) : 0);
+            const uint32_t lane_addr = tmem + ((uint32_t)(32 * quarter) << 16) + (uint32_t)(b * 2 * BN);
+            for (int c0 = 0; c0 < BN; c0 += 16) {
+                float re[16], im[16];
+                __syncwarp();
+                tmem_ld16(lane_addr + c0, re);
+                tmem_ld16(lane_addr + BN + c0, im);
+                const long long nb = (long long)tn_i * BN + c0;
+                if (m < M && nb < N) {
+                    const long long hi = cbase + (p.ln > 4 ? scatter_bits(nb >> 4, p.pos_n + 4, p.ln - 4) : 0);
+#pragma unroll
+                    for (int j = 0; j < 16; j++) {
+                        if (nb + j < N) {
+                            const long long off = hi + lo[j];
+                            const float2 x = make_float2(re[j] * p.out_scale, im[j] * p.out_scale);
+                            if (p.out_fmt == OUT_C64) static_cast<float2 *>(p.C)[off] = x;
+                            else store_split(p.C, p.c_plane, off, x, p.out_fmt == OUT_SPLIT_FP16);
+                        }
+                    }
+                }
+            }
+            asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+            __syncwarp();
+            if (lane == 0) asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(&acc_empty[b])) : "memory");
+        }
+    }
+    __syncwarp();
+    if (*abort_flag && threadIdx.x == 0) {
+        atomicExch(p.err, 1);
+        // let copies already issued land before the shared memory is released
+        for (long long k = 0; k < issued && k < STAGES; k++) {
+            const long long slot = issued - 1 - k;
+            mbar_drain(smem_u32(&full[slot % STAGES]), (uint32_t)((slot / STAGES) & 1), kLimit);
+        }
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    if (warp == 0) {
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(kCols) : "memory");
+    }
+}
+
+}  // namespace tnk

@@ -142,9 +142,14 @@ void tn_greedy_tree(const Network &net, uint64_t seed, int trials, Tree &best, T
 TreeCost tn_tree_cost(const Network &net, const Tree &t);
 void tn_recompute_deps(const Network &net, Tree &t);
 std::vector<int> tn_auto_slice(const Merged &mg, Network &net, Tree &t, int n_slice);
+// Shapes run on the tensor cores in the split precisions: K >= 16 and M, N >= 64.
+inline bool tn_tc_shape(int nm, int nn, int nk) { return nk >= 4 && nm >= 6 && nn >= 6; }
+
 // Compile with explicit-version legs E (bit e = I[e]); every other sliced leg below a
-// node is one more layout bit of that node (never summed until the root).
-int tn_compile(const Network &net, Tree &t, uint64_t E, std::vector<Step> &steps);
+// node is one more layout bit of that node (never summed until the root).  tc_roles:
+// tensor-core shaped steps put C's lowest layout bit on the row (M) side, since their
+// epilogue stores one row per thread; other steps put it on the column (N) side.
+int tn_compile(const Network &net, Tree &t, uint64_t E, std::vector<Step> &steps, bool tc_roles = false);
 Bits tn_node_bits(const Network &net, const Node &x, uint64_t E);
 
 // Whole host-side planning: sliced edges (given or auto), the amplitude network, the
@@ -155,4 +160,5 @@ int tn_plan_build_host(const Merged &mg, const tn_plan_opts &o, const int32_t *o
                        std::vector<int> &closed, uint64_t *E_used);
 // Greedy tree of a network (or the SSA order when given) + compile.
 int tn_tree_and_compile(const Network &net, const tn_plan_opts &o, const int32_t *order, int n_order,
-                        const Tree *candidate, Tree &tree, std::vector<Step> &steps, uint64_t *E_used);
+                        const Tree *candidate, Tree &tree, std::vector<Step> &steps, uint64_t *E_used,
+                        bool tc_roles = false);

@@ -114,6 +114,55 @@ def test_28q_256_batches_full_slice_set(grid28):
     close_c64(amps, oracle.batch_amplitudes(psi, 28, openq, cb))
 
 
+def split_errors(got, ref):
+    d = np.abs(got - ref)
+    rms = float(np.sqrt(np.mean(np.abs(ref) ** 2)))
+    rel_l2 = float(np.linalg.norm(got - ref) / np.linalg.norm(ref))
+    return {"max_over_rms": float(d.max()) / rms, "rms_err_over_rms": float(np.sqrt(np.mean(d ** 2))) / rms,
+            "rel_l2": rel_l2}
+
+
+def test_28q_bf16x2_split_full_slice_set(grid28):
+    """Split BF16 hi+lo on tcgen05 (3 products, FP32 accumulation): relative L2 <= 1e-3."""
+    P = pkg()
+    circ, psi = grid28
+    openq = cg.default_open_qubits(4, 7, 6)
+    C = P.circuit_load(circ.serialize())
+    plan = P.plan(C, openq, n_auto_sliced=10, log2_batches=8, order_trials=256, precision=P.tn.PREC_BF16X2)
+    cb = cg.random_closed_bits(256, 22, seed=1)
+    amps = plan.contract(np.arange(1024, dtype=np.uint64), cb)
+    ref = oracle.batch_amplitudes(psi, 28, openq, cb)
+    err = split_errors(amps, ref)
+    print("bf16x2 28q:", err)
+    assert err["rel_l2"] <= 1e-3, err
+    # the linear XEB of the computed distribution against the exact one (all batches)
+    p_got = np.abs(amps) ** 2
+    p_ref = np.abs(ref) ** 2
+    assert abs(np.sum(p_got * p_ref) / np.sum(p_ref * p_ref) - 1) < 2e-3
+
+
+@pytest.mark.parametrize("seed", [0, 1])
+def test_bf16x2_haar_batches_and_subsets(seed):
+    """Generic gates with the split path: big enough steps go to the tensor cores."""
+    P = pkg()
+    n = 16
+    circ = cg.random_haar(n, 150, seed=seed, p_two=0.8)
+    openq = [3, 9, 12, 1, 15, 6]
+    closed = oracle.closed_of(n, openq)
+    C = P.circuit_load(circ.serialize())
+    plan = P.plan(C, openq, n_auto_sliced=4, log2_batches=6, order_trials=16, precision=P.tn.PREC_BF16X2)
+    sl = plan.sliced_edges()
+    cb = cg.random_closed_bits(100, len(closed), seed=seed + 3)
+    psi = oracle.simulate(circ)
+    amps = plan.contract(np.arange(16, dtype=np.uint64), cb)
+    err = split_errors(amps, oracle.batch_amplitudes(psi, n, openq, cb))
+    assert err["rel_l2"] <= 1e-3, err
+    sub = np.array([3, 12, 7], dtype=np.uint64)
+    amps = plan.contract(sub, cb)
+    err = split_errors(amps, oracle.batch_amplitudes(oracle.sliced_state(circ, sl, sub), n, openq, cb))
+    assert err["rel_l2"] <= 1e-3, err
+
+
 def test_28q_single_slice_sampled(grid28):
     """One slice at full size, checked against the oracle's projector simulation."""
     P = pkg()
