@@ -24,7 +24,13 @@ import time
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
-WORKLOAD = dict(rows=4, cols=7, cycles=14, seed=0, n_sliced=10, n_open=6, log2_batches=8)
+WORKLOADS = {
+    # the measured workload: 28 qubits, 14 cycles, 2^10 slices, 256 batches of 64 per step
+    "grid4x7_m14": dict(rows=4, cols=7, cycles=14, seed=0, n_sliced=10, n_open=6, log2_batches=8),
+    # a smaller case of the same kernels (24 qubits), for detailed profiler captures
+    "grid4x6_m12": dict(rows=4, cols=6, cycles=12, seed=0, n_sliced=8, n_open=6, log2_batches=8),
+}
+WORKLOAD = WORKLOADS["grid4x7_m14"]
 METRIC = "samples/s at fixed fidelity"
 FFMA_PEAK_NOTE = "152 SMs x 128 FP32 lanes x 2 FLOP x 2070 MHz"
 
@@ -40,6 +46,7 @@ def parse():
     ap.add_argument("--seed", type=int, default=2024)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--precision", default="bf16x2", choices=["c64", "bf16x2"])
+    ap.add_argument("--workload", default="grid4x7_m14", choices=sorted(WORKLOADS))
     return ap.parse_args()
 
 
@@ -140,7 +147,7 @@ def run_reference(args):
     from paper_2112_15083_gb300 import circuits as cg
     import oracle
     oracle.lib()
-    w = WORKLOAD
+    w = WORKLOADS[args.workload]
     circ = cg.sycamore_grid(w["rows"], w["cols"], w["cycles"], seed=w["seed"])
     openq = cg.default_open_qubits(w["rows"], w["cols"], w["n_open"])
     T = 1 << w["log2_batches"]
@@ -159,17 +166,21 @@ def run_reference(args):
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
         "config": workload_config(args),
         "cpu_baseline": {"value": val, "unit": "samples/s", "cores": cores, "kind": "oracle",
-                         "sample": "per step: FP64 state vector of the 28-qubit circuit + the sampler on %d batches" % T},
+                         "sample": "per step: FP64 state vector of the %d-qubit circuit + the sampler on %d batches" % (
+                             circ.n_qubits, T)},
         "e2e": {"value": val, "unit": "samples/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line), flush=True)
 
 
 def workload_config(args):
-    w = WORKLOAD
-    return {"workload": "grid4x7_m14: 28-qubit 4x7 Sycamore-style ABCD circuit, 14 cycles, fSim(pi/2,pi/6); "
-                        "10 sliced legs (1024 slices); 256 batches of 64 bitstrings per step",
-            "qubits": 28, "cycles": w["cycles"], "sliced_legs": w["n_sliced"], "batches_per_step": 1 << w["log2_batches"],
+    w = WORKLOADS[args.workload]
+    q = w["rows"] * w["cols"]
+    return {"workload": "%s: %d-qubit %dx%d Sycamore-style ABCD circuit, %d cycles, fSim(pi/2,pi/6); "
+                        "%d sliced legs (%d slices); %d batches of 64 bitstrings per step" % (
+                            args.workload, q, w["rows"], w["cols"], w["cycles"], w["n_sliced"], 1 << w["n_sliced"],
+                            1 << w["log2_batches"]),
+            "qubits": q, "cycles": w["cycles"], "sliced_legs": w["n_sliced"], "batches_per_step": 1 << w["log2_batches"],
             "batch_size": 64, "fidelity_target": args.fidelity, "alpha": 2.0, "order_trials": args.trials,
             "precision": getattr(args, "precision", "c64"),
             "l2": "flushed between timed steps; dominant operands exceed L2"}
@@ -189,7 +200,7 @@ def run_ours(args):
     __graft_entry__.build()
     import paper_2112_15083_gb300 as P
     from paper_2112_15083_gb300 import circuits as cg
-    w = WORKLOAD
+    w = WORKLOADS[args.workload]
     circ = cg.sycamore_grid(w["rows"], w["cols"], w["cycles"], seed=w["seed"])
     openq = cg.default_open_qubits(w["rows"], w["cols"], w["n_open"])
     C = P.circuit_load(circ.serialize())
@@ -294,8 +305,8 @@ def run_ours(args):
         a = oracle_step(circ, openq, T, seed, 0)
         dt = time.perf_counter() - t
         cpu = {"value": a / dt, "unit": "samples/s", "cores": int(os.environ["OMP_NUM_THREADS"]), "kind": "oracle",
-               "sample": "one step: FP64 state vector of the 28-qubit circuit + the sampler on %d batches "
-                         "(%d accepted in %.1f s)" % (T, a, dt)}
+               "sample": "one step: FP64 state vector of the %d-qubit circuit + the sampler on %d batches "
+                         "(%d accepted in %.1f s)" % (circ.n_qubits, T, a, dt)}
 
     if rank == 0:
         line = {
