@@ -115,6 +115,10 @@ struct CNet {
     std::vector<char> use_tc;  // per step: tcgen05 kernel
     DBuf err;                  // device error word of the bounded waits
     int *d_err = nullptr;
+    // CUDA graphs of one execution (index: stem reuse off / on), valid for the current
+    // call plan and the (closed-pattern, output) buffers they were captured with
+    cudaGraphExec_t graph[2] = {nullptr, nullptr};
+    const void *graph_key[2][2] = {{nullptr, nullptr}, {nullptr, nullptr}};
     int elem = 8;  // 8: complex64, 16: complex128
     std::vector<DBuf> leaf_src, leaf_dst;
     std::vector<int> leaf_codebits;
@@ -319,7 +323,16 @@ int setup_leaves(DevMem &mem, CNet &cn) {
     return TN_OK;
 }
 
+void drop_graphs(CNet &cn) {
+    for (int i = 0; i < 2; i++)
+        if (cn.graph[i]) {
+            cudaGraphExecDestroy(cn.graph[i]);
+            cn.graph[i] = nullptr;
+        }
+}
+
 void free_cnet(DevMem &mem, CNet &cn) {
+    drop_graphs(cn);
     for (auto &b : cn.leaf_src) release(mem, b);
     for (auto &b : cn.leaf_dst) release(mem, b);
     release(mem, cn.d_beta_descs);
@@ -340,6 +353,7 @@ inline uint64_t leaf_code(uint64_t w, const std::vector<int> &sl) {
 // Versions, arena offsets and pointer tables for a slice set.
 int prepare_call(DevMem &mem, CNet &cn, const std::vector<uint64_t> &slices, double budget) {
     if (cn.cp.valid && cn.cp.slices == slices) return TN_OK;
+    drop_graphs(cn);
     CallPlan cp;
     cp.slices = slices;
     const auto &nodes = cn.tree.nodes;
@@ -594,9 +608,55 @@ int execute(CNet &cn, const uint64_t *d_closed, bool skip_beta_free, double2 *ou
     return TN_OK;
 }
 
+cudaStream_t capture_stream() {
+    static thread_local cudaStream_t s = nullptr;
+    if (!s) cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking);
+    return s;
+}
+
+// execute() through a CUDA graph: the first execution for a (call plan, buffers, stem
+// mode) is captured on an internal stream, later ones replay the graph on `st`.
+int execute_graphed(CNet &cn, const uint64_t *d_closed, bool skip_beta_free, double2 *out, cudaStream_t st) {
+    static const bool disabled = getenv("TN_NO_GRAPH") != nullptr;
+    if (cn.trace || disabled) return execute(cn, d_closed, skip_beta_free, out, st);
+    const int gi = skip_beta_free ? 1 : 0;
+    if (cn.graph[gi] && (cn.graph_key[gi][0] != d_closed || cn.graph_key[gi][1] != out)) {
+        cudaGraphExecDestroy(cn.graph[gi]);
+        cn.graph[gi] = nullptr;
+    }
+    if (!cn.graph[gi]) {
+        cudaStream_t cs = capture_stream();
+        if (!cs) return execute(cn, d_closed, skip_beta_free, out, st);
+        CK(cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal));
+        int rc = execute(cn, d_closed, skip_beta_free, out, cs);
+        cudaGraph_t g = nullptr;
+        cudaError_t ec = cudaStreamEndCapture(cs, &g);
+        if (rc) {
+            if (g) cudaGraphDestroy(g);
+            return rc;
+        }
+        if (ec != cudaSuccess || !g) {
+            tn_set_error(std::string("graph capture failed: ") + cudaGetErrorString(ec));
+            return TN_EDEVICE;
+        }
+        cudaError_t ei = cudaGraphInstantiate(&cn.graph[gi], g, 0);
+        cudaGraphDestroy(g);
+        if (ei != cudaSuccess) {
+            cn.graph[gi] = nullptr;
+            tn_set_error(std::string("graph instantiation failed: ") + cudaGetErrorString(ei));
+            return TN_EDEVICE;
+        }
+        cn.graph_key[gi][0] = d_closed;
+        cn.graph_key[gi][1] = out;
+    }
+    CK(cudaGraphLaunch(cn.graph[gi], st));
+    return TN_OK;
+}
+
 // Compile (and re-materialise the leaves) for explicit-version legs E, if not current.
 int ensure_variant(DevMem &mem, CNet &cn, uint64_t E) {
     if (cn.compiled && cn.E == E) return TN_OK;
+    drop_graphs(cn);
     RC(tn_compile(cn.net, cn.tree, E, cn.steps, cn.elem == 8 && cn.prec != TN_PREC_C64));
     cn.E = E;
     cn.compiled = true;
@@ -867,7 +927,7 @@ int tn_contract(tn_plan_h p, const uint64_t *slices, int64_t n_slices, const uin
         if (!p->closed.empty())
             CK(cudaMemcpyAsync(p->d_closed.p, closed_bits + g0, nb * sizeof(uint64_t),
                                dev ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, st));
-        RC(execute(p->amp, static_cast<const uint64_t *>(p->d_closed.p), g0 > 0, static_cast<double2 *>(p->d_amps.p), st));
+        RC(execute_graphed(p->amp, static_cast<const uint64_t *>(p->d_closed.p), g0 > 0, static_cast<double2 *>(p->d_amps.p), st));
         CK(cudaMemcpyAsync(amps + 2 * g0 * NA, p->d_amps.p, nb * NA * sizeof(double2),
                            dev ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, st));
     }
@@ -1101,7 +1161,7 @@ int tn_sample_step(tn_plan_h p, const uint64_t *slices, int64_t n_slices, double
     }
     tnk::draw_batches<<<(unsigned)((T + 255) / 256), 256, 0, st>>>(seed, t0, T, b_bits, static_cast<uint64_t *>(p->d_j.p));
     CK(cudaGetLastError());
-    RC(execute(p->amp, static_cast<const uint64_t *>(p->d_j.p), reuse_stem != 0, static_cast<double2 *>(p->d_amps.p), st));
+    RC(execute_graphed(p->amp, static_cast<const uint64_t *>(p->d_j.p), reuse_stem != 0, static_cast<double2 *>(p->d_amps.p), st));
     tnk::SampleParams sp;
     std::memset(&sp, 0, sizeof(sp));
     sp.amps = static_cast<const double2 *>(p->d_amps.p);
@@ -1189,7 +1249,7 @@ int tn_sample(tn_plan_h p, double f_target, int64_t N, uint64_t seed, double alp
         tnk::draw_batches<<<(unsigned)((T + 255) / 256), 256, 0, st>>>(seed, (uint64_t)t, T, b_bits,
                                                                          static_cast<uint64_t *>(p->d_j.p));
         CK(cudaGetLastError());
-        RC(execute(p->amp, static_cast<const uint64_t *>(p->d_j.p), group > 0, static_cast<double2 *>(p->d_amps.p), st));
+        RC(execute_graphed(p->amp, static_cast<const uint64_t *>(p->d_j.p), group > 0, static_cast<double2 *>(p->d_amps.p), st));
         sp.t0 = (uint64_t)t;
         tnk::sampler<<<(unsigned)((T * 32 + 255) / 256), 256, 0, st>>>(sp);
         CK(cudaGetLastError());
