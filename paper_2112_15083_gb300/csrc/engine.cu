@@ -110,6 +110,10 @@ struct CNet {
     uint64_t E = 0;            // explicit-version sliced legs of the compiled variant
     bool compiled = false;
     int prec = TN_PREC_C64;    // precision mode of the tensor-core steps
+    int prec_active = -1;      // formats currently materialised (bf16 while calibrating fp16)
+    bool calibrated = false;   // fp16 scales measured
+    bool calibrating = false;  // this execution records per-node maxima
+    DBuf absmax;               // per node: calibration maxima (float bits)
     std::vector<int> fmt;      // per node: storage format (tnk::OutFmt)
     std::vector<float> scale;  // per node: stored value = true value * scale
     std::vector<char> use_tc;  // per step: tcgen05 kernel
@@ -180,10 +184,11 @@ bool tc_step(const Step &s) { return tn_tc_shape(s.nm, s.nn, s.nk); }
 void assign_formats(CNet &cn) {
     const int NN = (int)cn.tree.nodes.size();
     cn.fmt.assign(NN, tnk::OUT_C64);
-    cn.scale.assign(NN, 1.0f);
+    if (!(cn.calibrated && (int)cn.scale.size() == NN)) cn.scale.assign(NN, 1.0f);
     cn.use_tc.assign(cn.steps.size(), 0);
-    if (cn.elem != 8 || cn.prec == TN_PREC_C64) return;
-    const int split = cn.prec == TN_PREC_FP16X2 ? tnk::OUT_SPLIT_FP16 : tnk::OUT_SPLIT_BF16;
+    if (cn.prec_active < 0) cn.prec_active = cn.prec == TN_PREC_FP16X2 ? TN_PREC_BF16X2 : cn.prec;
+    if (cn.elem != 8 || cn.prec_active == TN_PREC_C64) return;
+    const int split = cn.prec_active == TN_PREC_FP16X2 ? tnk::OUT_SPLIT_FP16 : tnk::OUT_SPLIT_BF16;
     for (size_t i = 0; i < cn.steps.size(); i++) {
         const Step &s = cn.steps[i];
         if (!tc_step(s)) continue;
@@ -191,6 +196,11 @@ void assign_formats(CNet &cn) {
         cn.fmt[s.a] = split;
         cn.fmt[s.b] = split;
     }
+    if (split != tnk::OUT_SPLIT_FP16)
+        for (auto &x : cn.scale) x = 1.0f;
+    else
+        for (int x = 0; x < NN; x++)
+            if (cn.fmt[x] != tnk::OUT_SPLIT_FP16) cn.scale[x] = 1.0f;
 }
 
 PFN_cuTensorMapEncodeTiled_v12000 g_encode = nullptr;
@@ -339,6 +349,7 @@ void free_cnet(DevMem &mem, CNet &cn) {
     release(mem, cn.arena);
     release(mem, cn.tables);
     release(mem, cn.err);
+    release(mem, cn.absmax);
     cn.d_err = nullptr;
     for (auto &x : cn.ev) cudaEventDestroy(x);
     cn.ev.clear();
@@ -591,6 +602,15 @@ int execute(CNet &cn, const uint64_t *d_closed, bool skip_beta_free, double2 *ou
         }
         if (cn.elem == 8) RC(launch_step<float2>(cn, s, st));
         else RC(launch_step<double2>(cn, s, st));
+        if (cn.calibrating) {
+            const long long n = 1LL << cn.tree.nodes[s.c].layout.size();
+            for (long long v = 0; v < cn.cp.nver[s.c]; v++) {
+                const char *base = static_cast<const char *>(cn.arena.p) + cn.cp.off[s.c] + v * n * 8;
+                tnk::absmax_kernel<<<(unsigned)std::min<long long>((n + 255) / 256, 1024), 256, 0, st>>>(
+                    base, n, cn.fmt[s.c], static_cast<int *>(cn.absmax.p) + s.c);
+            }
+            CK(cudaGetLastError());
+        }
         if (cn.trace) {
             CK(cudaEventRecord(cn.ev[2 * si + 1], st));
             cn.ev_pending[si] = 1;
@@ -608,6 +628,41 @@ int execute(CNet &cn, const uint64_t *d_closed, bool skip_beta_free, double2 *ou
     return TN_OK;
 }
 
+// fp16 split: the first execution runs with bf16 split operands and records every
+// node's largest |re|, |im|; each fp16-stored tensor then gets the power-of-two scale
+// putting that maximum at 2^8 (FP16 keeps values down to 2^-22 of it normal).
+int calibrate_fp16(DevMem &mem, CNet &cn, const uint64_t *d_closed, double2 *out, cudaStream_t st, double budget) {
+    const int NN = (int)cn.tree.nodes.size();
+    RC(ensure(mem, cn.absmax, NN * sizeof(int)));
+    CK(cudaMemsetAsync(cn.absmax.p, 0, NN * sizeof(int), st));
+    cn.calibrating = true;
+    int rc = execute(cn, d_closed, false, out, st);
+    cn.calibrating = false;
+    RC(rc);
+    std::vector<int> bits(NN);
+    CK(cudaMemcpyAsync(bits.data(), cn.absmax.p, NN * sizeof(int), cudaMemcpyDeviceToHost, st));
+    CK(cudaStreamSynchronize(st));
+    cn.scale.assign(NN, 1.0f);
+    for (int x = 0; x < NN; x++) {
+        double mx = 0;
+        if (cn.tree.nodes[x].ch[0] < 0) {
+            for (const cplx &v : cn.net.leaves[x].data) mx = std::max(mx, std::max(std::fabs(v.real()), std::fabs(v.imag())));
+        } else {
+            float f;
+            std::memcpy(&f, &bits[x], sizeof(f));
+            mx = f;
+        }
+        if (mx > 0 && std::isfinite(mx)) cn.scale[x] = (float)std::ldexp(1.0, 8 - (int)std::ceil(std::log2(mx)));
+    }
+    cn.calibrated = true;
+    cn.prec_active = TN_PREC_FP16X2;
+    std::vector<uint64_t> slices = cn.cp.slices;
+    drop_graphs(cn);
+    assign_formats(cn);
+    RC(setup_leaves(mem, cn));
+    return prepare_call(mem, cn, slices, budget);
+}
+
 cudaStream_t capture_stream() {
     static thread_local cudaStream_t s = nullptr;
     if (!s) cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking);
@@ -616,7 +671,12 @@ cudaStream_t capture_stream() {
 
 // execute() through a CUDA graph: the first execution for a (call plan, buffers, stem
 // mode) is captured on an internal stream, later ones replay the graph on `st`.
-int execute_graphed(CNet &cn, const uint64_t *d_closed, bool skip_beta_free, double2 *out, cudaStream_t st) {
+int execute_graphed(DevMem &mem, CNet &cn, const uint64_t *d_closed, bool skip_beta_free, double2 *out,
+                    cudaStream_t st, double budget) {
+    if (cn.prec == TN_PREC_FP16X2 && !cn.calibrated) {
+        RC(calibrate_fp16(mem, cn, d_closed, out, st, budget));
+        skip_beta_free = false;  // the stem was recomputed in the calibration formats
+    }
     static const bool disabled = getenv("TN_NO_GRAPH") != nullptr;
     if (cn.trace || disabled) return execute(cn, d_closed, skip_beta_free, out, st);
     const int gi = skip_beta_free ? 1 : 0;
@@ -762,10 +822,9 @@ int tn_plan(tn_circuit_h c, const int32_t *order, int32_t n_order, const tn_edge
     if (opts) o = *opts;
     else tn_plan_opts_default(&o);
     if (o.log2_batches < 0 || o.log2_batches > 16) { tn_set_error("log2_batches must be in [0,16]"); return TN_EINVAL; }
-    if (o.precision != TN_PREC_C64 && o.precision != TN_PREC_BF16X2) {
-        tn_set_error(o.precision == TN_PREC_FP16X2 ? "tn_plan: the fp16 split path is not built yet"
-                                                    : "tn_plan: unknown precision");
-        return o.precision == TN_PREC_FP16X2 ? TN_EUNSUPPORTED : TN_EINVAL;
+    if (o.precision != TN_PREC_C64 && o.precision != TN_PREC_BF16X2 && o.precision != TN_PREC_FP16X2) {
+        tn_set_error("tn_plan: unknown precision");
+        return TN_EINVAL;
     }
     if (sliced && (n_sliced < 0 || n_sliced > 62)) { tn_set_error("n_sliced must be in [0,62]"); return TN_EINVAL; }
     if (!sliced && (o.n_auto_sliced < 0 || o.n_auto_sliced > 62)) { tn_set_error("n_auto_sliced in [0,62]"); return TN_EINVAL; }
@@ -927,7 +986,7 @@ int tn_contract(tn_plan_h p, const uint64_t *slices, int64_t n_slices, const uin
         if (!p->closed.empty())
             CK(cudaMemcpyAsync(p->d_closed.p, closed_bits + g0, nb * sizeof(uint64_t),
                                dev ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, st));
-        RC(execute_graphed(p->amp, static_cast<const uint64_t *>(p->d_closed.p), g0 > 0, static_cast<double2 *>(p->d_amps.p), st));
+        RC(execute_graphed(p->mem, p->amp, static_cast<const uint64_t *>(p->d_closed.p), g0 > 0, static_cast<double2 *>(p->d_amps.p), st, p->budget));
         CK(cudaMemcpyAsync(amps + 2 * g0 * NA, p->d_amps.p, nb * NA * sizeof(double2),
                            dev ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, st));
     }
@@ -1161,7 +1220,7 @@ int tn_sample_step(tn_plan_h p, const uint64_t *slices, int64_t n_slices, double
     }
     tnk::draw_batches<<<(unsigned)((T + 255) / 256), 256, 0, st>>>(seed, t0, T, b_bits, static_cast<uint64_t *>(p->d_j.p));
     CK(cudaGetLastError());
-    RC(execute_graphed(p->amp, static_cast<const uint64_t *>(p->d_j.p), reuse_stem != 0, static_cast<double2 *>(p->d_amps.p), st));
+    RC(execute_graphed(p->mem, p->amp, static_cast<const uint64_t *>(p->d_j.p), reuse_stem != 0, static_cast<double2 *>(p->d_amps.p), st, p->budget));
     tnk::SampleParams sp;
     std::memset(&sp, 0, sizeof(sp));
     sp.amps = static_cast<const double2 *>(p->d_amps.p);
@@ -1249,7 +1308,7 @@ int tn_sample(tn_plan_h p, double f_target, int64_t N, uint64_t seed, double alp
         tnk::draw_batches<<<(unsigned)((T + 255) / 256), 256, 0, st>>>(seed, (uint64_t)t, T, b_bits,
                                                                          static_cast<uint64_t *>(p->d_j.p));
         CK(cudaGetLastError());
-        RC(execute_graphed(p->amp, static_cast<const uint64_t *>(p->d_j.p), group > 0, static_cast<double2 *>(p->d_amps.p), st));
+        RC(execute_graphed(p->mem, p->amp, static_cast<const uint64_t *>(p->d_j.p), group > 0, static_cast<double2 *>(p->d_amps.p), st, p->budget));
         sp.t0 = (uint64_t)t;
         tnk::sampler<<<(unsigned)((T * 32 + 255) / 256), 256, 0, st>>>(sp);
         CK(cudaGetLastError());

@@ -254,6 +254,26 @@ __global__ void materialize(const MatDesc *descs, const uint64_t *closed_bits) {
     }
 }
 
+// ---------------------------------------------------------------- calibration
+
+// *absmax_bits = max(*absmax_bits, max |re|, |im| over the n elements of one version of a
+// tensor stored in format fmt (split formats: planes 0 and 2, the hi parts).  Non-negative
+// floats compare as integers.
+__global__ void absmax_kernel(const void *data, long long n, int fmt, int *absmax_bits) {
+    float m = 0.f;
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+        if (fmt == OUT_C64) {
+            const float2 x = static_cast<const float2 *>(data)[i];
+            m = fmaxf(m, fmaxf(fabsf(x.x), fabsf(x.y)));
+        } else {
+            const __nv_bfloat16 *h = static_cast<const __nv_bfloat16 *>(data);
+            m = fmaxf(m, fmaxf(fabsf(__bfloat162float(h[i])), fabsf(__bfloat162float(h[2 * n + i]))));
+        }
+    }
+    for (int o = 16; o > 0; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
+    if ((threadIdx.x & 31) == 0) atomicMax(absmax_bits, __float_as_int(m));
+}
+
 // ---------------------------------------------------------------- slice sum
 
 // out[e] = sum over explicit root versions v (in order) and over the 2^nfree patterns f

@@ -141,16 +141,19 @@ def test_28q_bf16x2_split_full_slice_set(grid28):
     assert abs(np.sum(p_got * p_ref) / np.sum(p_ref * p_ref) - 1) < 2e-3
 
 
+@pytest.mark.parametrize("prec", ["bf16x2", "fp16x2"])
 @pytest.mark.parametrize("seed", [0, 1])
-def test_bf16x2_haar_batches_and_subsets(seed):
-    """Generic gates with the split path: big enough steps go to the tensor cores."""
+def test_split_haar_batches_and_subsets(seed, prec):
+    """Generic gates with the split paths: big enough steps go to the tensor cores; the
+    fp16 path calibrates per-tensor scales on its first execution."""
     P = pkg()
     n = 16
     circ = cg.random_haar(n, 150, seed=seed, p_two=0.8)
     openq = [3, 9, 12, 1, 15, 6]
     closed = oracle.closed_of(n, openq)
     C = P.circuit_load(circ.serialize())
-    plan = P.plan(C, openq, n_auto_sliced=4, log2_batches=6, order_trials=16, precision=P.tn.PREC_BF16X2)
+    precision = {"bf16x2": P.tn.PREC_BF16X2, "fp16x2": P.tn.PREC_FP16X2}[prec]
+    plan = P.plan(C, openq, n_auto_sliced=4, log2_batches=6, order_trials=16, precision=precision)
     sl = plan.sliced_edges()
     cb = cg.random_closed_bits(100, len(closed), seed=seed + 3)
     psi = oracle.simulate(circ)
@@ -161,6 +164,37 @@ def test_bf16x2_haar_batches_and_subsets(seed):
     amps = plan.contract(sub, cb)
     err = split_errors(amps, oracle.batch_amplitudes(oracle.sliced_state(circ, sl, sub), n, openq, cb))
     assert err["rel_l2"] <= 1e-3, err
+
+
+def test_28q_precision_report(grid28):
+    """Config 3: the same 28-qubit workload in complex64, bf16 x2 and fp16 x2 against the
+    FP64 oracle: per-amplitude error (max and RMS, relative to the RMS amplitude),
+    relative L2 and the linear-XEB deviation of the computed distribution."""
+    P = pkg()
+    circ, psi = grid28
+    openq = cg.default_open_qubits(4, 7, 6)
+    C = P.circuit_load(circ.serialize())
+    cb = cg.random_closed_bits(256, 22, seed=1)
+    ref = oracle.batch_amplitudes(psi, 28, openq, cb)
+    p_ref = np.abs(ref) ** 2
+    report = {}
+    for name, prec in (("c64", P.tn.PREC_C64), ("bf16x2", P.tn.PREC_BF16X2), ("fp16x2", P.tn.PREC_FP16X2)):
+        plan = P.plan(C, openq, n_auto_sliced=10, log2_batches=8, order_trials=256, precision=prec)
+        amps = plan.contract(np.arange(1024, dtype=np.uint64), cb)
+        err = split_errors(amps, ref)
+        p_got = np.abs(amps) ** 2
+        err["xeb_dev"] = float(abs(np.sum(p_got * p_ref) / np.sum(p_ref * p_ref) - 1))
+        report[name] = err
+        del plan
+    for name, err in report.items():
+        print("precision %-7s max/rms %.2e  rms/rms %.2e  relL2 %.2e  xeb_dev %.2e" % (
+            name, err["max_over_rms"], err["rms_err_over_rms"], err["rel_l2"], err["xeb_dev"]))
+    assert report["c64"]["max_over_rms"] <= TOL_C64
+    for name in ("bf16x2", "fp16x2"):
+        assert report[name]["rel_l2"] <= 1e-3 and report[name]["xeb_dev"] <= 2e-3
+    # fp16 keeps 11 mantissa bits per part, bf16 8, but at this workload's long K (up to
+    # 2^15) the FP32 accumulation in TMEM dominates both: they agree within 10%
+    assert report["fp16x2"]["rel_l2"] < 1.1 * report["bf16x2"]["rel_l2"]
 
 
 def test_28q_single_slice_sampled(grid28):
