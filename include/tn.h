@@ -147,7 +147,8 @@ int tn_plan_sliced_edges(tn_plan_h p, tn_edge *out, int32_t cap, int32_t *n_out)
  * Partial-slice norms (Sec. I.A, App. B Alg. 1 steps 1-3): S = SlicedVertexSelect(C, I,
  * k0) with k0 = ceil(3 - log2 f) (Alg. 2), C1 = union of the lightcones of S, and
  * R[i] = <0|C1* delta_{S=i} C1|0> = ||psi_i||^2 for i in {0,1}^k, computed on the GPU
- * by contracting the network C1 (x) C1* with the S legs identified (Fig. 1), in FP64.
+ * by contracting the network C1 (x) C1* with the S legs identified (Fig. 1) in the plan's
+ * contraction precision (complex64, or the split tensor-core path), summed in FP64.
  *  s_index  out, k entries: positions of S within the plan's sliced edges (ascending);
  *           bit t of i is S[t].
  *  R        out, host, cap_R >= 2^k doubles.

@@ -98,8 +98,11 @@ struct CallPlan {
     size_t arena_bytes = 0;
     double flops_all = 0, flops_beta = 0;      // per execution (all steps / beta steps)
     long long root_nver = 0;                   // explicit root versions (slice sum outer loop)
-    std::vector<size_t> map_off;               // per step: first tensor map (2 per version)
+    std::vector<size_t> map_off;               // per step: first tensor map (A, B)
     std::vector<CUtensorMap> maps;
+    std::vector<size_t> vidx_off;              // per step: offset into the version index table
+    std::vector<int> fold;                     // per step: 0, 1 (versions into M), 2 (into N)
+    std::vector<int> vidx;                     // host copy; device copy in CNet::vidx_dev
     bool valid = false;
 };
 
@@ -130,7 +133,7 @@ struct CNet {
     std::vector<char> leaf_beta;
     std::vector<tnk::MatDesc> beta_descs;
     DBuf d_beta_descs;
-    DBuf arena, tables;
+    DBuf arena, tables, vidx_dev;
     CallPlan cp;
     std::vector<int> parent;
     size_t leaf_bytes = 0;
@@ -180,8 +183,10 @@ int num_sms() {
 // and both output dimensions >= 64 (the tile is 128 x 128).
 bool tc_step(const Step &s) { return tn_tc_shape(s.nm, s.nn, s.nk); }
 
-// Storage format of every node = what its consumer reads.
-void assign_formats(CNet &cn) {
+// Storage format of every node = what its consumer reads; use_tc[i] != 0 marks the
+// steps run on the tensor cores (decided from the per-version shapes, or at call time
+// with version folding, see prepare_call).
+void apply_formats(CNet &cn, const std::vector<char> &use_tc) {
     const int NN = (int)cn.tree.nodes.size();
     cn.fmt.assign(NN, tnk::OUT_C64);
     if (!(cn.calibrated && (int)cn.scale.size() == NN)) cn.scale.assign(NN, 1.0f);
@@ -191,7 +196,7 @@ void assign_formats(CNet &cn) {
     const int split = cn.prec_active == TN_PREC_FP16X2 ? tnk::OUT_SPLIT_FP16 : tnk::OUT_SPLIT_BF16;
     for (size_t i = 0; i < cn.steps.size(); i++) {
         const Step &s = cn.steps[i];
-        if (!tc_step(s)) continue;
+        if (!use_tc[i]) continue;
         cn.use_tc[i] = 1;
         cn.fmt[s.a] = split;
         cn.fmt[s.b] = split;
@@ -201,6 +206,12 @@ void assign_formats(CNet &cn) {
     else
         for (int x = 0; x < NN; x++)
             if (cn.fmt[x] != tnk::OUT_SPLIT_FP16) cn.scale[x] = 1.0f;
+}
+
+void assign_formats(CNet &cn) {
+    std::vector<char> u(cn.steps.size(), 0);
+    for (size_t i = 0; i < cn.steps.size(); i++) u[i] = tc_step(cn.steps[i]) ? 1 : 0;
+    apply_formats(cn, u);
 }
 
 PFN_cuTensorMapEncodeTiled_v12000 g_encode = nullptr;
@@ -218,15 +229,20 @@ int get_encoder() {
     return TN_OK;
 }
 
-// 3-D map of a split operand: [4 * BAT planes][rows][K] of 2-byte elements, tiles of
-// 32 (K) x 128 rows, 64-byte swizzle; out-of-range rows/columns read as zero.
-int encode_operand(CUtensorMap *m, const void *base, int lk, int lrows, int lbat, bool fp16) {
+// 4-D map of a split operand: [versions][4 * BAT planes][rows][K] of 2-byte elements
+// (a version is 8 bytes per element: four planes), tiles of 32 (K) x 128 rows, 64-byte
+// swizzle; out-of-range rows/columns read as zero.
+int encode_operand(CUtensorMap *m, const void *base, int lk, int lrows, int lbat, long long nver, bool fp16,
+                   bool fold = false) {
     RC(get_encoder());
-    cuuint64_t dims[3] = {(cuuint64_t)1 << lk, (cuuint64_t)1 << lrows, (cuuint64_t)4 << lbat};
-    cuuint64_t strides[2] = {((cuuint64_t)1 << lk) * 2, ((cuuint64_t)1 << (lk + lrows)) * 2};
-    cuuint32_t box[3] = {(cuuint32_t)tnk::kTcBK, 128, 1};
-    cuuint32_t es[3] = {1, 1, 1};
-    CUresult r = g_encode(m, fp16 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT16 : CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 3,
+    cuuint64_t dims[4] = {(cuuint64_t)1 << lk, (cuuint64_t)1 << lrows, (cuuint64_t)4 << lbat, (cuuint64_t)nver};
+    cuuint64_t strides[3] = {((cuuint64_t)1 << lk) * 2, ((cuuint64_t)1 << (lk + lrows)) * 2,
+                             ((cuuint64_t)1 << (lk + lrows + lbat)) * 8};
+    // folded: one box = all rows of 128 >> lrows consecutive versions (128 rows total)
+    cuuint32_t box[4] = {(cuuint32_t)tnk::kTcBK, fold ? (cuuint32_t)1 << lrows : 128u, 1,
+                         fold ? (cuuint32_t)(128 >> lrows) : 1u};
+    cuuint32_t es[4] = {1, 1, 1, 1};
+    CUresult r = g_encode(m, fp16 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT16 : CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 4,
                           const_cast<void *>(base), dims, strides, box, es, CU_TENSOR_MAP_INTERLEAVE_NONE,
                           CU_TENSOR_MAP_SWIZZLE_64B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
                           CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
@@ -348,6 +364,7 @@ void free_cnet(DevMem &mem, CNet &cn) {
     release(mem, cn.d_beta_descs);
     release(mem, cn.arena);
     release(mem, cn.tables);
+    release(mem, cn.vidx_dev);
     release(mem, cn.err);
     release(mem, cn.absmax);
     cn.d_err = nullptr;
@@ -379,6 +396,40 @@ int prepare_call(DevMem &mem, CNet &cn, const std::vector<uint64_t> &slices, dou
             if (index[x].emplace(w, (int)vals[x].size()).second) vals[x].push_back(w);
         }
         cp.nver[x] = (long long)vals[x].size();
+    }
+    // tensor-core steps at call time: a step whose per-version rows (or columns) are too
+    // few is folded when the other operand is shared by all versions and this operand's
+    // versions are consecutive: the versions stack into one M (or N) axis
+    cp.fold.assign(cn.steps.size(), 0);
+    if (cn.elem == 8 && cn.prec != TN_PREC_C64) {
+        std::vector<char> u(cn.steps.size(), 0);
+        auto vindex = [&](int x, uint64_t w) -> long long {
+            if (nodes[x].ch[0] < 0) return (long long)leaf_code(w, cn.leaf_sl[x]);
+            return index[x].at(w);
+        };
+        for (size_t i = 0; i < cn.steps.size(); i++) {
+            const Step &s = cn.steps[i];
+            if (tc_step(s)) { u[i] = 1; continue; }
+            const long long nv = cp.nver[s.c];
+            if (s.nk < 4 || nv < 2) continue;
+            const uint64_t Da = nodes[s.a].dep & cn.E, Db = nodes[s.b].dep & cn.E;
+            bool a_const = true, b_const = true, a_seq = true, b_seq = true;
+            const long long a0 = vindex(s.a, vals[s.c][0] & Da), b0 = vindex(s.b, vals[s.c][0] & Db);
+            for (long long v = 0; v < nv; v++) {
+                const long long ia = vindex(s.a, vals[s.c][v] & Da), ib = vindex(s.b, vals[s.c][v] & Db);
+                a_const &= ia == a0;
+                b_const &= ib == b0;
+                a_seq &= ia == a0 + v;
+                b_seq &= ib == b0 + v;
+            }
+            if (s.nm < 7 && s.nn >= 6 && b_const && a_seq && (nv << s.nm) >= 64) { u[i] = 1; cp.fold[i] = 1; }
+            else if (s.nn < 7 && s.nm >= 6 && a_const && b_seq && (nv << s.nn) >= 64) { u[i] = 1; cp.fold[i] = 2; }
+        }
+        if (u != cn.use_tc) {
+            apply_formats(cn, u);
+            drop_graphs(cn);
+            RC(setup_leaves(mem, cn));
+        }
     }
     // arena: first fit, children released after their parent's step; beta-free
     // nodes consumed by beta steps stay alive (reused by later batch groups)
@@ -469,22 +520,44 @@ int prepare_call(DevMem &mem, CNet &cn, const std::vector<uint64_t> &slices, dou
     const int root = cn.tree.root;
     for (uint64_t w : vals[root]) cp.host_tab.push_back(base_of(root, w));
     cp.root_nver = (long long)vals[root].size();
-    // tensor maps of the tensor-core steps (A and B of every explicit version)
+    // tensor-core steps: one 4-D map per operand over all its versions (leaf codes or
+    // the node's arena versions) and a table giving each C version's operand versions
     cp.map_off.assign(cn.steps.size(), 0);
+    cp.vidx_off.assign(cn.steps.size(), 0);
     cp.maps.clear();
+    cp.vidx.clear();
+    auto version_index = [&](int x, uint64_t w) -> int {
+        if (nodes[x].ch[0] < 0) return (int)leaf_code(w, cn.leaf_sl[x]);
+        return index[x].at(w);
+    };
+    auto version_count = [&](int x) -> long long {
+        if (nodes[x].ch[0] < 0) return 1LL << cn.leaf_sl[x].size();
+        return cp.nver[x];
+    };
+    auto region = [&](int x) -> const void * {
+        if (nodes[x].ch[0] < 0) return cn.leaf_dst[x].p;
+        return static_cast<const char *>(cn.arena.p) + cp.off[x];
+    };
     for (size_t i = 0; i < cn.steps.size(); i++) {
         if (cn.use_tc.empty() || !cn.use_tc[i]) continue;
         const Step &s = cn.steps[i];
         cp.map_off[i] = cp.maps.size();
-        const long long nv = cp.nver[s.c];
+        cp.vidx_off[i] = cp.vidx.size();
         const bool f16 = cn.fmt[s.a] == tnk::OUT_SPLIT_FP16;
-        for (long long v = 0; v < nv; v++) {
-            CUtensorMap ma, mb;
-            RC(encode_operand(&ma, cp.host_tab[cp.tab_off[i] + v], s.nk, s.nm, s.nbat, f16));
-            RC(encode_operand(&mb, cp.host_tab[cp.tab_off[i] + nv + v], s.nk, s.nn, s.nbat, f16));
-            cp.maps.push_back(ma);
-            cp.maps.push_back(mb);
-        }
+        CUtensorMap ma, mb;
+        RC(encode_operand(&ma, region(s.a), s.nk, s.nm, s.nbat, version_count(s.a), f16, cp.fold[i] == 1));
+        RC(encode_operand(&mb, region(s.b), s.nk, s.nn, s.nbat, version_count(s.b), f16, cp.fold[i] == 2));
+        cp.maps.push_back(ma);
+        cp.maps.push_back(mb);
+        const uint64_t Da = nodes[s.a].dep & cn.E, Db = nodes[s.b].dep & cn.E;
+        for (uint64_t w : vals[s.c]) cp.vidx.push_back(version_index(s.a, w & Da));
+        for (uint64_t w : vals[s.c]) cp.vidx.push_back(version_index(s.b, w & Db));
+    }
+    if (!cp.vidx.empty()) {
+        RC(ensure(mem, cn.vidx_dev, cp.vidx.size() * sizeof(int)));
+        CK(cudaMemcpyAsync(cn.vidx_dev.p, cp.vidx.data(), cp.vidx.size() * sizeof(int), cudaMemcpyHostToDevice,
+                           mem.stream));
+        CK(cudaStreamSynchronize(mem.stream));
     }
     RC(ensure(mem, cn.tables, cp.host_tab.size() * sizeof(void *)));
     CK(cudaMemcpyAsync(cn.tables.p, cp.host_tab.data(), cp.host_tab.size() * sizeof(void *),
@@ -536,14 +609,19 @@ int launch_step(CNet &cn, const Step &s, cudaStream_t st) {
             for (int i = 0; i < s.nm; i++) tp.pos_m[i] = s.pos_m[i];
             for (int i = 0; i < s.nn; i++) tp.pos_n[i] = s.pos_n[i];
             using Lay = tnk::TcSmem<128, 3>;
+            const int fold = cp.fold.empty() ? 0 : cp.fold[si];
             const int ltm = std::min(s.nm, 7), ltn = std::min(s.nn, 7);
-            const long long tiles = 1LL << (s.nbat + (s.nm - ltm) + (s.nn - ltn));
+            long long tiles_m = 1LL << (s.nm - ltm), tiles_n = 1LL << (s.nn - ltn), tiles_v = p.nver;
+            if (fold == 1) { const long long vm = 128 >> s.nm; tiles_m = (p.nver + vm - 1) / vm; tiles_v = 1; }
+            if (fold == 2) { const long long vn = 128 >> s.nn; tiles_n = (p.nver + vn - 1) / vn; tiles_v = 1; }
+            const long long tiles = (tiles_m * tiles_n << s.nbat) * tiles_v;
             const long long blocks = std::min<long long>(tiles, num_sms());
-            for (long long v = 0; v < p.nver; v++) {
-                tp.C = static_cast<char *>(p.C) + v * p.c_vstride * 8;
-                const CUtensorMap *m = &cp.maps[cp.map_off[si] + 2 * v];
-                tnk::tc_cgemm<128, 3><<<(unsigned)blocks, tnk::kTcThreads, Lay::kBytes, st>>>(m[0], m[1], tp);
-            }
+            tp.C = p.C;
+            tp.nver = (int)p.nver;
+            tp.fold = fold;
+            tp.vidx = static_cast<const int *>(cn.vidx_dev.p) + cp.vidx_off[si];
+            const CUtensorMap *m = &cp.maps[cp.map_off[si]];
+            tnk::tc_cgemm<128, 3><<<(unsigned)blocks, tnk::kTcThreads, Lay::kBytes, st>>>(m[0], m[1], tp);
             CK(cudaGetLastError());
             return TN_OK;
         }
@@ -761,7 +839,8 @@ int build_cnet(const Merged &mg, CNet &cn, const tn_plan_opts &o, const int32_t 
     (void)mg;
     cn.elem = elem;
     uint64_t E0 = 0;
-    RC(tn_tree_and_compile(cn.net, o, order, n_order, nullptr, cn.tree, cn.steps, &E0));
+    RC(tn_tree_and_compile(cn.net, o, order, n_order, nullptr, cn.tree, cn.steps, &E0,
+                           elem == 8 && cn.prec != TN_PREC_C64));
     cn.E = E0;
     cn.compiled = true;
     assign_formats(cn);
@@ -1009,10 +1088,13 @@ int tn_partial_norms(tn_plan_h p, double f, int32_t *s_index, int32_t *k_out, do
     else {
         std::vector<tn_edge> S;
         for (int e : spos) S.push_back(p->I[e]);
+        // R in the plan's contraction precision (complex64 FFMA or split tensor cores);
+        // the FP64 work is the reduction of the slice cut
         CNet cn;
+        cn.prec = p->amp.prec;
         int rc = tn_build_norm_network(p->mg, S, cn.net);
         if (rc) return rc;
-        rc = build_cnet(p->mg, cn, p->opts, nullptr, 0, p->mem, 16);
+        rc = build_cnet(p->mg, cn, p->opts, nullptr, 0, p->mem, 8);
         if (rc) { free_cnet(p->mem, cn); return rc; }
         rc = prepare_call(p->mem, cn, {0ull}, p->budget);
         if (rc) { free_cnet(p->mem, cn); return rc; }

@@ -30,8 +30,11 @@ constexpr int kTcBM = 128;
 constexpr int kTcBK = 32;      // K elements per ring slot (64 bytes per row: 64B swizzle)
 
 struct TcParams {
-    void *C;                 // output base (this launch's version)
-    long long c_plane;       // split output: elements per plane
+    void *C;                 // output base (version 0); version v at C + 8 * v * c_plane bytes
+    long long c_plane;       // elements per version (= split plane stride)
+    const int *vidx;         // [v]: A version index, [nver + v]: B version index
+    int nver;                // explicit versions of C (power of two not required)
+    int fold;                // 0: versions are tiles; 1: versions folded into M; 2: into N
     int lm, ln, lk, lbat;
     int out_fmt;
     int in_fp16;             // operands are fp16 (else bf16)
@@ -89,12 +92,12 @@ __device__ __forceinline__ bool mbar_drain(uint32_t bar, uint32_t parity, long l
     }
 }
 
-__device__ __forceinline__ void tma_load_3d(uint32_t dst, const CUtensorMap *map, int c0, int c1, int c2,
+__device__ __forceinline__ void tma_load_4d(uint32_t dst, const CUtensorMap *map, int c0, int c1, int c2, int c3,
                                             uint32_t bar) {
     asm volatile(
-        "cp.async.bulk.tensor.3d.shared::cluster.global.tile.mbarrier::complete_tx::bytes "
-        "[%0], [%1, {%2, %3, %4}], [%5];" ::"r"(dst),
-        "l"(reinterpret_cast<uint64_t>(map)), "r"(c0), "r"(c1), "r"(c2), "r"(bar)
+        "cp.async.bulk.tensor.4d.shared::cluster.global.tile.mbarrier::complete_tx::bytes "
+        "[%0], [%1, {%2, %3, %4, %5}], [%6];" ::"r"(dst),
+        "l"(reinterpret_cast<uint64_t>(map)), "r"(c0), "r"(c1), "r"(c2), "r"(c3), "r"(bar)
         : "memory");
 }
 
@@ -157,7 +160,8 @@ struct TcSmem {
 constexpr int kTcThreads = 192;  // warp 0: TMA, warp 1: MMA, warps 2-5: epilogue
 
 // Persistent kernel: CTA c processes tiles c, c + gridDim.x, ...  Tile order: N tiles
-// fastest, then M tiles, then batch (CTAs running together share the A row panel).
+// fastest, then M tiles, then batch, then explicit version (CTAs running together share
+// the A row panel).  Operand maps are 4-D: [version][4 * BAT planes][rows][K].
 // TMEM holds two accumulator pairs (Cr | Ci for BN columns each) so the epilogue of
 // one tile overlaps the MMAs of the next.
 template <int BN, int STAGES>
@@ -175,9 +179,17 @@ __global__ void __launch_bounds__(kTcThreads, 1)
     volatile int *abort_flag = reinterpret_cast<volatile int *>(tmem_slot + 1);
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    // Tiles: (n tile, m tile, batch, version) without folding.  With folding the rows
+    // (fold 1) or columns (fold 2) of all versions form one axis: versions are stacked,
+    // 128/M (or BN/N) per tile, and the operand's map box spans that many versions.
     const int ltm = min(p.lm, 7), ltn = min(p.ln, __ffs(BN) - 1);
-    const int lt_n = p.ln - ltn, lt_m = p.lm - ltm;
-    const long long ntiles = 1LL << (p.lbat + lt_m + lt_n);
+    const int vm = p.fold == 1 ? (kTcBM >> p.lm) : 1;  // versions per m tile
+    const int vn = p.fold == 2 ? (BN >> p.ln) : 1;      // versions per n tile
+    const long long tiles_m = p.fold == 1 ? (p.nver + vm - 1) / vm : (1LL << (p.lm - ltm));
+    const long long tiles_n = p.fold == 2 ? (p.nver + vn - 1) / vn : (1LL << (p.ln - ltn));
+    const long long tiles_v = p.fold ? 1 : p.nver;
+    const long long per_bat = tiles_m * tiles_n;
+    const long long ntiles = per_bat * (1LL << p.lbat) * tiles_v;
     const int BAT = 1 << p.lbat;
     const int K = 1 << p.lk;
     const int nkb = (K + kTcBK - 1) / kTcBK;
@@ -214,9 +226,13 @@ __global__ void __launch_bounds__(kTcThreads, 1)
             long long slot = 0;
             bool ok = true;
             for (long long t = blockIdx.x; t < ntiles && ok; t += gridDim.x) {
-                const int tn_i = (int)(t & ((1LL << lt_n) - 1));
-                const int tm_i = (int)((t >> lt_n) & ((1LL << lt_m) - 1));
-                const int bat = (int)(t >> (lt_n + lt_m));
+                const int tn_i = (int)(t % tiles_n);
+                const int tm_i = (int)((t / tiles_n) % tiles_m);
+                const int bat = (int)((t / per_bat) & ((1LL << p.lbat) - 1));
+                const int v = (int)(t / (per_bat << p.lbat));
+                const int ia = p.fold == 1 ? p.vidx[0] + tm_i * vm : p.vidx[p.fold == 2 ? 0 : v];
+                const int ib = p.fold == 2 ? p.vidx[p.nver] + tn_i * vn : p.vidx[p.nver + (p.fold == 1 ? 0 : v)];
+                const int rowA = p.fold == 1 ? 0 : tm_i * kTcBM, rowB = p.fold == 2 ? 0 : tn_i * BN;
                 for (int kb = 0; kb < nkb; kb++, slot++) {
                     const int s = (int)(slot % STAGES);
                     if (slot >= STAGES &&
@@ -228,9 +244,9 @@ __global__ void __launch_bounds__(kTcThreads, 1)
                     mbar_expect_tx(fb, L::kStage);
                     unsigned char *st = smem + s * L::kStage;
                     for (int pl = 0; pl < 4; pl++) {
-                        tma_load_3d(smem_u32(st + pl * L::kAPlane), &tmA, kb * kTcBK, tm_i * kTcBM, pl * BAT + bat, fb);
-                        tma_load_3d(smem_u32(st + 4 * L::kAPlane + pl * L::kBPlane), &tmB, kb * kTcBK, tn_i * BN,
-                                    pl * BAT + bat, fb);
+                        tma_load_4d(smem_u32(st + pl * L::kAPlane), &tmA, kb * kTcBK, rowA, pl * BAT + bat, ia, fb);
+                        tma_load_4d(smem_u32(st + 4 * L::kAPlane + pl * L::kBPlane), &tmB, kb * kTcBK, rowB,
+                                    pl * BAT + bat, ib, fb);
                     }
                     issued = slot + 1;
                 }
@@ -300,27 +316,53 @@ __global__ void __launch_bounds__(kTcThreads, 1)
             const int b = it & 1;
             if (!mbar_wait(smem_u32(&acc_full[b]), (uint32_t)((it >> 1) & 1), abort_flag, kLimit)) break;
             asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-            const int tn_i = (int)(t & ((1LL << lt_n) - 1));
-            const int tm_i = (int)((t >> lt_n) & ((1LL << lt_m) - 1));
-            const int bat = (int)(t >> (lt_n + lt_m));
-            const long long m = (long long)tm_i * kTcBM + row;
-            const long long cbase = scatter_bits(bat, p.pos_bat, p.lbat) + (m < M ? scatter_bits(m, p.pos_m, p.lm) : 0);
+            const int tn_i = (int)(t % tiles_n);
+            const int tm_i = (int)((t / tiles_n) % tiles_m);
+            const int bat = (int)((t / per_bat) & ((1LL << p.lbat) - 1));
+            long long vrow = t / (per_bat << p.lbat);  // this row's version
+            long long m;
+            if (p.fold == 1) {
+                vrow = (long long)tm_i * vm + (row >> p.lm);
+                m = row & (M - 1);
+            } else {
+                m = (long long)tm_i * kTcBM + row;
+            }
+            const bool row_ok = m < M && vrow < p.nver;
+            const long long cbase = scatter_bits(bat, p.pos_bat, p.lbat) + (row_ok ? scatter_bits(m, p.pos_m, p.lm) : 0);
             const uint32_t lane_addr = tmem + ((uint32_t)(32 * quarter) << 16) + (uint32_t)(b * 2 * BN);
             for (int c0 = 0; c0 < BN; c0 += 16) {
                 float re[16], im[16];
                 __syncwarp();
                 tmem_ld16(lane_addr + c0, re);
                 tmem_ld16(lane_addr + BN + c0, im);
+                if (!row_ok) continue;
+                if (p.fold == 2) {
+                    // columns: version (c0 + j) / N of this tile, n = (c0 + j) % N
+#pragma unroll
+                    for (int j = 0; j < 16; j++) {
+                        const long long col = c0 + j;
+                        const long long v = (long long)tn_i * vn + (col >> p.ln), n = col & (N - 1);
+                        if (v < p.nver) {
+                            void *Cv = static_cast<char *>(p.C) + 8 * v * p.c_plane;
+                            const long long off = cbase + scatter_bits(n, p.pos_n, p.ln);
+                            const float2 x = make_float2(re[j] * p.out_scale, im[j] * p.out_scale);
+                            if (p.out_fmt == OUT_C64) static_cast<float2 *>(Cv)[off] = x;
+                            else store_split(Cv, p.c_plane, off, x, p.out_fmt == OUT_SPLIT_FP16);
+                        }
+                    }
+                    continue;
+                }
+                void *Cv = static_cast<char *>(p.C) + 8 * vrow * p.c_plane;
                 const long long nb = (long long)tn_i * BN + c0;
-                if (m < M && nb < N) {
+                if (nb < N) {
                     const long long hi = cbase + (p.ln > 4 ? scatter_bits(nb >> 4, p.pos_n + 4, p.ln - 4) : 0);
 #pragma unroll
                     for (int j = 0; j < 16; j++) {
                         if (nb + j < N) {
                             const long long off = hi + lo[j];
                             const float2 x = make_float2(re[j] * p.out_scale, im[j] * p.out_scale);
-                            if (p.out_fmt == OUT_C64) static_cast<float2 *>(p.C)[off] = x;
-                            else store_split(p.C, p.c_plane, off, x, p.out_fmt == OUT_SPLIT_FP16);
+                            if (p.out_fmt == OUT_C64) static_cast<float2 *>(Cv)[off] = x;
+                            else store_split(Cv, p.c_plane, off, x, p.out_fmt == OUT_SPLIT_FP16);
                         }
                     }
                 }

@@ -240,21 +240,27 @@ def test_hbm_budget_enforced():
 
 # ------------------------------------------------------------------ selection
 
+@pytest.mark.parametrize("prec", ["c64", "bf16x2"])
 @pytest.mark.parametrize("grid,f", [((3, 4, 8), 0.25), ((4, 5, 12), 1 / 64)])
-def test_partial_norms_fp64(grid, f):
+def test_partial_norms(grid, f, prec):
+    """R of Fig. 1's network in the plan's contraction precision: within 1e-5 (complex64)
+    or 1e-3 (split) of max R; S identical to the oracle's Alg. 2."""
     P = pkg()
     circ = cg.sycamore_grid(*grid, seed=0)
     n = grid[0] * grid[1]
     view = oracle.MergedView(circ)
     I = [(q, s) for q in range(n) for s in range(1, view.n2q[q] - 1)]
     C = P.circuit_load(circ.serialize())
-    plan = P.plan(C, cg.default_open_qubits(grid[0], grid[1], 6), sliced=I[:40], log2_batches=2)
+    precision = {"c64": P.tn.PREC_C64, "bf16x2": P.tn.PREC_BF16X2}[prec]
+    plan = P.plan(C, cg.default_open_qubits(grid[0], grid[1], 6), sliced=I[:40], log2_batches=2,
+                  precision=precision)
     S_idx, R = plan.partial_norms(f)
     S_ref = oracle.sliced_vertex_select(circ, I[:40], oracle.k0_for(f))
     assert [I[i] for i in S_idx] == S_ref
     R_ref = oracle.norms(circ, S_ref)
-    assert np.abs(R - R_ref).max() < 1e-12
-    assert abs(R.sum() - 1) < 1e-12
+    tol = 1e-5 if prec == "c64" else 1e-3
+    assert np.abs(R - R_ref).max() < tol * R_ref.max()
+    assert abs(R.sum() - 1) < tol
 
 
 @pytest.mark.parametrize("k,f", [(4, 0.3), (10, 0.02), (12, 0.002), (10, 0.999)])
@@ -270,25 +276,33 @@ def test_slice_cut_bit_exact(k, f):
     assert F == Fr
 
 
-def test_select_partial_state_20q():
-    """Alg. 1 end to end (GPU norms + cut), then the partial contraction of Sec. I.C."""
+@pytest.mark.parametrize("prec", ["c64", "bf16x2"])
+def test_select_partial_state_20q(prec):
+    """Alg. 1 end to end (GPU norms + cut), then the partial contraction of Sec. I.C; the
+    partial legs are explicit versions (folded into the tensor-core tiles when small)."""
     P = pkg()
     circ = cg.sycamore_grid(4, 5, 12, seed=0)
     view = oracle.MergedView(circ)
     openq = cg.default_open_qubits(4, 5, 6)
     C = P.circuit_load(circ.serialize())
     I = [(q, s) for q in range(20) for s in range(2, view.n2q[q] - 1)][:12]
-    plan = P.plan(C, openq, sliced=I, log2_batches=4, order_trials=16)
+    precision = {"c64": P.tn.PREC_C64, "bf16x2": P.tn.PREC_BF16X2}[prec]
+    plan = P.plan(C, openq, sliced=I, log2_batches=4, order_trials=16, precision=precision)
     f = 0.25
     slices, F = plan.select(f)
     S_ref, X_ref, F_ref, R_ref = oracle.slice_selection(circ, I, f)
-    assert abs(F - F_ref) < 1e-12
+    # R from complex64 / split contractions: F within 1e-5 / 1e-3; X identical (no
+    # near-ties here)
+    assert abs(F - F_ref) < (1e-5 if prec == "c64" else 1e-3)
     k = len(S_ref)
     assert len(slices) == len(X_ref) << (len(I) - k)
     cb = cg.random_closed_bits(20, 14, seed=3)
     amps = plan.contract(slices, cb)
     ref = oracle.batch_amplitudes(oracle.partial_state(circ, S_ref, X_ref), 20, openq, cb)
-    close_c64(amps, ref)
+    if prec == "c64":
+        close_c64(amps, ref)
+    else:
+        assert split_errors(amps, ref)["rel_l2"] <= 1e-3
 
 
 # ------------------------------------------------------------------ sampler
