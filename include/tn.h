@@ -191,6 +191,14 @@ int tn_select(tn_plan_h p, double f, uint64_t *slices, int64_t cap, int64_t *n_s
               double *F);
 
 /*
+ * Host-only estimate for a slice set (no device work): device_bytes = arena + leaves +
+ * per-group buffers (+ 64 MiB slack); flops_first / flops_next = algorithmic FLOPs of the
+ * first batch group and of each later group (which reuses the batch-free stem).
+ */
+int tn_plan_estimate(tn_plan_h p, const uint64_t *slices, int64_t n_slices, int64_t *device_bytes,
+                     double *flops_first, double *flops_next);
+
+/*
  * Amplitudes of n_batches batches summed over a slice set (Sec. I.C step 1; no
  * normalisation): amps[t*2^n_open + i] = sum over slices s of <i, closed_bits[t]|C_s|0>,
  * C_s the network with the sliced legs fixed by s.  Slices are summed in FP64 in the
@@ -268,6 +276,75 @@ int tn_rejection_sample(const double *p, int64_t T, int32_t b_bits, double alpha
 /* Batch draws j_t = low b_bits of Philox(seed, t0 + t, stream 0) words 0-1 (device out). */
 int tn_draw_batches(uint64_t seed, uint64_t t0, int64_t T, int32_t b_bits, uint64_t *j,
                     void *stream);
+
+/* Synchronise the plan's stream and report a deferred device error (a bounded device wait
+ * that gave up during asynchronous tn_sample_step calls): TN_OK or TN_ETIMEOUT. */
+int tn_plan_sync(tn_plan_h p);
+
+/* ------------------------------------------------------------------------------------
+ * Serving: a continuous-batching request loop above this C-ABI.  Requests (circuit, open
+ * qubits, precision, target fidelity f, N samples, seed, alpha) are planned on planner
+ * threads (tn_plan, tn_select, tn_plan_estimate), admitted while the sum of admitted
+ * device-memory estimates stays within hbm_budget_bytes and at most max_active run, and
+ * advanced one batch group (tn_sample_step) at a time on their own CUDA streams, so the
+ * groups of different requests overlap on the device.  A request's samples depend only on
+ * its own inputs (deterministic plan, counter-based draws, fixed-order sums), so they are
+ * the same alone and in any mix.  Requests whose estimated GPU time (FLOPs of all batch
+ * groups / assumed_flops) exceeds max_request_seconds are rejected (TN_REQ_REJECTED).
+ * (The paper describes no serving layer; this is a deployment component.)
+ * ---------------------------------------------------------------------------------- */
+typedef struct tn_server_s *tn_server_h;
+
+typedef struct {
+    double hbm_budget_bytes;    /* admission budget (default 150e9) */
+    int32_t max_active;         /* requests running at once (default 8) */
+    int32_t planner_threads;    /* default 2 */
+    int32_t log2_batches;       /* batch group size of every request (default 8) */
+    int32_t order_trials;       /* greedy order trials per plan (default 64) */
+    double max_request_seconds; /* estimated-time limit per request (default 600) */
+    double assumed_flops;       /* rate used for that estimate (default 3e14 FLOP/s) */
+    int32_t device;             /* CUDA device (default 0) */
+} tn_server_opts;
+
+#define TN_REQ_QUEUED 0
+#define TN_REQ_PLANNING 1
+#define TN_REQ_PLANNED 2
+#define TN_REQ_ACTIVE 3
+#define TN_REQ_DONE 4
+#define TN_REQ_FAILED 5
+#define TN_REQ_REJECTED 6
+
+typedef struct {
+    int32_t status;             /* TN_REQ_* */
+    int32_t error;              /* TN_OK or the failing call's code */
+    double F;                   /* retained fidelity of the slice set */
+    int64_t steps, accepted;    /* batches computed and accepted */
+    int64_t n_slices;
+    int64_t est_bytes;          /* admission estimate */
+    double flops;               /* algorithmic FLOPs spent */
+    double t_submit, t_admit, t_done; /* seconds since the server was created */
+} tn_request_info;
+
+typedef struct {
+    int64_t submitted, queued, planning, planned, active, done, failed, rejected;
+    double bytes_in_use;        /* sum of the admitted requests' estimates */
+    double time_s;              /* seconds since the server was created */
+} tn_server_stats;
+
+void tn_server_opts_default(tn_server_opts *opts);
+int tn_server_create(const tn_server_opts *opts, tn_server_h *out);
+/* Non-blocking; circuit is copied.  n_sliced: legs the planner slices (tn_plan_opts.n_auto_sliced). */
+int tn_server_submit(tn_server_h s, const void *circuit, size_t len, const int32_t *open_qubits,
+                     int32_t n_open, int32_t precision, int32_t n_sliced, double f, int64_t N,
+                     uint64_t seed, double alpha, int64_t *id);
+int tn_server_query(tn_server_h s, int64_t id, tn_request_info *info);
+/* Blocks until the request ends (timeout_s <= 0: no limit; else TN_ETIMEOUT); copies up to
+ * cap bitstrings (the first N accepted, in t order) when it succeeded. */
+int tn_server_wait(tn_server_h s, int64_t id, double timeout_s, uint64_t *bitstrings, int64_t cap,
+                   tn_request_info *info);
+int tn_server_get_stats(tn_server_h s, tn_server_stats *stats);
+/* Cancels queued requests, finishes active ones, joins the threads. */
+void tn_server_destroy(tn_server_h s);
 
 const char *tn_strerror(int code);
 const char *tn_last_error(void);

@@ -7,5 +7,5 @@ package holds the build step, the ctypes binding and the seeded input generators
 """
 from . import circuits  # noqa: F401
 from .tn import (  # noqa: F401
-    Circuit, Plan, TnError, circuit_load, draw_batches, lib, plan, rejection_sample, slice_cut,
+    Circuit, Plan, Server, TnError, circuit_load, draw_batches, lib, plan, rejection_sample, slice_cut,
 )

@@ -16,7 +16,7 @@ CSRC = os.path.join(HERE, "csrc")
 OUT = os.path.join(HERE, "_build")
 LIB = os.path.join(OUT, "libtn.so")
 INCLUDE = os.path.join(ROOT, "include")
-SOURCES = ["planner.cpp", "engine.cu"]
+SOURCES = ["planner.cpp", "engine.cu", "serve.cpp"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

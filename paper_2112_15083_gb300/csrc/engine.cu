@@ -216,7 +216,10 @@ void assign_formats(CNet &cn) {
 
 PFN_cuTensorMapEncodeTiled_v12000 g_encode = nullptr;
 
+std::mutex g_encode_mu;
+
 int get_encoder() {
+    std::lock_guard<std::mutex> lock(g_encode_mu);
     if (g_encode) return TN_OK;
     cudaDriverEntryPointQueryResult q;
     void *fn = nullptr;
@@ -378,63 +381,35 @@ inline uint64_t leaf_code(uint64_t w, const std::vector<int> &sl) {
     return code;
 }
 
-// Versions, arena offsets and pointer tables for a slice set.
-int prepare_call(DevMem &mem, CNet &cn, const std::vector<uint64_t> &slices, double budget) {
-    if (cn.cp.valid && cn.cp.slices == slices) return TN_OK;
-    drop_graphs(cn);
-    CallPlan cp;
-    cp.slices = slices;
-    const auto &nodes = cn.tree.nodes;
+// Versions of every node for a slice set and the arena layout (host only).
+struct CallLayout {
+    std::vector<std::vector<uint64_t>> vals;             // per node: distinct versions
+    std::vector<std::unordered_map<uint64_t, int>> index;
+    std::vector<long long> nver;
+    std::vector<size_t> off;
+    size_t arena_bytes = 0;
+    double flops = 0, flops_beta = 0;
+};
+
+void layout_call(const Tree &tree, const std::vector<Step> &steps, uint64_t E, int elem,
+                 const std::vector<uint64_t> &slices, CallLayout &L) {
+    const auto &nodes = tree.nodes;
     const int NN = (int)nodes.size();
-    std::vector<std::vector<uint64_t>> vals(NN);
-    std::vector<std::unordered_map<uint64_t, int>> index(NN);
-    cp.nver.assign(NN, 0);
+    L.vals.assign(NN, {});
+    L.index.assign(NN, {});
+    L.nver.assign(NN, 0);
     for (int x = 0; x < NN; x++) {
-        const uint64_t D = nodes[x].dep & cn.E;
+        const uint64_t D = nodes[x].dep & E;
         for (uint64_t s : slices) {
             uint64_t w = s & D;
-            if (index[x].emplace(w, (int)vals[x].size()).second) vals[x].push_back(w);
+            if (L.index[x].emplace(w, (int)L.vals[x].size()).second) L.vals[x].push_back(w);
         }
-        cp.nver[x] = (long long)vals[x].size();
-    }
-    // tensor-core steps at call time: a step whose per-version rows (or columns) are too
-    // few is folded when the other operand is shared by all versions and this operand's
-    // versions are consecutive: the versions stack into one M (or N) axis
-    cp.fold.assign(cn.steps.size(), 0);
-    if (cn.elem == 8 && cn.prec != TN_PREC_C64) {
-        std::vector<char> u(cn.steps.size(), 0);
-        auto vindex = [&](int x, uint64_t w) -> long long {
-            if (nodes[x].ch[0] < 0) return (long long)leaf_code(w, cn.leaf_sl[x]);
-            return index[x].at(w);
-        };
-        for (size_t i = 0; i < cn.steps.size(); i++) {
-            const Step &s = cn.steps[i];
-            if (tc_step(s)) { u[i] = 1; continue; }
-            const long long nv = cp.nver[s.c];
-            if (s.nk < 4 || nv < 2) continue;
-            const uint64_t Da = nodes[s.a].dep & cn.E, Db = nodes[s.b].dep & cn.E;
-            bool a_const = true, b_const = true, a_seq = true, b_seq = true;
-            const long long a0 = vindex(s.a, vals[s.c][0] & Da), b0 = vindex(s.b, vals[s.c][0] & Db);
-            for (long long v = 0; v < nv; v++) {
-                const long long ia = vindex(s.a, vals[s.c][v] & Da), ib = vindex(s.b, vals[s.c][v] & Db);
-                a_const &= ia == a0;
-                b_const &= ib == b0;
-                a_seq &= ia == a0 + v;
-                b_seq &= ib == b0 + v;
-            }
-            if (s.nm < 7 && s.nn >= 6 && b_const && a_seq && (nv << s.nm) >= 64) { u[i] = 1; cp.fold[i] = 1; }
-            else if (s.nn < 7 && s.nm >= 6 && a_const && b_seq && (nv << s.nn) >= 64) { u[i] = 1; cp.fold[i] = 2; }
-        }
-        if (u != cn.use_tc) {
-            apply_formats(cn, u);
-            drop_graphs(cn);
-            RC(setup_leaves(mem, cn));
-        }
+        L.nver[x] = (long long)L.vals[x].size();
     }
     // arena: first fit, children released after their parent's step; beta-free
     // nodes consumed by beta steps stay alive (reused by later batch groups)
     auto tensor_bytes = [&](int x) {
-        return (size_t)cp.nver[x] * (size_t(1) << nodes[x].layout.size()) * (size_t)cn.elem;
+        return (size_t)L.nver[x] * (size_t(1) << nodes[x].layout.size()) * (size_t)elem;
     };
     struct Blk { size_t off, len; };
     std::vector<Blk> freel;
@@ -469,26 +444,80 @@ int prepare_call(DevMem &mem, CNet &cn, const std::vector<uint64_t> &slices, dou
     // get a reserved prefix: batch-dependent tensors are rewritten in every group, so
     // the two must never share memory.
     std::vector<char> keep(NN, 0);
-    for (const Step &s : cn.steps)
+    for (const Step &s : steps)
         for (int ch : {s.a, s.b})
             if (nodes[ch].ch[0] >= 0 && !nodes[ch].beta && nodes[s.c].beta) keep[ch] = 1;
     size_t reserved = 0;
-    cp.off.assign(NN, 0);
-    for (const Step &s : cn.steps)
+    L.off.assign(NN, 0);
+    for (const Step &s : steps)
         if (keep[s.c]) {
-            cp.off[s.c] = reserved;
+            L.off[s.c] = reserved;
             reserved += (tensor_bytes(s.c) + 255) & ~size_t(255);
         }
     size_t peak = 0;
-    for (const Step &s : cn.steps) {
+    L.flops = L.flops_beta = 0;
+    for (const Step &s : steps) {
         if (!keep[s.c]) {
-            cp.off[s.c] = reserved + alloc(tensor_bytes(s.c));
+            L.off[s.c] = reserved + alloc(tensor_bytes(s.c));
             peak = std::max(peak, top);
         }
         for (int ch : {s.a, s.b})
-            if (nodes[ch].ch[0] >= 0 && !keep[ch]) dealloc(cp.off[ch] - reserved, tensor_bytes(ch));
+            if (nodes[ch].ch[0] >= 0 && !keep[ch]) dealloc(L.off[ch] - reserved, tensor_bytes(ch));
+        const double fl = s.flops_per_version * (double)L.nver[s.c];
+        L.flops += fl;
+        if (nodes[s.c].beta) L.flops_beta += fl;
     }
-    cp.arena_bytes = std::max<size_t>(reserved + peak, 256);
+    L.arena_bytes = std::max<size_t>(reserved + peak, 256);
+}
+
+// Versions, arena offsets and pointer tables for a slice set.
+int prepare_call(DevMem &mem, CNet &cn, const std::vector<uint64_t> &slices, double budget) {
+    if (cn.cp.valid && cn.cp.slices == slices) return TN_OK;
+    drop_graphs(cn);
+    CallPlan cp;
+    cp.slices = slices;
+    const auto &nodes = cn.tree.nodes;
+    CallLayout lay;
+    layout_call(cn.tree, cn.steps, cn.E, cn.elem, slices, lay);
+    auto &vals = lay.vals;
+    auto &index = lay.index;
+    cp.nver = lay.nver;
+    // tensor-core steps at call time: a step whose per-version rows (or columns) are too
+    // few is folded when the other operand is shared by all versions and this operand's
+    // versions are consecutive: the versions stack into one M (or N) axis
+    cp.fold.assign(cn.steps.size(), 0);
+    if (cn.elem == 8 && cn.prec != TN_PREC_C64) {
+        std::vector<char> u(cn.steps.size(), 0);
+        auto vindex = [&](int x, uint64_t w) -> long long {
+            if (nodes[x].ch[0] < 0) return (long long)leaf_code(w, cn.leaf_sl[x]);
+            return index[x].at(w);
+        };
+        for (size_t i = 0; i < cn.steps.size(); i++) {
+            const Step &s = cn.steps[i];
+            if (tc_step(s)) { u[i] = 1; continue; }
+            const long long nv = cp.nver[s.c];
+            if (s.nk < 4 || nv < 2) continue;
+            const uint64_t Da = nodes[s.a].dep & cn.E, Db = nodes[s.b].dep & cn.E;
+            bool a_const = true, b_const = true, a_seq = true, b_seq = true;
+            const long long a0 = vindex(s.a, vals[s.c][0] & Da), b0 = vindex(s.b, vals[s.c][0] & Db);
+            for (long long v = 0; v < nv; v++) {
+                const long long ia = vindex(s.a, vals[s.c][v] & Da), ib = vindex(s.b, vals[s.c][v] & Db);
+                a_const &= ia == a0;
+                b_const &= ib == b0;
+                a_seq &= ia == a0 + v;
+                b_seq &= ib == b0 + v;
+            }
+            if (s.nm < 7 && s.nn >= 6 && b_const && a_seq && (nv << s.nm) >= 64) { u[i] = 1; cp.fold[i] = 1; }
+            else if (s.nn < 7 && s.nm >= 6 && a_const && b_seq && (nv << s.nn) >= 64) { u[i] = 1; cp.fold[i] = 2; }
+        }
+        if (u != cn.use_tc) {
+            apply_formats(cn, u);
+            drop_graphs(cn);
+            RC(setup_leaves(mem, cn));
+        }
+    }
+    cp.off = lay.off;
+    cp.arena_bytes = lay.arena_bytes;
     if ((double)cp.arena_bytes + (double)cn.leaf_bytes > budget) {
         tn_set_error("working set of " + std::to_string(cp.arena_bytes) + " bytes exceeds the HBM budget");
         return TN_ENOMEM;
@@ -506,15 +535,13 @@ int prepare_call(DevMem &mem, CNet &cn, const std::vector<uint64_t> &slices, dou
     };
     cp.host_tab.clear();
     cp.tab_off.clear();
-    cp.flops_all = cp.flops_beta = 0;
+    cp.flops_all = lay.flops;
+    cp.flops_beta = lay.flops_beta;
     for (const Step &s : cn.steps) {
         cp.tab_off.push_back(cp.host_tab.size());
         const uint64_t Da = nodes[s.a].dep & cn.E, Db = nodes[s.b].dep & cn.E;
         for (uint64_t w : vals[s.c]) cp.host_tab.push_back(base_of(s.a, w & Da));
         for (uint64_t w : vals[s.c]) cp.host_tab.push_back(base_of(s.b, w & Db));
-        double fl = s.flops_per_version * (double)cp.nver[s.c];
-        cp.flops_all += fl;
-        if (nodes[s.c].beta) cp.flops_beta += fl;
     }
     cp.root_tab = cp.host_tab.size();
     const int root = cn.tree.root;
@@ -1036,6 +1063,24 @@ int tn_plan_sliced_edges(tn_plan_h p, tn_edge *out, int32_t cap, int32_t *n_out)
     return TN_OK;
 }
 
+int tn_plan_estimate(tn_plan_h p, const uint64_t *slices, int64_t n_slices, int64_t *device_bytes,
+                     double *flops_first, double *flops_next) {
+    if (!p || !slices || n_slices <= 0) { tn_set_error("tn_plan_estimate: bad arguments"); return TN_EINVAL; }
+    std::vector<uint64_t> sl(slices, slices + n_slices);
+    const uint64_t E = explicit_legs(sl, (int)p->I.size());
+    Tree t = p->amp.tree;
+    std::vector<Step> steps;
+    RC(tn_compile(p->amp.net, t, E, steps, p->amp.prec != TN_PREC_C64));
+    CallLayout lay;
+    layout_call(t, steps, E, 8, sl, lay);
+    const long long T = 1LL << p->log2T;
+    if (device_bytes)
+        *device_bytes = (int64_t)(lay.arena_bytes + 2 * p->amp.leaf_bytes + T * (64 * 16 + 64)) + (64ll << 20);
+    if (flops_first) *flops_first = lay.flops;
+    if (flops_next) *flops_next = lay.flops_beta;
+    return TN_OK;
+}
+
 int tn_contract(tn_plan_h p, const uint64_t *slices, int64_t n_slices, const uint64_t *closed_bits, int64_t n_batches,
                 double *amps, int32_t flags) {
     if (!p || !slices || n_slices <= 0 || !amps || n_batches <= 0 || (!closed_bits && !p->closed.empty())) {
@@ -1218,6 +1263,12 @@ int tn_rejection_sample(const double *p, int64_t T, int32_t b_bits, double alpha
     CK(cudaGetLastError());
     CK(cudaStreamSynchronize(static_cast<cudaStream_t>(stream)));
     return TN_OK;
+}
+
+int tn_plan_sync(tn_plan_h p) {
+    if (!p) { tn_set_error("null plan"); return TN_EINVAL; }
+    CK(cudaStreamSynchronize(p->mem.stream));
+    return check_err(p->amp, p->mem.stream);
 }
 
 int tn_trace_enable(tn_plan_h p, int32_t on) {

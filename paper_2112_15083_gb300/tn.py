@@ -24,8 +24,34 @@ EXPORTED = [
     "tn_plan_get_info", "tn_plan_sliced_edges", "tn_partial_norms", "tn_slice_cut", "tn_select",
     "tn_contract", "tn_sample", "tn_rejection_sample", "tn_draw_batches", "tn_strerror", "tn_last_error",
     "tn_plan_host", "tn_sliced_vertex_select", "tn_sample_step", "tn_trace_enable", "tn_trace_read",
-    "tn_slice_cut_noalloc",
+    "tn_slice_cut_noalloc", "tn_plan_estimate", "tn_plan_sync", "tn_server_opts_default", "tn_server_create",
+    "tn_server_submit", "tn_server_query", "tn_server_wait", "tn_server_get_stats", "tn_server_destroy",
 ]
+
+REQ_STATUS = {0: "queued", 1: "planning", 2: "planned", 3: "active", 4: "done", 5: "failed", 6: "rejected"}
+
+
+class ServerOpts(ctypes.Structure):
+    _fields_ = [
+        ("hbm_budget_bytes", ctypes.c_double), ("max_active", ctypes.c_int32), ("planner_threads", ctypes.c_int32),
+        ("log2_batches", ctypes.c_int32), ("order_trials", ctypes.c_int32), ("max_request_seconds", ctypes.c_double),
+        ("assumed_flops", ctypes.c_double), ("device", ctypes.c_int32),
+    ]
+
+
+class RequestInfo(ctypes.Structure):
+    _fields_ = [
+        ("status", ctypes.c_int32), ("error", ctypes.c_int32), ("F", ctypes.c_double), ("steps", ctypes.c_int64),
+        ("accepted", ctypes.c_int64), ("n_slices", ctypes.c_int64), ("est_bytes", ctypes.c_int64),
+        ("flops", ctypes.c_double), ("t_submit", ctypes.c_double), ("t_admit", ctypes.c_double),
+        ("t_done", ctypes.c_double),
+    ]
+
+
+class ServerStats(ctypes.Structure):
+    _fields_ = [(k, ctypes.c_int64) for k in ("submitted", "queued", "planning", "planned", "active", "done",
+                                                "failed", "rejected")] + [
+        ("bytes_in_use", ctypes.c_double), ("time_s", ctypes.c_double)]
 
 
 class TnError(RuntimeError):
@@ -118,6 +144,18 @@ def lib():
         L.tn_sample_step.argtypes = [vp, vp, i64, dbl, u64, u64, dbl, i32, vp, vp, i32]
         L.tn_trace_enable.argtypes = [vp, i32]
         L.tn_trace_read.argtypes = [vp, ctypes.POINTER(StepTrace), i32, ctypes.POINTER(i32)]
+        L.tn_plan_estimate.argtypes = [vp, vp, i64, ctypes.POINTER(i64), ctypes.POINTER(dbl), ctypes.POINTER(dbl)]
+        L.tn_plan_sync.argtypes = [vp]
+        L.tn_server_opts_default.argtypes = [ctypes.POINTER(ServerOpts)]
+        L.tn_server_opts_default.restype = None
+        L.tn_server_create.argtypes = [ctypes.POINTER(ServerOpts), ctypes.POINTER(vp)]
+        L.tn_server_submit.argtypes = [vp, ctypes.c_char_p, ctypes.c_size_t, vp, i32, i32, i32, dbl, i64, u64, dbl,
+                                       ctypes.POINTER(i64)]
+        L.tn_server_query.argtypes = [vp, i64, ctypes.POINTER(RequestInfo)]
+        L.tn_server_wait.argtypes = [vp, i64, dbl, vp, i64, ctypes.POINTER(RequestInfo)]
+        L.tn_server_get_stats.argtypes = [vp, ctypes.POINTER(ServerStats)]
+        L.tn_server_destroy.argtypes = [vp]
+        L.tn_server_destroy.restype = None
         L.tn_slice_cut_noalloc.argtypes = [vp, i32, dbl, vp, vp, ctypes.POINTER(i32), ctypes.POINTER(dbl)]
         L.tn_strerror.argtypes = [ctypes.c_int]
         L.tn_strerror.restype = ctypes.c_char_p
@@ -125,7 +163,7 @@ def lib():
         L.tn_last_error.restype = ctypes.c_char_p
         for name in EXPORTED:
             if name not in ("tn_plan_opts_default", "tn_circuit_destroy", "tn_plan_destroy",
-                            "tn_strerror", "tn_last_error"):
+                            "tn_strerror", "tn_last_error", "tn_server_opts_default", "tn_server_destroy"):
                 getattr(L, name).restype = ctypes.c_int
         _lib = L
     return _lib
@@ -317,6 +355,16 @@ class Plan:
         _check(rc, "tn_sample_step")
         return acc, b
 
+    def estimate(self, slices):
+        """Host-only (device bytes, FLOPs of the first batch group, FLOPs of later groups)."""
+        sl = np.ascontiguousarray(np.asarray(slices, dtype=np.uint64))
+        b = ctypes.c_int64()
+        f1 = ctypes.c_double()
+        f2 = ctypes.c_double()
+        _check(lib().tn_plan_estimate(self.h, _np_ptr(sl), sl.size, ctypes.byref(b), ctypes.byref(f1), ctypes.byref(f2)),
+               "tn_plan_estimate")
+        return b.value, f1.value, f2.value
+
     def trace(self, on: bool = True):
         _check(lib().tn_trace_enable(self.h, int(on)), "tn_trace_enable")
 
@@ -427,3 +475,64 @@ def draw_batches(seed: int, t0: int, T: int, b_bits: int, device="cuda", stream=
     _check(lib().tn_draw_batches(seed, t0, T, b_bits, ctypes.c_void_p(j.data_ptr()), _stream_ptr(stream)),
            "tn_draw_batches")
     return j
+
+
+class Server:
+    """Continuous-batching sampling server (tn_server_*)."""
+
+    def __init__(self, hbm_budget_bytes=150e9, max_active=8, planner_threads=2, log2_batches=8, order_trials=64,
+                 max_request_seconds=600.0, assumed_flops=3e14, device=0):
+        L = lib()
+        o = ServerOpts()
+        L.tn_server_opts_default(ctypes.byref(o))
+        o.hbm_budget_bytes = hbm_budget_bytes
+        o.max_active = max_active
+        o.planner_threads = planner_threads
+        o.log2_batches = log2_batches
+        o.order_trials = order_trials
+        o.max_request_seconds = max_request_seconds
+        o.assumed_flops = assumed_flops
+        o.device = device
+        self.h = ctypes.c_void_p()
+        _check(L.tn_server_create(ctypes.byref(o), ctypes.byref(self.h)), "tn_server_create")
+
+    def submit(self, circuit_bytes: bytes, open_qubits, N: int, f: float = 1.0, seed: int = 0, alpha: float = 2.0,
+               precision=PREC_C64, n_sliced=0) -> int:
+        openq = np.ascontiguousarray(np.asarray(open_qubits, dtype=np.int32))
+        rid = ctypes.c_int64()
+        _check(lib().tn_server_submit(self.h, circuit_bytes, len(circuit_bytes), _np_ptr(openq), openq.size, precision,
+                                      n_sliced, f, N, seed, alpha, ctypes.byref(rid)), "tn_server_submit")
+        return rid.value
+
+    @staticmethod
+    def _info(inf):
+        d = {k: getattr(inf, k) for k, _ in RequestInfo._fields_}
+        d["status"] = REQ_STATUS.get(d["status"], d["status"])
+        return d
+
+    def query(self, rid: int) -> dict:
+        inf = RequestInfo()
+        _check(lib().tn_server_query(self.h, rid, ctypes.byref(inf)), "tn_server_query")
+        return self._info(inf)
+
+    def wait(self, rid: int, N: int, timeout: float = 0.0):
+        """(bitstrings or None, info dict); bitstrings only when the request succeeded."""
+        out = np.zeros(max(1, N), dtype=np.uint64)
+        inf = RequestInfo()
+        rc = lib().tn_server_wait(self.h, rid, timeout, _np_ptr(out), N, ctypes.byref(inf))
+        info = self._info(inf)
+        info["rc"] = rc
+        return (out[:N] if rc == TN_OK else None), info
+
+    def stats(self) -> dict:
+        st = ServerStats()
+        _check(lib().tn_server_get_stats(self.h, ctypes.byref(st)), "tn_server_get_stats")
+        return {k: getattr(st, k) for k, _ in ServerStats._fields_}
+
+    def close(self):
+        if getattr(self, "h", None) and self.h.value and _lib is not None:
+            _lib.tn_server_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        self.close()
