@@ -47,6 +47,9 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--precision", default="bf16x2", choices=["c64", "bf16x2"])
     ap.add_argument("--workload", default="grid4x7_m14", choices=sorted(WORKLOADS))
+    ap.add_argument("--serve", action="store_true", help="serving run (Poisson request stream) instead of the step bench")
+    ap.add_argument("--serve-window", type=float, default=60.0, help="seconds of arrivals")
+    ap.add_argument("--serve-rate", type=float, default=4.0, help="requests per second")
     return ap.parse_args()
 
 
@@ -336,9 +339,94 @@ def run_ours(args):
         torch.distributed.destroy_process_group()
 
 
+# ---------------------------------------------------------------- serving
+
+SERVE_GRIDS = [(4, 5), (4, 6), (5, 5), (4, 7), (5, 6), (4, 8), (5, 7), (6, 6), (4, 9), (4, 10), (5, 8)]
+
+
+def run_serve(args):
+    """Serving run: Poisson arrivals at --serve-rate for --serve-window seconds, circuits
+    drawn uniformly from 20-40-qubit grids and 8-16 cycles, N in {1k, 10k, 100k}, f in
+    {1, 0.1, 0.01, 0.002}, half bf16 x2 / half complex64; 150 GB admission budget."""
+    import math
+    import numpy as np
+    import torch
+    import __graft_entry__
+    torch.cuda.set_device(0)
+    __graft_entry__.build()
+    import paper_2112_15083_gb300 as P
+    from paper_2112_15083_gb300 import circuits as cg
+    rng = np.random.default_rng(0)
+    srv = P.Server(hbm_budget_bytes=150e9, max_active=8, planner_threads=12, order_trials=16,
+                   max_request_seconds=30.0, assumed_flops=3e14, assumed_flops_c64=2.5e13)
+    t0 = time.perf_counter()
+    t = 0.0
+    reqs = []
+    while True:
+        t += rng.exponential(1.0 / args.serve_rate)
+        if t > args.serve_window:
+            break
+        r, c = SERVE_GRIDS[rng.integers(len(SERVE_GRIDS))]
+        cycles = int(rng.integers(8, 17))
+        N = int(rng.choice([1000, 10000, 100000]))
+        f = float(rng.choice([1.0, 0.1, 0.01, 0.002]))
+        prec = P.tn.PREC_BF16X2 if rng.random() < 0.5 else P.tn.PREC_C64
+        k0 = 0 if f >= 1 else int(math.ceil(3 - math.log2(f)))
+        circ = cg.sycamore_grid(r, c, cycles, seed=int(rng.integers(1 << 30)))
+        delay = t - (time.perf_counter() - t0)
+        if delay > 0:
+            time.sleep(delay)
+        rid = srv.submit(circ.serialize(), cg.default_open_qubits(r, c, 6), N=N, f=f, seed=len(reqs),
+                         precision=prec, n_sliced=max(2, k0 + 2))
+        reqs.append(dict(id=rid, qubits=r * c, cycles=cycles, N=N, f=f, prec=prec))
+    print("serve: %d requests submitted in %.1f s" % (len(reqs), time.perf_counter() - t0), file=sys.stderr, flush=True)
+    max_queue = 0
+    infos = []
+    deadline = t0 + args.serve_window + 600.0
+    for q in reqs:
+        st = srv.stats()
+        max_queue = max(max_queue, st["queued"] + st["planning"] + st["planned"])
+        left = max(1.0, deadline - time.perf_counter())
+        _, info = srv.wait(q["id"], q["N"], timeout=left)
+        infos.append(dict(q, **info))
+        if len(infos) % 20 == 0:
+            print("serve: %d/%d finished, %.1f s" % (len(infos), len(reqs), time.perf_counter() - t0), file=sys.stderr,
+                  flush=True)
+    makespan = time.perf_counter() - t0
+    srv.close()
+    done = [i for i in infos if i["status"] == "done"]
+
+    def pct(xs, p):
+        return float(np.percentile(xs, p)) if xs else None
+
+    classes = {}
+    for N in (1000, 10000, 100000):
+        lat = [i["t_done"] - i["t_submit"] for i in done if i["N"] == N]
+        classes["N=%d" % N] = {"done": len(lat), "p50_s": pct(lat, 50), "p99_s": pct(lat, 99)}
+    for f in (1.0, 0.1, 0.01, 0.002):
+        lat = [i["t_done"] - i["t_submit"] for i in done if i["f"] == f]
+        classes["f=%g" % f] = {"done": len(lat), "p50_s": pct(lat, 50), "p99_s": pct(lat, 99)}
+    lat_all = [i["t_done"] - i["t_submit"] for i in done]
+    samples = sum(i["N"] for i in done)
+    line = {"metric": "serving: p50/p99 latency and samples/s", "value": samples / makespan, "unit": "samples/s",
+            "n_gpus": 1, "higher_is_better": True, "data": "synthetic",
+            "config": {"workload": "Poisson %.1f req/s for %.0f s; grids %s; cycles 8-16; N in 1k/10k/100k; "
+                                   "f in 1/0.1/0.01/0.002; bf16x2 or c64 (50/50); 150 GB budget" % (
+                                       args.serve_rate, args.serve_window, SERVE_GRIDS)},
+            "requests": len(infos), "done": len(done),
+            "rejected": sum(1 for i in infos if i["status"] == "rejected"),
+            "failed": sum(1 for i in infos if i["status"] == "failed"),
+            "unfinished": sum(1 for i in infos if i["status"] not in ("done", "failed", "rejected")),
+            "p50_s": pct(lat_all, 50), "p99_s": pct(lat_all, 99), "classes": classes,
+            "max_waiting": max_queue, "makespan_s": makespan}
+    print(json.dumps(line), flush=True)
+
+
 if __name__ == "__main__":
     a = parse()
     if a.impl == "reference":
         run_reference(a)
+    elif a.serve:
+        run_serve(a)
     else:
         run_ours(a)

@@ -73,6 +73,8 @@ typedef struct {
     int32_t order_trials;    /* greedy trials (best estimated time wins); <= 0: 64 */
     int32_t n_auto_sliced;   /* when sliced == NULL: how many edges the planner slices */
     double hbm_budget_bytes; /* device working-set limit per call; <= 0: 64 GiB */
+    double max_norm_flops;   /* tn_partial_norms refuses norm networks above this many
+                                algorithmic FLOPs (TN_EUNSUPPORTED); <= 0: 2e15 */
     void *stream;            /* cudaStream_t; NULL = legacy default stream */
     tn_alloc_fn alloc;       /* optional device allocator */
     tn_free_fn free;
@@ -152,7 +154,9 @@ int tn_plan_sliced_edges(tn_plan_h p, tn_edge *out, int32_t cap, int32_t *n_out)
  *  s_index  out, k entries: positions of S within the plan's sliced edges (ascending);
  *           bit t of i is S[t].
  *  R        out, host, cap_R >= 2^k doubles.
- * Errors: TN_EINVAL (f outside (0,1], cap too small), TN_EDEVICE.
+ * Errors: TN_EINVAL (f outside (0,1], cap too small), TN_EUNSUPPORTED (the norm network's
+ * contraction would exceed tn_plan_opts.max_norm_flops; checked before any device work),
+ * TN_EDEVICE.
  */
 int tn_partial_norms(tn_plan_h p, double f, int32_t *s_index, int32_t *k, double *R,
                      int64_t cap_R);
@@ -301,8 +305,10 @@ typedef struct {
     int32_t planner_threads;    /* default 2 */
     int32_t log2_batches;       /* batch group size of every request (default 8) */
     int32_t order_trials;       /* greedy order trials per plan (default 64) */
-    double max_request_seconds; /* estimated-time limit per request (default 600) */
-    double assumed_flops;       /* rate used for that estimate (default 3e14 FLOP/s) */
+    double max_request_seconds; /* estimated-time limit per request (default 600); it also caps
+                                   the norm network of the slice selection */
+    double assumed_flops;       /* rate of split-precision plans for that estimate (3e14) */
+    double assumed_flops_c64;   /* rate of complex64 plans (default 3e13 FLOP/s) */
     int32_t device;             /* CUDA device (default 0) */
 } tn_server_opts;
 

@@ -902,6 +902,7 @@ void tn_plan_opts_default(tn_plan_opts *o) {
     o->order_trials = 64;
     o->n_auto_sliced = 0;
     o->hbm_budget_bytes = 64.0 * (1ull << 30);
+    o->max_norm_flops = 2e15;
 }
 
 int tn_circuit_load(const void *buf, size_t len, tn_circuit_h *out) {
@@ -1139,6 +1140,17 @@ int tn_partial_norms(tn_plan_h p, double f, int32_t *s_index, int32_t *k_out, do
         cn.prec = p->amp.prec;
         int rc = tn_build_norm_network(p->mg, S, cn.net);
         if (rc) return rc;
+        {
+            Tree t;
+            TreeCost tc;
+            tn_greedy_tree(cn.net, p->opts.order_seed, p->opts.order_trials > 0 ? p->opts.order_trials : 64, t, tc);
+            const double cap = p->opts.max_norm_flops > 0 ? p->opts.max_norm_flops : 2e15;
+            if (tc.flops > cap) {
+                tn_set_error("tn_partial_norms: the norm network needs " + std::to_string(tc.flops) +
+                             " FLOPs (limit " + std::to_string(cap) + ")");
+                return TN_EUNSUPPORTED;
+            }
+        }
         rc = build_cnet(p->mg, cn, p->opts, nullptr, 0, p->mem, 8);
         if (rc) { free_cnet(p->mem, cn); return rc; }
         rc = prepare_call(p->mem, cn, {0ull}, p->budget);

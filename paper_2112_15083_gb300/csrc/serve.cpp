@@ -107,6 +107,11 @@ void fail(tn_server_s *s, Req &r, int code, int32_t status) {
     s->cv_done.notify_all();
 }
 
+// Assumed device rate of a request's precision (for the time estimates).
+double rate_of(const tn_server_s *s, int32_t precision) {
+    return precision == TN_PREC_C64 ? s->o.assumed_flops_c64 : s->o.assumed_flops;
+}
+
 void planner_loop(tn_server_s *s) {
     cudaSetDevice(s->o.device);
     for (;;) {
@@ -133,6 +138,7 @@ void planner_loop(tn_server_s *s) {
             po.n_auto_sliced = r->n_sliced;
             po.hbm_budget_bytes = s->o.hbm_budget_bytes;
             po.stream = r->stream;
+            po.max_norm_flops = s->o.max_request_seconds * rate_of(s, r->precision);
             rc = tn_plan(r->circ, nullptr, 0, nullptr, 0, r->open.data(), (int32_t)r->open.size(), &po, &r->plan);
         }
         int64_t n = 0;
@@ -142,6 +148,10 @@ void planner_loop(tn_server_s *s) {
             rc = tn_select(r->plan, r->f, r->slices.data(), n, &n, &r->F);
         }
         if (!rc) rc = tn_plan_estimate(r->plan, r->slices.data(), n, &r->est_bytes, &r->flops_first, &r->flops_next);
+        if (rc == TN_EUNSUPPORTED) {  // e.g. a norm network over the time limit: a rejection
+            fail(s, *r, rc, TN_REQ_REJECTED);
+            continue;
+        }
         if (rc) {
             fail(s, *r, rc, TN_REQ_FAILED);
             continue;
@@ -151,7 +161,8 @@ void planner_loop(tn_server_s *s) {
         r->T = 1LL << info.log2_batches;
         r->max_steps = (int64_t)std::ceil(8.0 * r->alpha * (double)r->N) + 4096;
         const double groups = std::ceil(1.1 * r->alpha * (double)r->N / (double)r->T);
-        const double est_s = (r->flops_first + std::max(0.0, groups - 1) * r->flops_next) / s->o.assumed_flops;
+        const double est_s =
+            (r->flops_first + std::max(0.0, groups - 1) * r->flops_next) / rate_of(s, r->precision);
         if (est_s > s->o.max_request_seconds || (double)r->est_bytes > s->o.hbm_budget_bytes) {
             r->message = "rejected: estimated " + std::to_string(est_s) + " s / " + std::to_string(r->est_bytes) +
                          " bytes exceed the server limits";
@@ -300,6 +311,7 @@ void tn_server_opts_default(tn_server_opts *o) {
     o->order_trials = 64;
     o->max_request_seconds = 600;
     o->assumed_flops = 3e14;
+    o->assumed_flops_c64 = 3e13;
     o->device = 0;
 }
 
@@ -312,6 +324,7 @@ int tn_server_create(const tn_server_opts *opts, tn_server_h *out) {
     if (s->o.max_active < 1) s->o.max_active = 1;
     if (s->o.planner_threads < 1) s->o.planner_threads = 1;
     if (!(s->o.assumed_flops > 0)) s->o.assumed_flops = 3e14;
+    if (!(s->o.assumed_flops_c64 > 0)) s->o.assumed_flops_c64 = 3e13;
     s->t0 = std::chrono::steady_clock::now();
     for (int i = 0; i < s->o.planner_threads; i++) s->planners.emplace_back(planner_loop, s);
     s->sched = std::thread(sched_loop, s);

@@ -35,7 +35,7 @@ class ServerOpts(ctypes.Structure):
     _fields_ = [
         ("hbm_budget_bytes", ctypes.c_double), ("max_active", ctypes.c_int32), ("planner_threads", ctypes.c_int32),
         ("log2_batches", ctypes.c_int32), ("order_trials", ctypes.c_int32), ("max_request_seconds", ctypes.c_double),
-        ("assumed_flops", ctypes.c_double), ("device", ctypes.c_int32),
+        ("assumed_flops", ctypes.c_double), ("assumed_flops_c64", ctypes.c_double), ("device", ctypes.c_int32),
     ]
 
 
@@ -78,6 +78,7 @@ class PlanOpts(ctypes.Structure):
         ("order_trials", ctypes.c_int32),
         ("n_auto_sliced", ctypes.c_int32),
         ("hbm_budget_bytes", ctypes.c_double),
+        ("max_norm_flops", ctypes.c_double),
         ("stream", ctypes.c_void_p),
         ("alloc", ALLOC_FN),
         ("free", FREE_FN),
@@ -230,7 +231,7 @@ def circuit_load(buf: bytes) -> Circuit:
 class Plan:
     def __init__(self, circuit: Circuit, open_qubits, sliced=None, order=None, precision=PREC_C64,
                  log2_batches=8, order_seed=0, order_trials=64, n_auto_sliced=0,
-                 hbm_budget_bytes=0.0, stream=None, use_torch_allocator=True):
+                 hbm_budget_bytes=0.0, stream=None, use_torch_allocator=True, max_norm_flops=0.0):
         L = lib()
         o = PlanOpts()
         L.tn_plan_opts_default(ctypes.byref(o))
@@ -241,6 +242,8 @@ class Plan:
         o.n_auto_sliced = n_auto_sliced
         if hbm_budget_bytes:
             o.hbm_budget_bytes = hbm_budget_bytes
+        if max_norm_flops:
+            o.max_norm_flops = max_norm_flops
         o.stream = _stream_ptr(stream)
         self._alloc = None
         if use_torch_allocator:
@@ -481,7 +484,7 @@ class Server:
     """Continuous-batching sampling server (tn_server_*)."""
 
     def __init__(self, hbm_budget_bytes=150e9, max_active=8, planner_threads=2, log2_batches=8, order_trials=64,
-                 max_request_seconds=600.0, assumed_flops=3e14, device=0):
+                 max_request_seconds=600.0, assumed_flops=3e14, assumed_flops_c64=3e13, device=0):
         L = lib()
         o = ServerOpts()
         L.tn_server_opts_default(ctypes.byref(o))
@@ -492,6 +495,7 @@ class Server:
         o.order_trials = order_trials
         o.max_request_seconds = max_request_seconds
         o.assumed_flops = assumed_flops
+        o.assumed_flops_c64 = assumed_flops_c64
         o.device = device
         self.h = ctypes.c_void_p()
         _check(L.tn_server_create(ctypes.byref(o), ctypes.byref(self.h)), "tn_server_create")
