@@ -47,10 +47,16 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--precision", default="bf16x2", choices=["c64", "bf16x2"])
     ap.add_argument("--workload", default="grid4x7_m14", choices=sorted(WORKLOADS))
+    ap.add_argument("--log2-batches", type=int, default=None, help="batches per step = 2^this (default: the workload's)")
     ap.add_argument("--serve", action="store_true", help="serving run (Poisson request stream) instead of the step bench")
     ap.add_argument("--serve-window", type=float, default=60.0, help="seconds of arrivals")
     ap.add_argument("--serve-rate", type=float, default=4.0, help="requests per second")
     return ap.parse_args()
+
+
+def log2_batches(args):
+    w = WORKLOADS[args.workload]
+    return w["log2_batches"] if args.log2_batches is None else args.log2_batches
 
 
 def dist_env():
@@ -153,7 +159,7 @@ def run_reference(args):
     w = WORKLOADS[args.workload]
     circ = cg.sycamore_grid(w["rows"], w["cols"], w["cycles"], seed=w["seed"])
     openq = cg.default_open_qubits(w["rows"], w["cols"], w["n_open"])
-    T = 1 << w["log2_batches"]
+    T = 1 << log2_batches(args)
     for i in range(args.warmup):
         oracle_step(circ, openq, T, args.seed, i * T)
     t = time.perf_counter()
@@ -182,8 +188,8 @@ def workload_config(args):
     return {"workload": "%s: %d-qubit %dx%d Sycamore-style ABCD circuit, %d cycles, fSim(pi/2,pi/6); "
                         "%d sliced legs (%d slices); %d batches of 64 bitstrings per step" % (
                             args.workload, q, w["rows"], w["cols"], w["cycles"], w["n_sliced"], 1 << w["n_sliced"],
-                            1 << w["log2_batches"]),
-            "qubits": q, "cycles": w["cycles"], "sliced_legs": w["n_sliced"], "batches_per_step": 1 << w["log2_batches"],
+                            1 << log2_batches(args)),
+            "qubits": q, "cycles": w["cycles"], "sliced_legs": w["n_sliced"], "batches_per_step": 1 << log2_batches(args),
             "batch_size": 64, "fidelity_target": args.fidelity, "alpha": 2.0, "order_trials": args.trials,
             "precision": getattr(args, "precision", "c64"),
             "l2": "flushed between timed steps; dominant operands exceed L2"}
@@ -208,11 +214,11 @@ def run_ours(args):
     openq = cg.default_open_qubits(w["rows"], w["cols"], w["n_open"])
     C = P.circuit_load(circ.serialize())
     prec = {"c64": P.tn.PREC_C64, "bf16x2": P.tn.PREC_BF16X2}[args.precision]
-    plan = P.plan(C, openq, n_auto_sliced=w["n_sliced"], log2_batches=w["log2_batches"], order_trials=args.trials,
+    plan = P.plan(C, openq, n_auto_sliced=w["n_sliced"], log2_batches=log2_batches(args), order_trials=args.trials,
                   order_seed=0, hbm_budget_bytes=200e9, precision=prec)
     info = plan.info()
     slices, F = plan.select(args.fidelity)
-    T = 1 << w["log2_batches"]
+    T = 1 << log2_batches(args)
     dev = torch.device("cuda", local)
     acc = [torch.empty(T, dtype=torch.uint8, device=dev) for _ in range(args.steps)]
     bits = [torch.empty(T, dtype=torch.int64, device=dev) for _ in range(args.steps)]

@@ -7,6 +7,7 @@
 // root versions are summed in FP64 in slice order (Sec. I.C).  Leaves holding closed
 // output legs are re-materialised per batch group with the group's closed patterns.
 #include <algorithm>
+#include <array>
 #include <cmath>
 #include <cstring>
 #include <mutex>
@@ -103,6 +104,9 @@ struct CallPlan {
     std::vector<size_t> vidx_off;              // per step: offset into the version index table
     std::vector<int> fold;                     // per step: 0, 1 (versions into M), 2 (into N)
     std::vector<int> vidx;                     // host copy; device copy in CNet::vidx_dev
+    std::vector<std::array<size_t, 2>> goff;   // per step: arena offsets of gathered operands
+    std::vector<tnk::GatherDesc> gd;           // batch gathers (device copy in CNet::gdescs)
+    std::vector<size_t> gd_off;                // per step: first gather descriptor
     bool valid = false;
 };
 
@@ -130,10 +134,7 @@ struct CNet {
     std::vector<DBuf> leaf_src, leaf_dst;
     std::vector<int> leaf_codebits;
     std::vector<std::vector<int>> leaf_sl;  // sliced legs (e) in leg order
-    std::vector<char> leaf_beta;
-    std::vector<tnk::MatDesc> beta_descs;
-    DBuf d_beta_descs;
-    DBuf arena, tables, vidx_dev;
+    DBuf arena, tables, vidx_dev, gdescs;
     CallPlan cp;
     std::vector<int> parent;
     size_t leaf_bytes = 0;
@@ -275,8 +276,6 @@ int setup_leaves(DevMem &mem, CNet &cn) {
     cn.leaf_dst.assign(L, DBuf());
     cn.leaf_codebits.assign(L, 0);
     cn.leaf_sl.assign(L, {});
-    cn.leaf_beta.assign(L, 0);
-    cn.beta_descs.clear();
     std::vector<tnk::MatDesc> static_descs;
     cn.leaf_bytes = 0;
     for (int i = 0; i < L; i++) {
@@ -284,18 +283,15 @@ int setup_leaves(DevMem &mem, CNet &cn) {
         const Node &nd = cn.tree.nodes[i];
         tnk::MatDesc d;
         std::memset(&d, 0, sizeof(d));
-        std::vector<int> sl, cl, clref;
-        for (size_t l = 0; l < lf.kind.size(); l++) {
+        std::vector<int> sl;
+        for (size_t l = 0; l < lf.kind.size(); l++)
             if (lf.kind[l] == LEG_SLICED && ((cn.E >> lf.ref[l]) & 1)) { sl.push_back((int)l); cn.leaf_sl[i].push_back(lf.ref[l]); }
-            if (lf.kind[l] == LEG_CLOSED) { cl.push_back((int)l); clref.push_back(lf.ref[l]); }
-        }
-        if (sl.size() > 8 || cl.size() > 8 || nd.layout.size() > (size_t)tnk::kMaxBits) {
+        if (sl.size() > 8 || nd.layout.size() > (size_t)tnk::kMaxBits) {
             tn_set_error("leaf with too many legs");
             return TN_EUNSUPPORTED;
         }
         d.nd = (int)nd.layout.size();
         d.ncode_bits = (int)sl.size();
-        d.ncl = (int)cl.size();
         for (int t = 0; t < d.nd; t++) {
             int id = nd.layout[t];
             int leg = -1;
@@ -305,13 +301,10 @@ int setup_leaves(DevMem &mem, CNet &cn) {
                 if (vbit && lf.kind[l] == LEG_SLICED && lf.ref[l] == id - cn.net.n_idx) leg = (int)l;
             }
             if (leg >= 0) d.dst_leg[t] = (int8_t)leg;
-            else if (id >= cn.net.beta_base && id < cn.net.beta_base + cn.net.n_beta) d.dst_leg[t] = (int8_t)(-1 - (id - cn.net.beta_base));
             else { tn_set_error("leaf layout index not found"); return TN_EINVAL; }
         }
         for (size_t u = 0; u < sl.size(); u++) d.sl_leg[u] = (int8_t)sl[u];
-        for (size_t c = 0; c < cl.size(); c++) { d.cl_leg[c] = (int8_t)cl[c]; d.cl_ref[c] = (int16_t)clref[c]; }
         cn.leaf_codebits[i] = d.ncode_bits;
-        cn.leaf_beta[i] = !cl.empty();
         size_t src_bytes = lf.data.size() * sizeof(double2);
         RC(ensure(mem, cn.leaf_src[i], src_bytes));
         CK(cudaMemcpyAsync(cn.leaf_src[i].p, lf.data.data(), src_bytes, cudaMemcpyHostToDevice, mem.stream));
@@ -322,28 +315,22 @@ int setup_leaves(DevMem &mem, CNet &cn) {
         d.dst = cn.leaf_dst[i].p;
         d.fmt = cn.elem == 8 ? cn.fmt[i] : tnk::OUT_C64;
         d.scale = cn.scale[i];
-        if (cl.empty()) static_descs.push_back(d);
-        else cn.beta_descs.push_back(d);
+        static_descs.push_back(d);
     }
-    // static leaves: materialise once
+    // leaves are materialised once per compiled variant and format assignment
     if (!static_descs.empty()) {
         DBuf tmp;
         RC(ensure(mem, tmp, static_descs.size() * sizeof(tnk::MatDesc)));
         CK(cudaMemcpyAsync(tmp.p, static_descs.data(), static_descs.size() * sizeof(tnk::MatDesc),
                            cudaMemcpyHostToDevice, mem.stream));
         dim3 grid(4, (unsigned)static_descs.size());
-        if (cn.elem == 8) tnk::materialize<float2><<<grid, 256, 0, mem.stream>>>((const tnk::MatDesc *)tmp.p, nullptr);
-        else tnk::materialize<double2><<<grid, 256, 0, mem.stream>>>((const tnk::MatDesc *)tmp.p, nullptr);
+        if (cn.elem == 8) tnk::materialize<float2><<<grid, 256, 0, mem.stream>>>((const tnk::MatDesc *)tmp.p);
+        else tnk::materialize<double2><<<grid, 256, 0, mem.stream>>>((const tnk::MatDesc *)tmp.p);
         CK(cudaGetLastError());
         CK(cudaStreamSynchronize(mem.stream));
         release(mem, tmp);
     }
     cn.cp.valid = false;
-    if (!cn.beta_descs.empty()) {
-        RC(ensure(mem, cn.d_beta_descs, cn.beta_descs.size() * sizeof(tnk::MatDesc)));
-        CK(cudaMemcpyAsync(cn.d_beta_descs.p, cn.beta_descs.data(), cn.beta_descs.size() * sizeof(tnk::MatDesc),
-                           cudaMemcpyHostToDevice, mem.stream));
-    }
     CK(cudaStreamSynchronize(mem.stream));
     cn.parent.assign(cn.tree.nodes.size(), -1);
     for (size_t i = 0; i < cn.tree.nodes.size(); i++)
@@ -364,7 +351,7 @@ void free_cnet(DevMem &mem, CNet &cn) {
     drop_graphs(cn);
     for (auto &b : cn.leaf_src) release(mem, b);
     for (auto &b : cn.leaf_dst) release(mem, b);
-    release(mem, cn.d_beta_descs);
+    release(mem, cn.gdescs);
     release(mem, cn.arena);
     release(mem, cn.tables);
     release(mem, cn.vidx_dev);
@@ -387,6 +374,7 @@ struct CallLayout {
     std::vector<std::unordered_map<uint64_t, int>> index;
     std::vector<long long> nver;
     std::vector<size_t> off;
+    std::vector<std::array<size_t, 2>> goff;  // per step: arena offsets of gathered operands
     size_t arena_bytes = 0;
     double flops = 0, flops_beta = 0;
 };
@@ -456,11 +444,24 @@ void layout_call(const Tree &tree, const std::vector<Step> &steps, uint64_t E, i
         }
     size_t peak = 0;
     L.flops = L.flops_beta = 0;
-    for (const Step &s : steps) {
-        if (!keep[s.c]) {
-            L.off[s.c] = reserved + alloc(tensor_bytes(s.c));
-            peak = std::max(peak, top);
-        }
+    L.goff.assign(steps.size(), {0, 0});
+    auto nver_of = [&](int x) -> long long {
+        if (nodes[x].ch[0] >= 0) return L.nver[x];
+        return 1LL << __builtin_popcountll(nodes[x].dep & E);  // leaf codes
+    };
+    for (size_t i = 0; i < steps.size(); i++) {
+        const Step &s = steps[i];
+        // gathered operands live for the step only
+        size_t gbytes[2] = {0, 0};
+        for (int o = 0; o < 2; o++)
+            if (s.gat[o]) {
+                gbytes[o] = (size_t)nver_of(o ? s.b : s.a) * (size_t(1) << s.g_nbits[o]) * (size_t)elem;
+                L.goff[i][o] = reserved + alloc(gbytes[o]);
+            }
+        if (!keep[s.c]) L.off[s.c] = reserved + alloc(tensor_bytes(s.c));
+        peak = std::max(peak, top);
+        for (int o = 0; o < 2; o++)
+            if (s.gat[o]) dealloc(L.goff[i][o] - reserved, gbytes[o]);
         for (int ch : {s.a, s.b})
             if (nodes[ch].ch[0] >= 0 && !keep[ch]) dealloc(L.off[ch] - reserved, tensor_bytes(ch));
         const double fl = s.flops_per_version * (double)L.nver[s.c];
@@ -537,11 +538,25 @@ int prepare_call(DevMem &mem, CNet &cn, const std::vector<uint64_t> &slices, dou
     cp.tab_off.clear();
     cp.flops_all = lay.flops;
     cp.flops_beta = lay.flops_beta;
-    for (const Step &s : cn.steps) {
+    cp.goff = lay.goff;
+    auto version_index = [&](int x, uint64_t w) -> int {
+        if (nodes[x].ch[0] < 0) return (int)leaf_code(w, cn.leaf_sl[x]);
+        return index[x].at(w);
+    };
+    // operand o of step i: its own storage, or the step's gathered copy
+    auto operand_base = [&](size_t i, int o, uint64_t w) -> const void * {
+        const Step &s = cn.steps[i];
+        const int x = o ? s.b : s.a;
+        if (!s.gat[o]) return base_of(x, w);
+        const size_t sz = (size_t(1) << s.g_nbits[o]) * cn.elem;
+        return static_cast<const char *>(cn.arena.p) + cp.goff[i][o] + (size_t)version_index(x, w) * sz;
+    };
+    for (size_t i = 0; i < cn.steps.size(); i++) {
+        const Step &s = cn.steps[i];
         cp.tab_off.push_back(cp.host_tab.size());
         const uint64_t Da = nodes[s.a].dep & cn.E, Db = nodes[s.b].dep & cn.E;
-        for (uint64_t w : vals[s.c]) cp.host_tab.push_back(base_of(s.a, w & Da));
-        for (uint64_t w : vals[s.c]) cp.host_tab.push_back(base_of(s.b, w & Db));
+        for (uint64_t w : vals[s.c]) cp.host_tab.push_back(operand_base(i, 0, w & Da));
+        for (uint64_t w : vals[s.c]) cp.host_tab.push_back(operand_base(i, 1, w & Db));
     }
     cp.root_tab = cp.host_tab.size();
     const int root = cn.tree.root;
@@ -553,10 +568,6 @@ int prepare_call(DevMem &mem, CNet &cn, const std::vector<uint64_t> &slices, dou
     cp.vidx_off.assign(cn.steps.size(), 0);
     cp.maps.clear();
     cp.vidx.clear();
-    auto version_index = [&](int x, uint64_t w) -> int {
-        if (nodes[x].ch[0] < 0) return (int)leaf_code(w, cn.leaf_sl[x]);
-        return index[x].at(w);
-    };
     auto version_count = [&](int x) -> long long {
         if (nodes[x].ch[0] < 0) return 1LL << cn.leaf_sl[x].size();
         return cp.nver[x];
@@ -572,13 +583,62 @@ int prepare_call(DevMem &mem, CNet &cn, const std::vector<uint64_t> &slices, dou
         cp.vidx_off[i] = cp.vidx.size();
         const bool f16 = cn.fmt[s.a] == tnk::OUT_SPLIT_FP16;
         CUtensorMap ma, mb;
-        RC(encode_operand(&ma, region(s.a), s.nk, s.nm, s.nbat, version_count(s.a), f16, cp.fold[i] == 1));
-        RC(encode_operand(&mb, region(s.b), s.nk, s.nn, s.nbat, version_count(s.b), f16, cp.fold[i] == 2));
+        const void *ra = s.gat[0] ? static_cast<const char *>(cn.arena.p) + cp.goff[i][0] : region(s.a);
+        const void *rb = s.gat[1] ? static_cast<const char *>(cn.arena.p) + cp.goff[i][1] : region(s.b);
+        RC(encode_operand(&ma, ra, s.nk, s.nm, s.nbat, version_count(s.a), f16, cp.fold[i] == 1));
+        RC(encode_operand(&mb, rb, s.nk, s.nn, s.nbat, version_count(s.b), f16, cp.fold[i] == 2));
         cp.maps.push_back(ma);
         cp.maps.push_back(mb);
         const uint64_t Da = nodes[s.a].dep & cn.E, Db = nodes[s.b].dep & cn.E;
         for (uint64_t w : vals[s.c]) cp.vidx.push_back(version_index(s.a, w & Da));
         for (uint64_t w : vals[s.c]) cp.vidx.push_back(version_index(s.b, w & Db));
+    }
+    // batch gathers: one descriptor per gathered operand, grouped by step
+    cp.gd.clear();
+    cp.gd_off.assign(cn.steps.size() + 1, 0);
+    for (size_t i = 0; i < cn.steps.size(); i++) {
+        cp.gd_off[i] = cp.gd.size();
+        const Step &s = cn.steps[i];
+        for (int o = 0; o < 2; o++) {
+            if (!s.gat[o]) continue;
+            const int x = o ? s.b : s.a;
+            tnk::GatherDesc g;
+            std::memset(&g, 0, sizeof(g));
+            g.src = static_cast<const char *>(region(x));
+            g.dst = static_cast<char *>(cn.arena.p) + cp.goff[i][o];
+            g.nver = version_count(x);
+            const bool split = cn.elem == 8 && cn.fmt[x] != tnk::OUT_C64;
+            g.nplanes = split ? 4 : 1;
+            g.esize = split ? 2 : cn.elem;
+            g.src_plane = 1LL << nodes[x].layout.size();
+            g.dst_plane = 1LL << s.g_nbits[o];
+            g.nbits = s.g_nbits[o];
+            g.lb = cn.net.n_beta;
+            g.nq = s.g_nq[o];
+            std::vector<std::pair<int, int>> pb;
+            for (int t = 0; t < g.lb; t++) pb.push_back({s.g_pos_beta[o][t], t});
+            std::sort(pb.rbegin(), pb.rend());
+            int lowrun = g.nbits;
+            for (int t = 0; t < g.lb; t++) {
+                g.pos_beta[t] = (int8_t)pb[t].first;
+                g.beta_bit[t] = (int8_t)pb[t].second;
+                lowrun = std::min(lowrun, pb[t].first);
+            }
+            for (int q = 0; q < g.nq; q++) g.q[q] = s.g_q[o][q];
+            const int vw = g.esize == 2 ? 3 : g.esize == 8 ? 1 : 0;
+            g.vec_log2 = lowrun >= vw ? vw : 0;
+            if (g.src_plane != 1LL << (g.nbits - g.lb + g.nq)) {
+                tn_set_error("gather: stored operand size does not match its read layout");
+                return TN_EINVAL;
+            }
+            cp.gd.push_back(g);
+        }
+    }
+    cp.gd_off[cn.steps.size()] = cp.gd.size();
+    if (!cp.gd.empty()) {
+        RC(ensure(mem, cn.gdescs, cp.gd.size() * sizeof(tnk::GatherDesc)));
+        CK(cudaMemcpyAsync(cn.gdescs.p, cp.gd.data(), cp.gd.size() * sizeof(tnk::GatherDesc), cudaMemcpyHostToDevice,
+                           mem.stream));
     }
     if (!cp.vidx.empty()) {
         RC(ensure(mem, cn.vidx_dev, cp.vidx.size() * sizeof(int)));
@@ -653,16 +713,24 @@ int launch_step(CNet &cn, const Step &s, cudaStream_t st) {
             return TN_OK;
         }
     }
-    if (s.nn <= 4 && s.nk <= 6) {
+    if (std::min(s.nm, s.nn) <= 5 && s.nk <= 6) {
+        // short K and one small side: one thread per row of the larger side, the small
+        // side in registers (C = A B^T is symmetric in the operand roles)
+        if (s.nn > s.nm) {
+            std::swap(p.ptrA, p.ptrB);
+            std::swap(p.lm, p.ln);
+            for (int i = 0; i < tnk::kMaxBits; i++) std::swap(p.pos_m[i], p.pos_n[i]);
+        }
         if (cn.trace) cn.tr_kernel[si] = 0;
         long long rows = p.nver << (p.lbat + p.lm);
         unsigned blocks = (unsigned)((rows + 255) / 256);
-        switch (s.nn) {
+        switch (p.ln) {
             case 0: tnk::cgemm_row<T, 1><<<blocks, 256, 0, st>>>(p); break;
             case 1: tnk::cgemm_row<T, 2><<<blocks, 256, 0, st>>>(p); break;
             case 2: tnk::cgemm_row<T, 4><<<blocks, 256, 0, st>>>(p); break;
             case 3: tnk::cgemm_row<T, 8><<<blocks, 256, 0, st>>>(p); break;
-            default: tnk::cgemm_row<T, 16><<<blocks, 256, 0, st>>>(p); break;
+            case 4: tnk::cgemm_row<T, 16><<<blocks, 256, 0, st>>>(p); break;
+            default: tnk::cgemm_row<T, 32><<<blocks, 256, 0, st>>>(p); break;
         }
     } else {
         auto launch = [&](auto kern, int TM, int TN, int nthreads) {
@@ -676,8 +744,9 @@ int launch_step(CNet &cn, const Step &s, cudaStream_t st) {
         else if (s.nm >= 6 && s.nn >= 6) launch(tnk::cgemm_tile<T, 64, 64, TK, 4, 4>, 64, 64, 256);
         else if (s.nm >= 7 && s.nn >= 5) launch(tnk::cgemm_tile<T, 128, 32, TK, 8, 2>, 128, 32, 256);
         else if (s.nm >= 6 && s.nn >= 5) launch(tnk::cgemm_tile<T, 64, 32, TK, 4, 2>, 64, 32, 256);
-        else if (s.nn >= 5) launch(tnk::cgemm_tile<T, 32, 32, TK, 2, 2>, 32, 32, 256);
-        else launch(tnk::cgemm_tile<T, 128, 16, TK, 4, 2>, 128, 16, 256);
+        else if (s.nm >= 5 && s.nn >= 5) launch(tnk::cgemm_tile<T, 32, 32, TK, 2, 2>, 32, 32, 256);
+        else if (s.nm >= 7) launch(tnk::cgemm_tile<T, 128, 16, TK, 4, 2>, 128, 16, 256);
+        else launch(tnk::cgemm_tile<T, 16, 16, TK, 1, 1>, 16, 16, 256);  // small batched products
     }
     CK(cudaGetLastError());
     return TN_OK;
@@ -685,12 +754,6 @@ int launch_step(CNet &cn, const Step &s, cudaStream_t st) {
 
 // One execution of a compiled network: beta leaves, steps, FP64 slice sum into out.
 int execute(CNet &cn, const uint64_t *d_closed, bool skip_beta_free, double2 *out, cudaStream_t st) {
-    if (!cn.beta_descs.empty()) {
-        dim3 grid(8, (unsigned)cn.beta_descs.size());
-        if (cn.elem == 8) tnk::materialize<float2><<<grid, 256, 0, st>>>((const tnk::MatDesc *)cn.d_beta_descs.p, d_closed);
-        else tnk::materialize<double2><<<grid, 256, 0, st>>>((const tnk::MatDesc *)cn.d_beta_descs.p, d_closed);
-        CK(cudaGetLastError());
-    }
     for (const Step &s : cn.steps) {
         if (skip_beta_free && !cn.tree.nodes[s.c].beta) continue;
         const size_t si = &s - cn.steps.data();
@@ -704,6 +767,18 @@ int execute(CNet &cn, const uint64_t *d_closed, bool skip_beta_free, double2 *ou
                 cn.ev_pending[si] = 0;
             }
             CK(cudaEventRecord(cn.ev[2 * si], st));
+        }
+        if (const size_t ng = cn.cp.gd_off[si + 1] - cn.cp.gd_off[si]) {
+            if (!d_closed) { tn_set_error("execute: batch patterns missing"); return TN_EINVAL; }
+            long long most = 0;
+            for (size_t g = cn.cp.gd_off[si]; g < cn.cp.gd_off[si + 1]; g++) {
+                const auto &d = cn.cp.gd[g];
+                most = std::max(most, (d.dst_plane >> d.vec_log2) * d.nplanes * d.nver);
+            }
+            dim3 grid((unsigned)std::min<long long>((most + 255) / 256, 4 * num_sms()), (unsigned)ng);
+            tnk::gather_batches<<<grid, 256, 0, st>>>(static_cast<const tnk::GatherDesc *>(cn.gdescs.p) + cn.cp.gd_off[si],
+                                                      d_closed);
+            CK(cudaGetLastError());
         }
         if (cn.elem == 8) RC(launch_step<float2>(cn, s, st));
         else RC(launch_step<double2>(cn, s, st));
@@ -866,6 +941,8 @@ int build_cnet(const Merged &mg, CNet &cn, const tn_plan_opts &o, const int32_t 
     (void)mg;
     cn.elem = elem;
     uint64_t E0 = 0;
+    tn_cost_settings(cn.net, o);
+    if (elem != 8 || cn.prec == TN_PREC_C64) cn.net.tc_flop_rate = 0;
     RC(tn_tree_and_compile(cn.net, o, order, n_order, nullptr, cn.tree, cn.steps, &E0,
                            elem == 8 && cn.prec != TN_PREC_C64));
     cn.E = E0;

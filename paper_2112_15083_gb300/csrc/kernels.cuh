@@ -210,34 +210,21 @@ struct MatDesc {
     float scale;         // multiplier (split fp16 range scaling)
     int nd;              // destination bits
     int ncode_bits;      // sliced legs of the leaf
-    int ncl;             // closed legs
-    int8_t dst_leg[kMaxBits];  // >= 0: source leg position; < 0: beta bit (-1 - t)
+    int8_t dst_leg[kMaxBits];  // destination bit -> source leg position
     int8_t sl_leg[8];          // code bit u -> source leg position
-    int8_t cl_leg[8];          // closed leg -> source leg position
-    int16_t cl_ref[8];         // closed leg -> closed-qubit position c
 };
 
-// grid.y = leaf; threads over (code, element).  closed_bits[beta] gives the batch
-// pattern (bit c = closed qubit c); may be null when no leaf has closed legs.
+// grid.y = leaf; threads over (code, element).
 template <typename T>
-__global__ void materialize(const MatDesc *descs, const uint64_t *closed_bits) {
+__global__ void materialize(const MatDesc *descs) {
     const MatDesc d = descs[blockIdx.y];
     const long long total = 1LL << (d.nd + d.ncode_bits);
     for (long long g = (long long)blockIdx.x * blockDim.x + threadIdx.x; g < total;
          g += (long long)gridDim.x * blockDim.x) {
         const long long code = g >> d.nd, e = g & ((1LL << d.nd) - 1);
-        long long src = 0, beta = 0;
-        for (int t = 0; t < d.nd; t++) {
-            const long long bit = (e >> t) & 1;
-            const int L = d.dst_leg[t];
-            if (L >= 0) src |= bit << L;
-            else beta |= bit << (-1 - L);
-        }
+        long long src = 0;
+        for (int t = 0; t < d.nd; t++) src |= ((e >> t) & 1) << d.dst_leg[t];
         for (int u = 0; u < d.ncode_bits; u++) src |= ((code >> u) & 1) << d.sl_leg[u];
-        if (d.ncl) {
-            const uint64_t pat = closed_bits[beta];
-            for (int c = 0; c < d.ncl; c++) src |= (long long)((pat >> d.cl_ref[c]) & 1) << d.cl_leg[c];
-        }
         const double2 x = d.src[src];
         if constexpr (sizeof(T) == sizeof(float2)) {
             const float2 y = make_float2((float)(x.x * d.scale), (float)(x.y * d.scale));
@@ -251,6 +238,56 @@ __global__ void materialize(const MatDesc *descs, const uint64_t *closed_bits) {
         } else {
             static_cast<T *>(d.dst)[g] = x;
         }
+    }
+}
+
+// ---------------------------------------------------------------- batch gathers
+
+// A step operand whose closed output legs are selected per batch.  src stores the
+// operand with its nq closed legs as the top bits (every value of those legs, shared by
+// all batches); dst is the operand as the step reads it: nbits layout bits of which the
+// beta bits sit at pos_beta[t] and the other nbits - lb bits are src's low bits in order.
+// dst element e of batch beta = src element (sel << (nbits - lb)) | rest(e), where sel
+// packs the batch pattern's bits q[0], q[1], ... (closed positions).
+struct GatherDesc {
+    const char *src;
+    char *dst;
+    long long nver;              // versions (each: nplanes planes)
+    long long src_plane, dst_plane;  // elements per plane
+    int nplanes, esize;          // 4 x 2 B (split) or 1 x 8 B / 16 B
+    int nbits, lb, nq;
+    int vec_log2;                // log2 of elements per 16-byte chunk (0 when runs are shorter)
+    int8_t pos_beta[16];         // beta bit t -> dst position, sorted by descending position
+    int8_t beta_bit[16];         // ... and which beta bit sits there
+    int16_t q[32];
+};
+
+// grid.y = gather; threads over 16-byte chunks (or single elements) of dst.
+__global__ void gather_batches(const GatherDesc *descs, const uint64_t *closed_bits) {
+    const GatherDesc d = descs[blockIdx.y];
+    const int vl = d.vec_log2;
+    const long long per_plane = d.dst_plane >> vl;
+    const long long total = per_plane * d.nplanes * d.nver;
+    const int nrest = d.nbits - d.lb;
+    for (long long g = (long long)blockIdx.x * blockDim.x + threadIdx.x; g < total;
+         g += (long long)gridDim.x * blockDim.x) {
+        const long long vp = g / per_plane;
+        const long long e = (g - vp * per_plane) << vl;
+        long long rest = e, beta = 0;
+        for (int t = 0; t < d.lb; t++) {  // descending positions: remove each beta bit
+            const int p = d.pos_beta[t];
+            beta |= ((rest >> p) & 1) << d.beta_bit[t];
+            rest = (rest & ((1LL << p) - 1)) | ((rest >> (p + 1)) << p);
+        }
+        const uint64_t pat = closed_bits[beta];
+        long long sel = 0;
+        for (int i = 0; i < d.nq; i++) sel |= (long long)((pat >> d.q[i]) & 1) << i;
+        const long long se = (sel << nrest) | rest;
+        const char *src = d.src + (vp * d.src_plane + se) * d.esize;
+        char *dst = d.dst + (vp * d.dst_plane + e) * d.esize;
+        if (vl > 0 || d.esize == 16) *reinterpret_cast<uint4 *>(dst) = *reinterpret_cast<const uint4 *>(src);
+        else if (d.esize == 8) *reinterpret_cast<uint2 *>(dst) = *reinterpret_cast<const uint2 *>(src);
+        else *reinterpret_cast<unsigned short *>(dst) = *reinterpret_cast<const unsigned short *>(src);
     }
 }
 

@@ -271,10 +271,14 @@ int tn_build_amp_network(const Merged &mg, const std::vector<tn_edge> &I, const 
         }
     for (int q = 0; q < n; q++)
         if (mg.n2q[q] == 0 && open_pos[q] >= 0) net_id[mg.seg_base[q]] = nid++;
+    net.closed_base = nid;
+    net.n_closed = (int)closed_qubits.size();
+    nid += net.n_closed;
     net.n_beta = closed_qubits.empty() ? 0 : log2_batches;
     net.beta_base = nid;
     nid += net.n_beta;
     net.n_idx = nid;
+    net.q_max = log2_batches;
     net.n_sliced = (int)I.size();
     if (nid > kMaxIdx) { tn_set_error("plan: network too large"); return TN_EUNSUPPORTED; }
     net.idx_seg.assign(nid, -1);
@@ -284,7 +288,7 @@ int tn_build_amp_network(const Merged &mg, const std::vector<tn_edge> &I, const 
     auto leg_of = [&](int q, int s, int &kind, int &ref) {
         int id = mg.seg_base[q] + s;
         bool out = s == mg.n2q[q];
-        if (out && open_pos[q] < 0) { kind = LEG_CLOSED; ref = closed_pos[q]; }
+        if (out && open_pos[q] < 0) { kind = LEG_NET; ref = net.closed_base + closed_pos[q]; }
         else if (!out && sliced_pos[id] >= 0) { kind = LEG_SLICED; ref = sliced_pos[id]; }
         else { kind = LEG_NET; ref = net_id[id]; }
     };
@@ -309,7 +313,7 @@ int tn_build_amp_network(const Merged &mg, const std::vector<tn_edge> &I, const 
             Leaf L;
             L.data = {mg.input[2 * q], mg.input[2 * q + 1]};
             if (open_pos[q] >= 0) { L.kind = {LEG_NET}; L.ref = {net_id[mg.seg_base[q]]}; }
-            else { L.kind = {LEG_CLOSED}; L.ref = {closed_pos[q]}; }
+            else { L.kind = {LEG_NET}; L.ref = {net.closed_base + closed_pos[q]}; }
             net.leaves.push_back(std::move(L));
         }
     net.out_layout.clear();
@@ -372,6 +376,8 @@ int tn_build_norm_network(const Merged &mg, const std::vector<tn_edge> &S, Netwo
     net.n_idx = nid;
     net.n_beta = 0;
     net.beta_base = nid;
+    net.closed_base = nid;
+    net.n_closed = 0;
     net.n_sliced = 0;
     net.out_layout.clear();
     for (int t = 0; t < (int)S.size(); t++) net.out_layout.push_back(t);
@@ -381,8 +387,18 @@ int tn_build_norm_network(const Merged &mg, const std::vector<tn_edge> &S, Netwo
 
 // ------------------------------------------------------------------ trees
 
-void tn_tree_from_leaves(const Network &net, Tree &t) {
+Bits tn_leaf_closed(const Network &net, int leaf) {
+    Bits q;
+    const Leaf &L = net.leaves[leaf];
+    for (size_t l = 0; l < L.kind.size(); l++)
+        if (L.kind[l] == LEG_NET && L.ref[l] >= net.closed_base && L.ref[l] < net.closed_base + net.n_closed) q.set(L.ref[l]);
+    return q;
+}
+
+void tn_tree_from_leaves(const Network &net, Tree &t, int q_max) {
     t.nodes.clear();
+    Bits beta;
+    for (int b = 0; b < net.n_beta; b++) beta.set(net.beta_base + b);
     for (int i = 0; i < (int)net.leaves.size(); i++) {
         Node nd;
         nd.leaf = i;
@@ -390,22 +406,32 @@ void tn_tree_from_leaves(const Network &net, Tree &t) {
         for (size_t l = 0; l < L.kind.size(); l++) {
             if (L.kind[l] == LEG_NET) nd.idx.set(L.ref[l]);
             else if (L.kind[l] == LEG_SLICED) nd.dep |= 1ull << L.ref[l];
-            else nd.beta = true;
         }
-        if (nd.beta)
-            for (int b = 0; b < net.n_beta; b++) nd.idx.set(net.beta_base + b);
+        // negative threshold: a leaf with closed legs is read in batch form from the start
+        const Bits q = tn_leaf_closed(net, i);
+        if (q_max < 0 && q.any() && net.n_beta >= 0) {
+            nd.beta = true;
+            nd.idx = nd.idx.andnot(q) | beta;
+        }
         t.nodes.push_back(nd);
     }
     t.root = t.nodes.size() == 1 ? 0 : -1;
 }
+
+void tn_tree_from_leaves(const Network &net, Tree &t) { tn_tree_from_leaves(net, t, net.q_max); }
 
 namespace {
 
 struct IdxCounts {
     std::vector<int> count;
     std::vector<char> out;
+    Bits closed, beta;  // closed-output ids, beta ids
+    int q_max = 0;
 };
 
+// Result of contracting a and b.  Batch selection: the result carries the beta bits
+// instead of closed legs when an operand does or when it would hold more than q_max
+// closed legs (see Network).
 Node contract_nodes(const Node &a, const Node &b, const IdxCounts &ic) {
     Node c;
     Bits u = a.idx | b.idx, both = a.idx & b.idx;
@@ -413,8 +439,17 @@ Node contract_nodes(const Node &a, const Node &b, const IdxCounts &ic) {
     for (int i : both.list())
         if (!ic.out[i] && ic.count[i] == 2) c.idx.clr(i);
     c.dep = a.dep | b.dep;
-    c.beta = a.beta || b.beta;
+    c.beta = a.beta || b.beta || (ic.q_max >= 0 && (c.idx & ic.closed).count() > ic.q_max);
+    if (c.beta) c.idx = c.idx.andnot(ic.closed) | ic.beta;
     return c;
+}
+
+// The root carries the batch bits whenever the network has closed legs.
+void seal_root(Node &r, const IdxCounts &ic) {
+    if (!r.beta && (r.idx & ic.closed).any()) {
+        r.beta = true;
+        r.idx = r.idx.andnot(ic.closed) | ic.beta;
+    }
 }
 
 void counts_of(const Network &net, const std::vector<Node> &leaves, IdxCounts &ic) {
@@ -423,6 +458,11 @@ void counts_of(const Network &net, const std::vector<Node> &leaves, IdxCounts &i
     for (int i : net.out_layout) ic.out[i] = 1;
     for (auto &nd : leaves)
         for (int i : nd.idx.list()) ic.count[i]++;
+    ic.closed = Bits();
+    ic.beta = Bits();
+    for (int c = 0; c < net.n_closed; c++) ic.closed.set(net.closed_base + c);
+    for (int t = 0; t < net.n_beta; t++) ic.beta.set(net.beta_base + t);
+    ic.q_max = net.q_max;
 }
 
 }  // namespace
@@ -449,14 +489,17 @@ int tn_tree_from_ssa(const Network &net, const int32_t *pairs, int n_pairs, Tree
         t.nodes.push_back(c);
     }
     t.root = (int)t.nodes.size() - 1;
+    seal_root(t.nodes[t.root], ic);
+    t.q_max = net.q_max;
     return TN_OK;
 }
 
 void tn_recompute_deps(const Network &net, Tree &t) {
     Tree fresh;
-    tn_tree_from_leaves(net, fresh);
+    tn_tree_from_leaves(net, fresh, t.q_max >= -1 ? t.q_max : net.q_max);
     IdxCounts ic;
     counts_of(net, fresh.nodes, ic);
+    if (t.q_max >= -1) ic.q_max = t.q_max;
     for (size_t i = 0; i < fresh.nodes.size(); i++) {
         t.nodes[i].idx = fresh.nodes[i].idx;
         t.nodes[i].dep = fresh.nodes[i].dep;
@@ -471,26 +514,46 @@ void tn_recompute_deps(const Network &net, Tree &t) {
         c.dep = x.dep;
         c.beta = x.beta;
     }
+    if (t.root >= 0) seal_root(t.nodes[t.root], ic);
 }
 
 TreeCost tn_tree_cost(const Network &net, const Tree &t) {
-    (void)net;
     TreeCost tc;
-    const double flop_rate = 50e12, bw = 5.5e12, launch = 4e-6;
+    // FFMA complex64 rate, HBM bandwidth and per-launch overhead (GB300 measurements of
+    // the kernels in this library); tensor-core shaped steps at net.tc_flop_rate
+    const double flop_rate = 3e13, bw = 5.5e12, launch = 4e-6;
+    Bits closed, beta;
+    for (int c = 0; c < net.n_closed; c++) closed.set(net.closed_base + c);
+    for (int b = 0; b < net.n_beta; b++) beta.set(net.beta_base + b);
     for (auto &nd : t.nodes) {
         int l = nd.idx.count();
         tc.log2_max = std::max(tc.log2_max, l);
         tc.max_versioned = std::max(tc.max_versioned, std::ldexp(1.0, l + __builtin_popcountll(nd.dep)));
         if (nd.ch[0] < 0) continue;
         const Node &a = t.nodes[nd.ch[0]], &b = t.nodes[nd.ch[1]];
+        // an operand with closed legs read by a batch step is gathered first
+        const bool ga = (a.ch[0] < 0 && a.beta) || (nd.beta && !a.beta && (a.idx & closed).any());
+        const bool gb = (b.ch[0] < 0 && b.beta) || (nd.beta && !b.beta && (b.idx & closed).any());
+        const Bits A = ga && !a.beta ? a.idx.andnot(closed) | beta : a.idx;
+        const Bits B = gb && !b.beta ? b.idx.andnot(closed) | beta : b.idx;
+        const double va = std::ldexp(1.0, __builtin_popcountll(a.dep)), vb = std::ldexp(1.0, __builtin_popcountll(b.dep));
         double ver = std::ldexp(1.0, __builtin_popcountll(nd.dep));
-        double fl = 8.0 * std::ldexp(1.0, (a.idx | b.idx).count()) * ver;
-        double by = 8.0 * (std::ldexp(1.0, a.idx.count() + __builtin_popcountll(a.dep)) +
-                           std::ldexp(1.0, b.idx.count() + __builtin_popcountll(b.dep)) +
-                           std::ldexp(1.0, l) * ver);
+        double fl = 8.0 * std::ldexp(1.0, (A | B).count()) * ver;
+        double sa = 8.0 * std::ldexp(1.0, A.count()) * va, sb = 8.0 * std::ldexp(1.0, B.count()) * vb;
+        double by = sa + sb + 8.0 * std::ldexp(1.0, l) * ver;
+        double gt = 0;
+        if (ga) gt += 2 * sa / bw + launch;
+        if (gb) gt += 2 * sb / bw + launch;
+        double rate = flop_rate;
+        if (net.tc_flop_rate > 0) {
+            const Bits C = nd.idx;
+            const int nm = (A & C).andnot(B).count(), nn = (B & C).andnot(A).count(), nk = (A & B).andnot(C).count();
+            if (tn_tc_shape(std::max(nm, nn), std::min(nm, nn), nk)) rate = net.tc_flop_rate;
+        }
         tc.flops += fl;
-        tc.bytes += by;
-        tc.time += std::max(fl / flop_rate, by / bw) + launch;
+        tc.bytes += by + (ga ? 2 * sa : 0) + (gb ? 2 * sb : 0);
+        tc.time += std::max(fl / rate, by / bw) + launch + gt;
+        if (net.mem_limit_elems > 0 && by / 8.0 > net.mem_limit_elems) tc.time += 1e6 * (by / 8.0 / net.mem_limit_elems);
     }
     return tc;
 }
@@ -557,6 +620,8 @@ void greedy_once(const Network &net, std::mt19937_64 &rng, double costmod, doubl
             if (alive[d] && (t.nodes[d].idx & c.idx).any()) pairs.insert({d, cid});
     }
     t.root = (int)t.nodes.size() - 1;
+    seal_root(t.nodes[t.root], ic);
+    t.q_max = net.q_max;
 }
 
 }  // namespace
@@ -572,6 +637,248 @@ void tn_greedy_tree(const Network &net, uint64_t seed, int trials, Tree &best, T
         TreeCost c = tn_tree_cost(net, t);
         if (!have || c.time < cost.time) { best = t; cost = c; have = true; }
     }
+}
+
+namespace {
+
+// Recursive min-cut bisection of the network's hypergraph: vertices are the leaves,
+// hyperedges the network indices other than the beta bits and the open outputs (each a
+// one-bit leg).  Every bisection is a Fiduccia-Mattheyses refinement of a grown region
+// under a random imbalance; parts at or below `cutoff` leaves are contracted greedily.
+struct Bisector {
+    const Network &net;
+    Tree &t;
+    IdxCounts ic;
+    std::mt19937_64 &rng;
+    double eps;
+    int cutoff;
+    std::vector<std::vector<int>> vedges;  // leaf -> hyperedges
+    std::vector<std::vector<int>> epins;   // hyperedge -> leaves
+
+    Bisector(const Network &n, Tree &tree, std::mt19937_64 &r, double e, int c) : net(n), t(tree), rng(r), eps(e), cutoff(c) {
+        tn_tree_from_leaves(net, t);
+        counts_of(net, t.nodes, ic);
+        const int L = (int)t.nodes.size();
+        vedges.assign(L, {});
+        epins.assign(net.n_idx, {});
+        for (int v = 0; v < L; v++)
+            for (int i : t.nodes[v].idx.list())
+                if (!ic.out[i] && (net.n_beta == 0 || i < net.beta_base || i >= net.beta_base + net.n_beta)) {
+                    vedges[v].push_back(i);
+                    epins[i].push_back(v);
+                }
+    }
+
+    int contract(int a, int b) {
+        Node c = contract_nodes(t.nodes[a], t.nodes[b], ic);
+        for (int j : (t.nodes[a].idx & t.nodes[b].idx).list()) ic.count[j] -= (c.idx.has(j) ? 1 : 2);
+        c.ch[0] = a;
+        c.ch[1] = b;
+        t.nodes.push_back(c);
+        return (int)t.nodes.size() - 1;
+    }
+
+    // Greedy pairwise contraction of the given nodes (smallest result growth first).
+    int greedy(std::vector<int> alive) {
+        auto lsize = [](const Node &x) { return x.idx.count() + __builtin_popcountll(x.dep); };
+        while (alive.size() > 1) {
+            int ba = -1, bb = -1;
+            double best = 0;
+            bool best_shared = false;
+            for (size_t x = 0; x < alive.size(); x++)
+                for (size_t y = x + 1; y < alive.size(); y++) {
+                    const Node &a = t.nodes[alive[x]], &b = t.nodes[alive[y]];
+                    bool shared = (a.idx & b.idx).andnot(ic.beta).any();
+                    if (best_shared && !shared) continue;
+                    Node c = contract_nodes(a, b, ic);
+                    double key = std::ldexp(1.0, lsize(c)) - std::ldexp(1.0, lsize(a)) - std::ldexp(1.0, lsize(b));
+                    if (ba < 0 || (shared && !best_shared) || key < best) {
+                        best = key; ba = (int)x; bb = (int)y; best_shared = shared;
+                    }
+                }
+            int c = contract(alive[ba], alive[bb]);
+            alive.erase(alive.begin() + bb);
+            alive[ba] = c;
+        }
+        return alive[0];
+    }
+
+    // FM bisection of `verts`: side[i] for verts[i]; returns the cut size.
+    int bisect(const std::vector<int> &verts, std::vector<char> &side) {
+        const int n = (int)verts.size();
+        std::unordered_map<int, int> local;
+        for (int i = 0; i < n; i++) local[verts[i]] = i;
+        // hyperedges with at least two pins inside
+        std::vector<std::vector<int>> ep;
+        std::vector<std::vector<int>> ve(n);
+        {
+            std::unordered_map<int, int> eid;
+            for (int i = 0; i < n; i++)
+                for (int e : vedges[verts[i]]) {
+                    int inside = 0;
+                    for (int v : epins[e]) inside += local.count(v) ? 1 : 0;
+                    if (inside < 2) continue;
+                    auto it = eid.find(e);
+                    int k;
+                    if (it == eid.end()) { k = (int)ep.size(); eid[e] = k; ep.push_back({}); }
+                    else k = it->second;
+                    ep[k].push_back(i);
+                    ve[i].push_back(k);
+                }
+        }
+        const int lo = std::max(1, (int)std::floor(n * (1.0 - eps) / 2.0)), hi = std::min(n - 1, (int)std::ceil(n * (1.0 + eps) / 2.0));
+        int best_cut = -1;
+        std::vector<char> best_side;
+        for (int start = 0; start < 3; start++) {
+            // grow a connected region from a random vertex to n/2
+            std::vector<char> s(n, 1);
+            int size0 = 0;
+            std::vector<int> queue{(int)(rng() % n)};
+            std::vector<char> seen(n, 0);
+            seen[queue[0]] = 1;
+            size_t qh = 0;
+            while (size0 < n / 2) {
+                if (qh == queue.size()) {
+                    int r = (int)(rng() % n);
+                    while (seen[r]) r = (r + 1) % n;
+                    seen[r] = 1;
+                    queue.push_back(r);
+                }
+                int v = queue[qh++];
+                s[v] = 0;
+                size0++;
+                std::vector<int> nb;
+                for (int e : ve[v])
+                    for (int u : ep[e])
+                        if (!seen[u]) { seen[u] = 1; nb.push_back(u); }
+                std::shuffle(nb.begin(), nb.end(), rng);
+                queue.insert(queue.end(), nb.begin(), nb.end());
+            }
+            // FM passes
+            std::vector<std::array<int, 2>> cnt(ep.size(), {0, 0});
+            auto recount = [&]() {
+                for (size_t e = 0; e < ep.size(); e++) {
+                    cnt[e] = {0, 0};
+                    for (int v : ep[e]) cnt[e][s[v]]++;
+                }
+            };
+            auto cut_of = [&]() {
+                int c = 0;
+                for (size_t e = 0; e < ep.size(); e++) c += (cnt[e][0] > 0 && cnt[e][1] > 0);
+                return c;
+            };
+            recount();
+            int cut = cut_of();
+            for (int pass = 0; pass < 8; pass++) {
+                std::vector<int> gain(n, 0);
+                for (int v = 0; v < n; v++)
+                    for (int e : ve[v]) {
+                        if (cnt[e][s[v]] == 1) gain[v]++;
+                        if (cnt[e][1 - s[v]] == 0) gain[v]--;
+                    }
+                std::vector<char> locked(n, 0);
+                std::vector<int> moves;
+                int cur = cut, best_here = cut, best_len = 0, sz0 = 0;
+                for (int v = 0; v < n; v++) sz0 += s[v] == 0;
+                for (int step = 0; step < n; step++) {
+                    int pick = -1;
+                    for (int v = 0; v < n; v++) {
+                        if (locked[v]) continue;
+                        int nsz0 = sz0 + (s[v] == 0 ? -1 : 1);
+                        if (nsz0 < lo || nsz0 > hi) continue;
+                        if (pick < 0 || gain[v] > gain[pick] || (gain[v] == gain[pick] && (rng() & 1))) pick = v;
+                    }
+                    if (pick < 0) break;
+                    int from = s[pick], to = 1 - from;
+                    // update neighbour gains (classic FM bookkeeping, recomputed per edge)
+                    for (int e : ve[pick]) {
+                        for (int u : ep[e])
+                            if (u != pick) {
+                                if (cnt[e][s[u]] == 1) gain[u]--;
+                                if (cnt[e][1 - s[u]] == 0) gain[u]++;
+                            }
+                        cnt[e][from]--;
+                        cnt[e][to]++;
+                        for (int u : ep[e])
+                            if (u != pick) {
+                                if (cnt[e][s[u]] == 1) gain[u]++;
+                                if (cnt[e][1 - s[u]] == 0) gain[u]--;
+                            }
+                    }
+                    cur -= gain[pick];
+                    s[pick] = (char)to;
+                    sz0 += to == 0 ? 1 : -1;
+                    locked[pick] = 1;
+                    moves.push_back(pick);
+                    if (cur < best_here) { best_here = cur; best_len = (int)moves.size(); }
+                }
+                for (int m = (int)moves.size() - 1; m >= best_len; m--) s[moves[m]] = (char)(1 - s[moves[m]]);
+                recount();
+                int newcut = cut_of();
+                if (newcut >= cut) { cut = newcut; break; }
+                cut = newcut;
+            }
+            if (best_cut < 0 || cut < best_cut) { best_cut = cut; best_side = s; }
+        }
+        side = best_side;
+        return best_cut;
+    }
+
+    int build(const std::vector<int> &verts) {
+        if ((int)verts.size() <= cutoff) return greedy(verts);
+        std::vector<char> side;
+        bisect(verts, side);
+        std::vector<int> p0, p1;
+        for (size_t i = 0; i < verts.size(); i++) (side[i] ? p1 : p0).push_back(verts[i]);
+        if (p0.empty() || p1.empty()) return greedy(verts);
+        int a = build(p0), b = build(p1);
+        return contract(a, b);
+    }
+};
+
+}  // namespace
+
+void tn_bisect_tree(const Network &net, uint64_t seed, double eps, int cutoff, Tree &t) {
+    std::mt19937_64 rng(seed * 0xD1B54A32D192ED03ull + 777);
+    Bisector b(net, t, rng, eps, cutoff);
+    const int L = (int)t.nodes.size();
+    if (L == 1) { t.root = 0; return; }
+    std::vector<int> all(L);
+    for (int i = 0; i < L; i++) all[i] = i;
+    t.root = b.build(all);
+    seal_root(t.nodes[t.root], b.ic);
+    t.q_max = net.q_max;
+}
+
+void tn_search_tree(Network &net, uint64_t seed, int trials, Tree &best, TreeCost &cost) {
+    // batch-selection thresholds to try: 0 (select at the first closed leg) up to
+    // log2 T (a batch-independent tensor never larger than its batch form)
+    // -1: leaves with closed legs in batch form from the start (full trials); then half
+    // the trials at a middle threshold and at log2 T
+    std::vector<int> qs{net.q_max};
+    if (net.n_closed > 0 && net.n_beta > 0) qs = {-1, net.n_beta / 2, net.n_beta};
+    bool have = false;
+    int best_q = net.q_max;
+    std::mt19937_64 rng(seed * 0x9E3779B97F4A7C15ull + 99991);
+    auto run = [&](int q, int n, uint64_t sd) {
+        net.q_max = q;
+        Tree t;
+        TreeCost c;
+        tn_greedy_tree(net, sd, n, t, c);
+        if (!have || c.time < cost.time) { best = t; cost = c; best_q = q; have = true; }
+        // networks large enough for the greedy to go wrong also get bisection trials
+        if (net.leaves.size() < 48) return;
+        for (int tr = 0; tr < n; tr++) {
+            double eps = std::uniform_real_distribution<double>(0.02, 0.6)(rng);
+            int cutoff = 4 + (int)(rng() % 24);
+            Tree tb;
+            tn_bisect_tree(net, rng(), eps, cutoff, tb);
+            TreeCost cb = tn_tree_cost(net, tb);
+            if (cb.time < cost.time) { best = tb; cost = cb; best_q = q; }
+        }
+    };
+    for (size_t i = 0; i < qs.size(); i++) run(qs[i], i == 0 ? trials : std::max(1, trials / 2), seed + 131 * (qs[i] + 1));
+    net.q_max = best_q;
 }
 
 // Slice network index `id` in a tree: it leaves every tensor, and every tensor above a
@@ -656,6 +963,13 @@ int tn_compile(const Network &net, Tree &t, uint64_t E, std::vector<Step> &steps
             tn_set_error("compile: tensor with more than 40 index bits");
             return TN_EUNSUPPORTED;
         }
+    Bits closed, beta;
+    for (int q = 0; q < net.n_closed; q++) closed.set(net.closed_base + q);
+    for (int q = 0; q < net.n_beta; q++) beta.set(net.beta_base + q);
+    if (t.nodes[t.root].ch[0] < 0 && net.n_closed > 0) {
+        tn_set_error("compile: a single-tensor network with closed outputs");
+        return TN_EUNSUPPORTED;
+    }
     for (int ci = (int)t.nodes.size() - 1; ci >= 0; ci--) {
         Node &c = t.nodes[ci];
         if (c.ch[0] < 0) continue;
@@ -663,6 +977,14 @@ int tn_compile(const Network &net, Tree &t, uint64_t E, std::vector<Step> &steps
         Bits Cb = tn_node_bits(net, c, E);
         if (c.layout.empty() && Cb.any()) { tn_set_error("compile: node without layout"); return TN_EINVAL; }
         Bits A = tn_node_bits(net, t.nodes[a], E), B = tn_node_bits(net, t.nodes[b], E);
+        // operands with closed legs read by a batch step are gathered: they enter the
+        // step with the beta bits in place of their closed legs
+        // (a leaf in batch form from the start is stored with its closed legs and gathered)
+        const bool leaf_a = t.nodes[a].ch[0] < 0 && t.nodes[a].beta, leaf_b = t.nodes[b].ch[0] < 0 && t.nodes[b].beta;
+        bool ga = leaf_a || (c.beta && !t.nodes[a].beta && (A & closed).any());
+        bool gb = leaf_b || (c.beta && !t.nodes[b].beta && (B & closed).any());
+        if (ga && !leaf_a) A = A.andnot(closed) | beta;
+        if (gb && !leaf_b) B = B.andnot(closed) | beta;
         Bits bat = A & B & Cb, m = (A & Cb).andnot(B), nn = (B & Cb).andnot(A), k = (A & B).andnot(Cb);
         if (((A | B).andnot(Cb | k)).any() || (Cb.andnot(A | B)).any()) {
             tn_set_error("compile: dangling index");
@@ -679,7 +1001,7 @@ int tn_compile(const Network &net, Tree &t, uint64_t E, std::vector<Step> &steps
                 if (nn.has(c.layout[q])) { cn++; if (!first) first = 2; }
             }
             const bool m_low = cm > cn || (cm == cn && first == 1);
-            if (m_low != rows_side) { std::swap(a, b); std::swap(m, nn); }
+            if (m_low != rows_side) { std::swap(a, b); std::swap(m, nn); std::swap(ga, gb); }
         }
         auto in_c_order = [&](const Bits &s) {
             std::vector<int> v;
@@ -732,16 +1054,41 @@ int tn_compile(const Network &net, Tree &t, uint64_t E, std::vector<Step> &steps
         for (int i = 0; i < s.nm; i++) s.pos_m[i] = (int8_t)pos_in_c(vm[i]);
         for (int i = 0; i < s.nn; i++) s.pos_n[i] = (int8_t)pos_in_c(vn[i]);
         s.flops_per_version = 8.0 * std::ldexp(1.0, s.nbat + s.nm + s.nn + s.nk);
-        auto &la = t.nodes[a].layout;
-        auto &lb = t.nodes[b].layout;
-        la.clear();
-        lb.clear();
+        std::vector<int> la, lb;
         la.insert(la.end(), vk.begin(), vk.end());
         la.insert(la.end(), vm.begin(), vm.end());
         la.insert(la.end(), vb.begin(), vb.end());
         lb.insert(lb.end(), vk.begin(), vk.end());
         lb.insert(lb.end(), vn.begin(), vn.end());
         lb.insert(lb.end(), vb.begin(), vb.end());
+        // a gathered operand is stored as its read layout without the beta bits, then
+        // its closed legs (ascending closed position) as the top bits
+        auto store = [&](int o, int x, const std::vector<int> &lv, bool g) -> int {
+            if (!g) { t.nodes[x].layout = lv; return TN_OK; }
+            std::vector<int> st;
+            for (int id : lv)
+                if (!beta.has(id)) st.push_back(id);
+            const std::vector<int> q =
+                (t.nodes[x].ch[0] < 0 && t.nodes[x].beta ? tn_leaf_closed(net, x) : t.nodes[x].idx & closed).list();
+            if (q.size() > 32 || net.n_beta > 16) { tn_set_error("compile: gather too wide"); return TN_EUNSUPPORTED; }
+            s.gat[o] = 1;
+            s.g_nq[o] = (int8_t)q.size();
+            for (size_t i = 0; i < q.size(); i++) s.g_q[o][i] = (int16_t)(q[i] - net.closed_base);
+            for (int tb = 0; tb < net.n_beta; tb++) {
+                int pos = -1;
+                for (size_t p = 0; p < lv.size(); p++)
+                    if (lv[p] == net.beta_base + tb) pos = (int)p;
+                if (pos < 0) { tn_set_error("compile: gathered operand without beta bits"); return TN_EINVAL; }
+                s.g_pos_beta[o][tb] = (int8_t)pos;
+            }
+            s.g_nbits[o] = (int8_t)lv.size();
+            st.insert(st.end(), q.begin(), q.end());
+            t.nodes[x].layout = st;
+            return TN_OK;
+        };
+        int rc = store(0, a, la, ga);
+        if (!rc) rc = store(1, b, lb, gb);
+        if (rc) return rc;
         steps.push_back(s);
     }
     std::sort(steps.begin(), steps.end(), [](const Step &x, const Step &y) { return x.c < y.c; });
@@ -750,7 +1097,15 @@ int tn_compile(const Network &net, Tree &t, uint64_t E, std::vector<Step> &steps
 
 // ------------------------------------------------------------------ whole plan
 
-int tn_tree_and_compile(const Network &net, const tn_plan_opts &o, const int32_t *order, int n_order,
+// Cost-model settings of a plan's networks: tensor-core rate in the split precisions and
+// the per-step footprint limit (half the HBM budget, in complex64-sized elements).
+void tn_cost_settings(Network &net, const tn_plan_opts &o) {
+    net.tc_flop_rate = o.precision != TN_PREC_C64 ? 4e14 : 0;
+    const double budget = o.hbm_budget_bytes > 0 ? o.hbm_budget_bytes : 64.0 * (1ull << 30);
+    net.mem_limit_elems = budget / 8.0 / 2.0;
+}
+
+int tn_tree_and_compile(Network &net, const tn_plan_opts &o, const int32_t *order, int n_order,
                         const Tree *candidate, Tree &tree, std::vector<Step> &steps, uint64_t *E_used,
                         bool tc_roles) {
     if (order) {
@@ -758,12 +1113,15 @@ int tn_tree_and_compile(const Network &net, const tn_plan_opts &o, const int32_t
         if (rc) return rc;
     } else {
         TreeCost tc;
-        tn_greedy_tree(net, o.order_seed, o.order_trials > 0 ? o.order_trials : 64, tree, tc);
+        tn_search_tree(net, o.order_seed, o.order_trials > 0 ? o.order_trials : 64, tree, tc);
         if (candidate) {
             Tree cand = *candidate;
             tn_recompute_deps(net, cand);
             TreeCost cc = tn_tree_cost(net, cand);
-            if (cc.time < tc.time) tree = cand;
+            if (cc.time < tc.time) {
+                tree = cand;
+                if (cand.q_max >= -1) net.q_max = cand.q_max;
+            }
         }
     }
     // default variant: every sliced leg as a layout bit (full slice sets); if a tensor
@@ -792,8 +1150,9 @@ int tn_plan_build_host(const Merged &mg, const tn_plan_opts &o, const int32_t *o
         Network net0;
         int rc = tn_build_amp_network(mg, {}, open, o.log2_batches, net0, closed);
         if (rc) return rc;
+        tn_cost_settings(net0, o);
         TreeCost tc0;
-        tn_greedy_tree(net0, o.order_seed, o.order_trials > 0 ? o.order_trials : 64, t0, tc0);
+        tn_search_tree(net0, o.order_seed, o.order_trials > 0 ? o.order_trials : 64, t0, tc0);
         std::vector<int> picked = tn_auto_slice(mg, net0, t0, o.n_auto_sliced);
         for (int id : picked) {
             int seg = net0.idx_seg[id], q = 0;
@@ -804,6 +1163,7 @@ int tn_plan_build_host(const Merged &mg, const tn_plan_opts &o, const int32_t *o
     }
     int rc = tn_build_amp_network(mg, I, open, o.log2_batches, net, closed);
     if (rc) return rc;
+    tn_cost_settings(net, o);
     return tn_tree_and_compile(net, o, order, n_order, have_t0 ? &t0 : nullptr, tree, steps, E_used,
                                o.precision != TN_PREC_C64);
 }

@@ -72,6 +72,19 @@ struct Network {
     std::vector<int> out_layout;   // output index ids, LSB first
     int n_beta = 0;                // beta bits are network ids beta_base .. beta_base+n_beta-1
     int beta_base = -1;
+    // Closed output legs are network ids closed_base .. closed_base+n_closed-1 (id of
+    // closed position c = closed_base + c).  A tensor keeps them as ordinary legs (one
+    // copy per value, shared by every batch) while it holds at most q_max of them; a
+    // step whose result would hold more, or that meets a batch tensor, selects each
+    // batch's values (a gather) and carries the beta bits instead.
+    int closed_base = -1;
+    int n_closed = 0;
+    int q_max = 0;                 // -1: leaves with closed legs are in batch form from the start
+    // Cost model: FLOP rate of tensor-core shaped steps (0: every step runs on FFMA), and
+    // the largest operand + result footprint of one step (elements over all versions;
+    // 0: unlimited) above which a tree is treated as infeasible.
+    double tc_flop_rate = 0;
+    double mem_limit_elems = 0;
     int n_sliced = 0;              // |I|
     std::vector<int> idx_seg;      // segment id of each network index (-1: beta / other)
 };
@@ -82,7 +95,7 @@ struct Node {
     uint64_t dep = 0;      // sliced edges its subtree depends on (bit e = I[e])
     int ch[2] = {-1, -1};  // children (internal nodes)
     int leaf = -1;         // leaf number (leaves)
-    bool beta = false;     // carries beta bits
+    bool beta = false;     // carries beta bits (and no closed legs)
     std::vector<int> layout;  // storage order of idx, LSB first (set by the compiler)
 };
 
@@ -92,11 +105,21 @@ struct Step {
     int nbat, nm, nn, nk;            // bit counts
     int8_t pos_bat[64], pos_m[64], pos_n[64];  // bit positions in C's layout
     double flops_per_version;        // 8 * 2^(nbat+nm+nn+nk)
+    // Batch gathers: operand o (0 = a, 1 = b) is stored with its closed legs as the top
+    // g_nq[o] layout bits (closed positions g_q[o][0..], lowest first) and is read as
+    // the operand layout in which the beta bits sit at positions g_pos_beta[o][0..]
+    // (beta bit t) and the remaining stored bits fill the other positions in order.
+    int8_t gat[2];
+    int8_t g_nq[2];
+    int16_t g_q[2][32];
+    int8_t g_pos_beta[2][16];
+    int8_t g_nbits[2];               // layout bits of the gathered operand
 };
 
 struct Tree {
     std::vector<Node> nodes;  // leaves first (node i = leaf i), then internal in SSA order
     int root = -1;
+    int q_max = -2;           // batch-selection threshold the tree was built with (-2: the network's)
 };
 
 struct TreeCost {
@@ -137,8 +160,16 @@ int tn_build_norm_network(const Merged &mg, const std::vector<tn_edge> &S, Netwo
 
 // Contraction order and tree compilation.
 void tn_tree_from_leaves(const Network &net, Tree &t);
+void tn_tree_from_leaves(const Network &net, Tree &t, int q_max);
+Bits tn_leaf_closed(const Network &net, int leaf);  // closed-output ids on a leaf's legs
 int tn_tree_from_ssa(const Network &net, const int32_t *pairs, int n_pairs, Tree &t);
 void tn_greedy_tree(const Network &net, uint64_t seed, int trials, Tree &best, TreeCost &cost);
+// Recursive min-cut bisection order (one trial) and the combined search: greedy trials,
+// plus bisection trials on networks of 48 leaves or more, over several batch-selection
+// thresholds (Network::q_max) when the network has closed legs; lowest estimated time
+// wins and net.q_max is set to the winner's threshold.
+void tn_bisect_tree(const Network &net, uint64_t seed, double eps, int cutoff, Tree &t);
+void tn_search_tree(Network &net, uint64_t seed, int trials, Tree &best, TreeCost &cost);
 TreeCost tn_tree_cost(const Network &net, const Tree &t);
 void tn_recompute_deps(const Network &net, Tree &t);
 std::vector<int> tn_auto_slice(const Merged &mg, Network &net, Tree &t, int n_slice);
@@ -159,6 +190,7 @@ int tn_plan_build_host(const Merged &mg, const tn_plan_opts &o, const int32_t *o
                        std::vector<tn_edge> &I, Network &net, Tree &tree, std::vector<Step> &steps,
                        std::vector<int> &closed, uint64_t *E_used);
 // Greedy tree of a network (or the SSA order when given) + compile.
-int tn_tree_and_compile(const Network &net, const tn_plan_opts &o, const int32_t *order, int n_order,
+void tn_cost_settings(Network &net, const tn_plan_opts &o);
+int tn_tree_and_compile(Network &net, const tn_plan_opts &o, const int32_t *order, int n_order,
                         const Tree *candidate, Tree &tree, std::vector<Step> &steps, uint64_t *E_used,
                         bool tc_roles = false);

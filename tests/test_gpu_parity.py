@@ -243,8 +243,10 @@ def test_hbm_budget_enforced():
 @pytest.mark.parametrize("prec", ["c64", "bf16x2"])
 @pytest.mark.parametrize("grid,f", [((3, 4, 8), 0.25), ((4, 5, 12), 1 / 64)])
 def test_partial_norms(grid, f, prec):
-    """R of Fig. 1's network in the plan's contraction precision: within 1e-5 (complex64)
-    or 1e-3 (split) of max R; S identical to the oracle's Alg. 2."""
+    """R of Fig. 1's network in the plan's contraction precision: within 1e-4 (complex64)
+    or 1e-3 (split) of max R; S identical to the oracle's Alg. 2.  R is quadratic in the
+    amplitudes of C1, so the complex64 amplitude bound (1e-4 of the RMS) allows about
+    twice that relative error in R; 1e-4 of max R is the matching bound."""
     P = pkg()
     circ = cg.sycamore_grid(*grid, seed=0)
     n = grid[0] * grid[1]
@@ -258,7 +260,7 @@ def test_partial_norms(grid, f, prec):
     S_ref = oracle.sliced_vertex_select(circ, I[:40], oracle.k0_for(f))
     assert [I[i] for i in S_idx] == S_ref
     R_ref = oracle.norms(circ, S_ref)
-    tol = 1e-5 if prec == "c64" else 1e-3
+    tol = 1e-4 if prec == "c64" else 1e-3
     assert np.abs(R - R_ref).max() < tol * R_ref.max()
     assert abs(R.sum() - 1) < tol
 
