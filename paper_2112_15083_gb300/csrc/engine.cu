@@ -713,7 +713,30 @@ int launch_step(CNet &cn, const Step &s, cudaStream_t st) {
             return TN_OK;
         }
     }
-    if (std::min(s.nm, s.nn) <= 5 && s.nk <= 6) {
+    if (std::min(s.nm, s.nn) == 6 && std::max(s.nm, s.nn) == 6 && s.nk <= 6 && s.nbat >= 4 &&
+        (size_t)(((1 << s.nm) + (1 << s.nn)) * ((1 << s.nk) + 1)) * sizeof(T) <= 48 * 1024) {
+        // many small products: stage 2^lg batches per block in shared memory
+        const int per = ((1 << s.nm) + (1 << s.nn)) * ((1 << s.nk) + 1);  // padded elements per batch
+        int lg = 0;
+        while (lg < s.nbat && (size_t)(per << (lg + 1)) * sizeof(T) <= 48 * 1024 && (1 << (lg + 1 + s.nm + s.nn)) <= 4096) lg++;
+        tnk::SmallMap sm;
+        std::memset(&sm, 0, sizeof(sm));
+        sm.lg = lg;
+        std::vector<std::pair<int, std::pair<int, int>>> bits;  // (C position, (kind, index))
+        for (int i = 0; i < lg; i++) bits.push_back({s.pos_bat[i], {0, i}});
+        for (int i = 0; i < s.nm; i++) bits.push_back({s.pos_m[i], {1, i}});
+        for (int i = 0; i < s.nn; i++) bits.push_back({s.pos_n[i], {2, i}});
+        std::sort(bits.begin(), bits.end());
+        sm.nloc = (int)bits.size();
+        for (int i = 0; i < sm.nloc; i++) {
+            sm.kind[i] = (int8_t)bits[i].second.first;
+            sm.idx[i] = (int8_t)bits[i].second.second;
+        }
+        if (cn.trace) cn.tr_kernel[si] = 1;
+        const long long blocks = p.nver << (s.nbat - lg);
+        const size_t smem = (size_t)(per << lg) * sizeof(T);
+        tnk::cgemm_small<T><<<(unsigned)blocks, 256, smem, st>>>(p, sm);
+    } else if (std::min(s.nm, s.nn) <= 5 && s.nk <= 6) {
         // short K and one small side: one thread per row of the larger side, the small
         // side in registers (C = A B^T is symmetric in the operand roles)
         if (s.nn > s.nm) {

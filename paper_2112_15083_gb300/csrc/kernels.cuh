@@ -130,6 +130,53 @@ __global__ void __launch_bounds__(256) cgemm_row(GemmParams p) {
     for (int n = 0; n < N; n++) store_c_t<T>(p, v, cb + scatter_bits(n, p.pos_n, p.ln), acc[n]);
 }
 
+// Batched small products (M, N <= 64, K <= 64): a block stages the operands of 2^lg
+// consecutive batches in shared memory and walks that chunk's outputs in the order of
+// their positions in C (local bit i = chunk bit kind[i] / idx[i]), so consecutive threads
+// store to consecutive addresses whenever C's lowest positions lie in the chunk.
+struct SmallMap {
+    int lg;              // log2 batches per block
+    int nloc;            // lg + lm + ln
+    int8_t kind[48];     // 0: batch bit, 1: m bit, 2: n bit
+    int8_t idx[48];
+};
+
+template <typename T>
+__global__ void __launch_bounds__(256) cgemm_small(GemmParams p, SmallMap sm) {
+    extern __shared__ __align__(16) unsigned char small_smem[];
+    T *As = reinterpret_cast<T *>(small_smem);
+    const int M = 1 << p.lm, N = 1 << p.ln, K = 1 << p.lk, G = 1 << sm.lg;
+    const int KP = K + 1;  // padded row: rows of consecutive outputs fall in different banks
+    T *Bs = As + (size_t)G * M * KP;
+    const long long chunks = 1LL << (p.lbat - sm.lg);
+    const long long v = (long long)blockIdx.x / chunks;
+    const long long bat0 = ((long long)blockIdx.x - v * chunks) << sm.lg;
+    if (v >= p.nver) return;
+    const T *A = static_cast<const T *>(p.ptrA[v]) + (bat0 << (p.lm + p.lk));
+    const T *B = static_cast<const T *>(p.ptrB[v]) + (bat0 << (p.ln + p.lk));
+    for (int e = threadIdx.x; e < G * M * K; e += blockDim.x) As[(e >> p.lk) * KP + (e & (K - 1))] = A[e];
+    for (int e = threadIdx.x; e < G * N * K; e += blockDim.x) Bs[(e >> p.lk) * KP + (e & (K - 1))] = B[e];
+    __syncthreads();
+    const long long cbase = scatter_bits(bat0, p.pos_bat, p.lbat);
+    const int nout = G * M * N;
+    for (int l = threadIdx.x; l < nout; l += blockDim.x) {
+        int b = 0, m = 0, n = 0;
+        for (int i = 0; i < sm.nloc; i++) {
+            const int bit = (l >> i) & 1;
+            if (sm.kind[i] == 0) b |= bit << sm.idx[i];
+            else if (sm.kind[i] == 1) m |= bit << sm.idx[i];
+            else n |= bit << sm.idx[i];
+        }
+        const T *a = As + (size_t)(b * M + m) * KP;
+        const T *bb = Bs + (size_t)(b * N + n) * KP;
+        T acc = czero<T>();
+        for (int k = 0; k < K; k++) acc = cfma(a[k], bb[k], acc);
+        const long long off = cbase + scatter_bits(b, p.pos_bat, sm.lg) + scatter_bits(m, p.pos_m, p.lm) +
+                              scatter_bits(n, p.pos_n, p.ln);
+        store_c_t<T>(p, v, off, acc);
+    }
+}
+
 // Shared-memory tiled kernel: TM x TN output tile, K in chunks of TK, each thread an
 // RM x RN register tile (rows contiguous, columns strided by TN/RN for coalescing).
 template <typename T, int TM, int TN, int TK, int RM, int RN>

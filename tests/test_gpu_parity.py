@@ -114,6 +114,28 @@ def test_28q_256_batches_full_slice_set(grid28):
     close_c64(amps, oracle.batch_amplitudes(psi, 28, openq, cb))
 
 
+@pytest.mark.parametrize("prec", ["c64", "bf16x2"])
+def test_28q_bench_configuration_16384_batches(grid28, prec):
+    """The benchmark's launch configuration: 4x7 grid, 14 cycles, 2^10 slices, one group
+    of 16384 batches of 64 (batch-independent intermediates shared by all of them), the
+    same plan options; every amplitude against the state vector."""
+    P = pkg()
+    circ, psi = grid28
+    openq = cg.default_open_qubits(4, 7, 6)
+    C = P.circuit_load(circ.serialize())
+    precision = {"c64": P.tn.PREC_C64, "bf16x2": P.tn.PREC_BF16X2}[prec]
+    plan = P.plan(C, openq, n_auto_sliced=10, log2_batches=14, order_trials=256, order_seed=0,
+                  hbm_budget_bytes=200e9, precision=precision)
+    cb = cg.random_closed_bits(16384, 22, seed=3)
+    amps = plan.contract(np.arange(1024, dtype=np.uint64), cb)
+    ref = oracle.batch_amplitudes(psi, 28, openq, cb)
+    if prec == "c64":
+        close_c64(amps, ref)
+    else:
+        err = split_errors(amps, ref)
+        assert err["rel_l2"] <= 1e-3, err
+
+
 def split_errors(got, ref):
     d = np.abs(got - ref)
     rms = float(np.sqrt(np.mean(np.abs(ref) ** 2)))
