@@ -269,7 +269,16 @@ def run_ours(args):
     else:
         tot_ms_max, accepted_all = tot_ms, float(accepted)
     value = accepted_all / (tot_ms_max / 1e3)
+    # the last trace entry is the FP64 slice sum (kernel 2); the rest are contraction steps
+    ssum = [s for s in trace if s["kernel"] == 2]
+    trace = [s for s in trace if s["kernel"] != 2]
     flops_step = sum(s["flops_per_launch"] for s in trace)
+    slice_sum = None
+    if ssum and ssum[0]["launches"]:
+        s0 = ssum[0]
+        ms1 = s0["ms"] / s0["launches"]
+        slice_sum = {"ms": round(ms1, 3), "fp64_gflops": round(s0["flops_per_launch"] / (ms1 / 1e3) / 1e9, 1),
+                     "gbs": round(s0["bytes_per_launch"] / (ms1 / 1e3) / 1e9, 1)}
 
     # dominant kernel from the live per-step events
     dom = max(trace, key=lambda s: s["ms"])
@@ -338,8 +347,9 @@ def run_ours(args):
             "data": "synthetic", "config": workload_config(args),
             "fidelity": F, "contraction_tflops": flops_step * args.steps / (tot_ms / 1e3) / 1e12,
             "flops_per_step": flops_step, "plan": info, "clocks": clk, "roofline": roofline,
-            "cpu_baseline": cpu, "e2e": e2e, "top_steps": top_steps,
-            "gpu_launches": args.steps * (len(trace) + 4),
+            "cpu_baseline": cpu, "e2e": e2e, "top_steps": top_steps, "slice_sum": slice_sum,
+            # per step: contraction launches, batch gathers, slice sum, batch draws, sampler
+            "gpu_launches": args.steps * (len(trace) + sum(s["gathers"] for s in trace) + 3),
         }
         print(json.dumps(line), flush=True)
     if world > 1:

@@ -75,6 +75,14 @@ typedef struct {
     double hbm_budget_bytes; /* device working-set limit per call; <= 0: 64 GiB */
     double max_norm_flops;   /* tn_partial_norms refuses norm networks above this many
                                 algorithmic FLOPs (TN_EUNSUPPORTED); <= 0: 2e15 */
+    int32_t autotune;        /* 1 (default): the first execution of each step shape times
+                                every applicable kernel variant (FFMA tile shape, row or
+                                staged kernel, tensor-core tile width) and keeps the
+                                fastest; the choice is cached per shape for the process.
+                                0: fixed shape rules.  k >= 2: step i runs variant
+                                (i + k - 2) mod (its variant count), so that tests can run
+                                every variant.  All variants accumulate each output over k
+                                in the same order. */
     void *stream;            /* cudaStream_t; NULL = legacy default stream */
     tn_alloc_fn alloc;       /* optional device allocator */
     tn_free_fn free;
@@ -251,9 +259,10 @@ int tn_sample_step(tn_plan_h p, const uint64_t *slices, int64_t n_slices, double
                    int32_t flags);
 
 /* Tracing: when on, every execution records CUDA events around each contraction step
- * on the plan's stream.  tn_trace_read synchronises and reports, per step, the launches,
- * the summed device time, and the algorithmic FLOPs (8 per complex multiply-add) and
- * bytes (operands read + result written, complex64) of one launch. */
+ * and around the FP64 slice sum on the plan's stream.  tn_trace_read synchronises and
+ * reports, per step, the launches, the summed device time, and the algorithmic FLOPs
+ * (8 per complex multiply-add) and bytes (operands read + result written, complex64) of
+ * one launch; entry n_steps (the last) is the slice sum (FLOPs = FP64 additions). */
 typedef struct {
     int32_t step;
     int32_t launches;
@@ -262,7 +271,9 @@ typedef struct {
     double bytes_per_launch;
     int32_t nbat, nm, nn, nk;
     int64_t nver;
-    int32_t kernel; /* 0: row kernel, 1..: tile kernel variant */
+    int32_t kernel; /* 0: row kernel, 1: staged small products, 2: FP64 slice sum,
+                       9128: tensor-core kernel, TM*1000+TN: FFMA tile kernel */
+    int32_t gathers; /* batch-gather launches that precede the step (0 or 1) */
 } tn_step_trace;
 int tn_trace_enable(tn_plan_h p, int32_t on);
 int tn_trace_read(tn_plan_h p, tn_step_trace *out, int32_t cap, int32_t *n_out);

@@ -10,6 +10,7 @@
 #include <array>
 #include <cmath>
 #include <cstring>
+#include <map>
 #include <mutex>
 #include <numeric>
 #include <unordered_map>
@@ -124,6 +125,9 @@ struct CNet {
     std::vector<int> fmt;      // per node: storage format (tnk::OutFmt)
     std::vector<float> scale;  // per node: stored value = true value * scale
     std::vector<char> use_tc;  // per step: tcgen05 kernel
+    std::vector<int> variant;  // per step: kernel variant (-1: not chosen yet)
+    int autotune = 1;          // 1: time the applicable variants of unseen step shapes;
+                               // 0: fixed shape rules; k >= 2: variant (step + k - 2) mod count
     DBuf err;                  // device error word of the bounded waits
     int *d_err = nullptr;
     // CUDA graphs of one execution (index: stem reuse off / on), valid for the current
@@ -237,14 +241,18 @@ int get_encoder() {
 // (a version is 8 bytes per element: four planes), tiles of 32 (K) x 128 rows, 64-byte
 // swizzle; out-of-range rows/columns read as zero.
 int encode_operand(CUtensorMap *m, const void *base, int lk, int lrows, int lbat, long long nver, bool fp16,
-                   bool fold = false) {
+                   bool fold = false, int box_rows = 128) {
     RC(get_encoder());
     cuuint64_t dims[4] = {(cuuint64_t)1 << lk, (cuuint64_t)1 << lrows, (cuuint64_t)4 << lbat, (cuuint64_t)nver};
     cuuint64_t strides[3] = {((cuuint64_t)1 << lk) * 2, ((cuuint64_t)1 << (lk + lrows)) * 2,
                              ((cuuint64_t)1 << (lk + lrows + lbat)) * 8};
-    // folded: one box = all rows of 128 >> lrows consecutive versions (128 rows total)
-    cuuint32_t box[4] = {(cuuint32_t)tnk::kTcBK, fold ? (cuuint32_t)1 << lrows : 128u, 1,
-                         fold ? (cuuint32_t)(128 >> lrows) : 1u};
+    // folded: one box = all rows of box_rows >> lrows consecutive versions (box_rows rows)
+    if (fold && lrows > __builtin_ctz((unsigned)box_rows)) {
+        tn_set_error("encode_operand: folded operand wider than the tile");
+        return TN_EINVAL;
+    }
+    cuuint32_t box[4] = {(cuuint32_t)tnk::kTcBK, fold ? (cuuint32_t)1 << lrows : (cuuint32_t)box_rows, 1,
+                         fold ? (cuuint32_t)(box_rows >> lrows) : 1u};
     cuuint32_t es[4] = {1, 1, 1, 1};
     CUresult r = g_encode(m, fp16 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT16 : CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 4,
                           const_cast<void *>(base), dims, strides, box, es, CU_TENSOR_MAP_INTERLEAVE_NONE,
@@ -268,6 +276,8 @@ int setup_leaves(DevMem &mem, CNet &cn) {
     if (!smem_set) {
         CK(cudaFuncSetAttribute(tnk::tc_cgemm<128, 3>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                 tnk::TcSmem<128, 3>::kBytes));
+        CK(cudaFuncSetAttribute(tnk::tc_cgemm<64, 4>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                tnk::TcSmem<64, 4>::kBytes));
         smem_set = true;
     }
     for (auto &b : cn.leaf_src) release(mem, b);
@@ -585,10 +595,15 @@ int prepare_call(DevMem &mem, CNet &cn, const std::vector<uint64_t> &slices, dou
         CUtensorMap ma, mb;
         const void *ra = s.gat[0] ? static_cast<const char *>(cn.arena.p) + cp.goff[i][0] : region(s.a);
         const void *rb = s.gat[1] ? static_cast<const char *>(cn.arena.p) + cp.goff[i][1] : region(s.b);
+        // B for 128- and 64-column tiles (a folded B narrower than 64 columns only in the former)
+        CUtensorMap mb64;
         RC(encode_operand(&ma, ra, s.nk, s.nm, s.nbat, version_count(s.a), f16, cp.fold[i] == 1));
         RC(encode_operand(&mb, rb, s.nk, s.nn, s.nbat, version_count(s.b), f16, cp.fold[i] == 2));
+        if (cp.fold[i] == 2 && s.nn > 6) mb64 = mb;
+        else RC(encode_operand(&mb64, rb, s.nk, s.nn, s.nbat, version_count(s.b), f16, cp.fold[i] == 2, 64));
         cp.maps.push_back(ma);
         cp.maps.push_back(mb);
+        cp.maps.push_back(mb64);
         const uint64_t Da = nodes[s.a].dep & cn.E, Db = nodes[s.b].dep & cn.E;
         for (uint64_t w : vals[s.c]) cp.vidx.push_back(version_index(s.a, w & Da));
         for (uint64_t w : vals[s.c]) cp.vidx.push_back(version_index(s.b, w & Db));
@@ -652,11 +667,90 @@ int prepare_call(DevMem &mem, CNet &cn, const std::vector<uint64_t> &slices, dou
     CK(cudaStreamSynchronize(mem.stream));
     cp.valid = true;
     cn.cp = std::move(cp);
+    cn.variant.assign(cn.steps.size(), -1);
+    return TN_OK;
+}
+
+// Kernel variants of a step (ids as in tn_step_trace.kernel): 0 row kernel, 1 staged
+// small products, TM*1000+TN FFMA tile, 9128 / 9064 tensor-core tile of 128 / 64 columns.
+constexpr int kVarRow = 0, kVarSmall = 1, kVarTc128 = 9128, kVarTc64 = 9064;
+constexpr int kTiles[7][2] = {{128, 64}, {64, 64}, {128, 32}, {64, 32}, {32, 32}, {128, 16}, {16, 16}};
+
+bool small_fits(const Step &s, size_t esz) {
+    return s.nm <= 6 && s.nn <= 6 && s.nk <= 6 && s.nbat >= 4 &&
+           (size_t)(((1 << s.nm) + (1 << s.nn)) * ((1 << s.nk) + 1)) * esz <= 48 * 1024;
+}
+
+// Every variant that can run step si (the tensor-core ones when its operands are split).
+std::vector<int> step_variants(const CNet &cn, size_t si) {
+    const Step &s = cn.steps[si];
+    std::vector<int> v;
+    if (!cn.use_tc.empty() && cn.use_tc[si]) return {kVarTc128, kVarTc64};
+    if (std::min(s.nm, s.nn) <= 5 && s.nk <= 6) v.push_back(kVarRow);
+    if (small_fits(s, (size_t)cn.elem)) v.push_back(kVarSmall);
+    for (auto &t : kTiles)
+        if (t[0] == 16 || ((2LL << s.nm) >= t[0] && (2LL << s.nn) >= t[1])) v.push_back(t[0] * 1000 + t[1]);
+    return v;
+}
+
+// The fixed shape rules used without autotuning.
+int default_variant(const CNet &cn, size_t si) {
+    const Step &s = cn.steps[si];
+    if (!cn.use_tc.empty() && cn.use_tc[si]) return kVarTc128;
+    if (std::min(s.nm, s.nn) == 6 && std::max(s.nm, s.nn) == 6 && small_fits(s, (size_t)cn.elem)) return kVarSmall;
+    if (std::min(s.nm, s.nn) <= 5 && s.nk <= 6) return kVarRow;
+    if (s.nm >= 7 && s.nn >= 6) return 128064;
+    if (s.nm >= 6 && s.nn >= 6) return 64064;
+    if (s.nm >= 7 && s.nn >= 5) return 128032;
+    if (s.nm >= 6 && s.nn >= 5) return 64032;
+    if (s.nm >= 5 && s.nn >= 5) return 32032;
+    if (s.nm >= 7) return 128016;
+    return 16016;
+}
+
+template <int BN, int ST>
+int launch_tc(CNet &cn, const Step &s, size_t si, const tnk::GemmParams &p, cudaStream_t st) {
+    const CallPlan &cp = cn.cp;
+    tnk::TcParams tp;
+    std::memset(&tp, 0, sizeof(tp));
+    tp.lm = s.nm;
+    tp.ln = s.nn;
+    tp.lk = s.nk;
+    tp.lbat = s.nbat;
+    tp.out_fmt = p.out_fmt;
+    tp.in_fp16 = cn.fmt[s.a] == tnk::OUT_SPLIT_FP16;
+    tp.out_scale = p.out_scale;
+    tp.err = cn.d_err;
+    tp.c_plane = p.c_vstride;
+    for (int i = 0; i < s.nbat; i++) tp.pos_bat[i] = s.pos_bat[i];
+    for (int i = 0; i < s.nm; i++) tp.pos_m[i] = s.pos_m[i];
+    for (int i = 0; i < s.nn; i++) tp.pos_n[i] = s.pos_n[i];
+    using Lay = tnk::TcSmem<BN, ST>;
+    const int fold = cp.fold.empty() ? 0 : cp.fold[si];
+    const int lbn = __builtin_ctz(BN);
+    const int ltm = std::min(s.nm, 7), ltn = std::min(s.nn, lbn);
+    long long tiles_m = 1LL << (s.nm - ltm), tiles_n = 1LL << (s.nn - ltn), tiles_v = p.nver;
+    if (fold == 1) { const long long vm = 128 >> s.nm; tiles_m = (p.nver + vm - 1) / vm; tiles_v = 1; }
+    if (fold == 2) {
+        if (s.nn > lbn) { tn_set_error("tensor-core tile narrower than a folded operand"); return TN_EINVAL; }
+        const long long vn = BN >> s.nn;
+        tiles_n = (p.nver + vn - 1) / vn;
+        tiles_v = 1;
+    }
+    const long long tiles = (tiles_m * tiles_n << s.nbat) * tiles_v;
+    const long long blocks = std::min<long long>(tiles, num_sms());
+    tp.C = p.C;
+    tp.nver = (int)p.nver;
+    tp.fold = fold;
+    tp.vidx = static_cast<const int *>(cn.vidx_dev.p) + cp.vidx_off[si];
+    const CUtensorMap *m = &cp.maps[cp.map_off[si]];
+    tnk::tc_cgemm<BN, ST><<<(unsigned)blocks, tnk::kTcThreads, Lay::kBytes, st>>>(m[0], m[BN == 128 ? 1 : 2], tp);
+    CK(cudaGetLastError());
     return TN_OK;
 }
 
 template <typename T>
-int launch_step(CNet &cn, const Step &s, cudaStream_t st) {
+int launch_variant(CNet &cn, const Step &s, cudaStream_t st, int var) {
     const CallPlan &cp = cn.cp;
     const auto &nodes = cn.tree.nodes;
     tnk::GemmParams p;
@@ -678,44 +772,17 @@ int launch_step(CNet &cn, const Step &s, cudaStream_t st) {
     const size_t si = &s - cn.steps.data();
     p.out_fmt = cn.fmt[s.c];
     p.out_scale = cn.scale[s.c] / (cn.scale[s.a] * cn.scale[s.b]);
-    if constexpr (sizeof(T) == sizeof(float2)) {
-        if (!cn.use_tc.empty() && cn.use_tc[si]) {
-            if (cn.trace) cn.tr_kernel[si] = 9128;
-            tnk::TcParams tp;
-            std::memset(&tp, 0, sizeof(tp));
-            tp.lm = s.nm;
-            tp.ln = s.nn;
-            tp.lk = s.nk;
-            tp.lbat = s.nbat;
-            tp.out_fmt = p.out_fmt;
-            tp.in_fp16 = cn.fmt[s.a] == tnk::OUT_SPLIT_FP16;
-            tp.out_scale = p.out_scale;
-            tp.err = cn.d_err;
-            tp.c_plane = p.c_vstride;
-            for (int i = 0; i < s.nbat; i++) tp.pos_bat[i] = s.pos_bat[i];
-            for (int i = 0; i < s.nm; i++) tp.pos_m[i] = s.pos_m[i];
-            for (int i = 0; i < s.nn; i++) tp.pos_n[i] = s.pos_n[i];
-            using Lay = tnk::TcSmem<128, 3>;
-            const int fold = cp.fold.empty() ? 0 : cp.fold[si];
-            const int ltm = std::min(s.nm, 7), ltn = std::min(s.nn, 7);
-            long long tiles_m = 1LL << (s.nm - ltm), tiles_n = 1LL << (s.nn - ltn), tiles_v = p.nver;
-            if (fold == 1) { const long long vm = 128 >> s.nm; tiles_m = (p.nver + vm - 1) / vm; tiles_v = 1; }
-            if (fold == 2) { const long long vn = 128 >> s.nn; tiles_n = (p.nver + vn - 1) / vn; tiles_v = 1; }
-            const long long tiles = (tiles_m * tiles_n << s.nbat) * tiles_v;
-            const long long blocks = std::min<long long>(tiles, num_sms());
-            tp.C = p.C;
-            tp.nver = (int)p.nver;
-            tp.fold = fold;
-            tp.vidx = static_cast<const int *>(cn.vidx_dev.p) + cp.vidx_off[si];
-            const CUtensorMap *m = &cp.maps[cp.map_off[si]];
-            tnk::tc_cgemm<128, 3><<<(unsigned)blocks, tnk::kTcThreads, Lay::kBytes, st>>>(m[0], m[1], tp);
-            CK(cudaGetLastError());
-            return TN_OK;
+    if (cn.trace) cn.tr_kernel[si] = var;
+    if (var == kVarTc128 || var == kVarTc64) {
+        if constexpr (sizeof(T) == sizeof(float2)) {
+            if (var == kVarTc128) return launch_tc<128, 3>(cn, s, si, p, st);
+            return launch_tc<64, 4>(cn, s, si, p, st);
         }
+        tn_set_error("tensor-core variant on a complex128 network");
+        return TN_EINVAL;
     }
-    if (std::min(s.nm, s.nn) == 6 && std::max(s.nm, s.nn) == 6 && s.nk <= 6 && s.nbat >= 4 &&
-        (size_t)(((1 << s.nm) + (1 << s.nn)) * ((1 << s.nk) + 1)) * sizeof(T) <= 48 * 1024) {
-        // many small products: stage 2^lg batches per block in shared memory
+    if (var == kVarSmall) {
+        // stage 2^lg batches per block in shared memory
         const int per = ((1 << s.nm) + (1 << s.nn)) * ((1 << s.nk) + 1);  // padded elements per batch
         int lg = 0;
         while (lg < s.nbat && (size_t)(per << (lg + 1)) * sizeof(T) <= 48 * 1024 && (1 << (lg + 1 + s.nm + s.nn)) <= 4096) lg++;
@@ -732,19 +799,17 @@ int launch_step(CNet &cn, const Step &s, cudaStream_t st) {
             sm.kind[i] = (int8_t)bits[i].second.first;
             sm.idx[i] = (int8_t)bits[i].second.second;
         }
-        if (cn.trace) cn.tr_kernel[si] = 1;
         const long long blocks = p.nver << (s.nbat - lg);
         const size_t smem = (size_t)(per << lg) * sizeof(T);
         tnk::cgemm_small<T><<<(unsigned)blocks, 256, smem, st>>>(p, sm);
-    } else if (std::min(s.nm, s.nn) <= 5 && s.nk <= 6) {
-        // short K and one small side: one thread per row of the larger side, the small
-        // side in registers (C = A B^T is symmetric in the operand roles)
+    } else if (var == kVarRow) {
+        // one thread per row of the larger side, the small side in registers (C = A B^T
+        // is symmetric in the operand roles)
         if (s.nn > s.nm) {
             std::swap(p.ptrA, p.ptrB);
             std::swap(p.lm, p.ln);
             for (int i = 0; i < tnk::kMaxBits; i++) std::swap(p.pos_m[i], p.pos_n[i]);
         }
-        if (cn.trace) cn.tr_kernel[si] = 0;
         long long rows = p.nver << (p.lbat + p.lm);
         unsigned blocks = (unsigned)((rows + 255) / 256);
         switch (p.ln) {
@@ -756,26 +821,81 @@ int launch_step(CNet &cn, const Step &s, cudaStream_t st) {
             default: tnk::cgemm_row<T, 32><<<blocks, 256, 0, st>>>(p); break;
         }
     } else {
-        auto launch = [&](auto kern, int TM, int TN, int nthreads) {
-            if (cn.trace) cn.tr_kernel[si] = TM * 1000 + TN;
+        auto launch = [&](auto kern, int TM, int TN) {
             int ltm = std::min(s.nm, __builtin_ctz(TM)), ltn = std::min(s.nn, __builtin_ctz(TN));
             long long blocks = p.nver << (s.nbat + (s.nm - ltm) + (s.nn - ltn));
-            kern<<<(unsigned)blocks, nthreads, 0, st>>>(p);
+            kern<<<(unsigned)blocks, 256, 0, st>>>(p);
         };
         constexpr int TK = sizeof(T) == 8 ? 16 : 8;
-        if (s.nm >= 7 && s.nn >= 6) launch(tnk::cgemm_tile<T, 128, 64, TK, 8, 4>, 128, 64, 256);
-        else if (s.nm >= 6 && s.nn >= 6) launch(tnk::cgemm_tile<T, 64, 64, TK, 4, 4>, 64, 64, 256);
-        else if (s.nm >= 7 && s.nn >= 5) launch(tnk::cgemm_tile<T, 128, 32, TK, 8, 2>, 128, 32, 256);
-        else if (s.nm >= 6 && s.nn >= 5) launch(tnk::cgemm_tile<T, 64, 32, TK, 4, 2>, 64, 32, 256);
-        else if (s.nm >= 5 && s.nn >= 5) launch(tnk::cgemm_tile<T, 32, 32, TK, 2, 2>, 32, 32, 256);
-        else if (s.nm >= 7) launch(tnk::cgemm_tile<T, 128, 16, TK, 4, 2>, 128, 16, 256);
-        else launch(tnk::cgemm_tile<T, 16, 16, TK, 1, 1>, 16, 16, 256);  // small batched products
+        switch (var) {
+            case 128064: launch(tnk::cgemm_tile<T, 128, 64, TK, 8, 4>, 128, 64); break;
+            case 64064: launch(tnk::cgemm_tile<T, 64, 64, TK, 4, 4>, 64, 64); break;
+            case 128032: launch(tnk::cgemm_tile<T, 128, 32, TK, 8, 2>, 128, 32); break;
+            case 64032: launch(tnk::cgemm_tile<T, 64, 32, TK, 4, 2>, 64, 32); break;
+            case 32032: launch(tnk::cgemm_tile<T, 32, 32, TK, 2, 2>, 32, 32); break;
+            case 128016: launch(tnk::cgemm_tile<T, 128, 16, TK, 4, 2>, 128, 16); break;
+            case 16016: launch(tnk::cgemm_tile<T, 16, 16, TK, 1, 1>, 16, 16); break;
+            default: tn_set_error("unknown kernel variant " + std::to_string(var)); return TN_EINVAL;
+        }
     }
     CK(cudaGetLastError());
     return TN_OK;
 }
 
-// One execution of a compiled network: beta leaves, steps, FP64 slice sum into out.
+template <typename T>
+int launch_step(CNet &cn, const Step &s, cudaStream_t st) {
+    const size_t si = &s - cn.steps.data();
+    const int var = si < cn.variant.size() && cn.variant[si] >= 0 ? cn.variant[si] : default_variant(cn, si);
+    return launch_variant<T>(cn, s, st, var);
+}
+
+int launch_gathers(CNet &cn, size_t si, const uint64_t *d_closed, cudaStream_t st) {
+    const size_t ng = cn.cp.gd_off[si + 1] - cn.cp.gd_off[si];
+    if (!ng) return TN_OK;
+    if (!d_closed) { tn_set_error("execute: batch patterns missing"); return TN_EINVAL; }
+    long long most = 0;
+    for (size_t g = cn.cp.gd_off[si]; g < cn.cp.gd_off[si + 1]; g++) {
+        const auto &d = cn.cp.gd[g];
+        most = std::max(most, (d.dst_plane >> d.vec_log2) * d.nplanes * d.nver);
+    }
+    dim3 grid((unsigned)std::min<long long>((most + 255) / 256, 4 * num_sms()), (unsigned)ng);
+    tnk::gather_batches<<<grid, 256, 0, st>>>(static_cast<const tnk::GatherDesc *>(cn.gdescs.p) + cn.cp.gd_off[si],
+                                              d_closed);
+    CK(cudaGetLastError());
+    return TN_OK;
+}
+
+int launch_slice_sum(CNet &cn, double2 *out, cudaStream_t st) {
+    const int root = cn.tree.root;
+    const int nout = (int)cn.net.out_layout.size();
+    const int nfree = (int)cn.tree.nodes[root].layout.size() - nout;
+    long long nelem = 1LL << nout;
+    const void *const *rt = static_cast<const void *const *>(cn.tables.p) + cn.cp.root_tab;
+    unsigned blocks = (unsigned)((nelem + 255) / 256);
+    const size_t ss = cn.steps.size();
+    if (cn.trace) {
+        if (cn.ev_pending[ss]) {
+            float ms = 0;
+            CK(cudaEventSynchronize(cn.ev[2 * ss + 1]));
+            CK(cudaEventElapsedTime(&ms, cn.ev[2 * ss], cn.ev[2 * ss + 1]));
+            cn.tr_ms[ss] += ms;
+            cn.tr_launches[ss]++;
+            cn.ev_pending[ss] = 0;
+        }
+        CK(cudaEventRecord(cn.ev[2 * ss], st));
+    }
+    if (cn.elem == 8) tnk::slice_sum<float2><<<blocks, 256, 0, st>>>(rt, cn.cp.root_nver, nfree, nout, out);
+    else tnk::slice_sum<double2><<<blocks, 256, 0, st>>>(rt, cn.cp.root_nver, nfree, nout, out);
+    CK(cudaGetLastError());
+    if (cn.trace) {
+        CK(cudaEventRecord(cn.ev[2 * ss + 1], st));
+        cn.ev_pending[ss] = 1;
+        cn.tr_kernel[ss] = 2;
+    }
+    return TN_OK;
+}
+
+// One execution of a compiled network: batch gathers, steps, FP64 slice sum into out.
 int execute(CNet &cn, const uint64_t *d_closed, bool skip_beta_free, double2 *out, cudaStream_t st) {
     for (const Step &s : cn.steps) {
         if (skip_beta_free && !cn.tree.nodes[s.c].beta) continue;
@@ -791,18 +911,7 @@ int execute(CNet &cn, const uint64_t *d_closed, bool skip_beta_free, double2 *ou
             }
             CK(cudaEventRecord(cn.ev[2 * si], st));
         }
-        if (const size_t ng = cn.cp.gd_off[si + 1] - cn.cp.gd_off[si]) {
-            if (!d_closed) { tn_set_error("execute: batch patterns missing"); return TN_EINVAL; }
-            long long most = 0;
-            for (size_t g = cn.cp.gd_off[si]; g < cn.cp.gd_off[si + 1]; g++) {
-                const auto &d = cn.cp.gd[g];
-                most = std::max(most, (d.dst_plane >> d.vec_log2) * d.nplanes * d.nver);
-            }
-            dim3 grid((unsigned)std::min<long long>((most + 255) / 256, 4 * num_sms()), (unsigned)ng);
-            tnk::gather_batches<<<grid, 256, 0, st>>>(static_cast<const tnk::GatherDesc *>(cn.gdescs.p) + cn.cp.gd_off[si],
-                                                      d_closed);
-            CK(cudaGetLastError());
-        }
+        RC(launch_gathers(cn, si, d_closed, st));
         if (cn.elem == 8) RC(launch_step<float2>(cn, s, st));
         else RC(launch_step<double2>(cn, s, st));
         if (cn.calibrating) {
@@ -819,16 +928,88 @@ int execute(CNet &cn, const uint64_t *d_closed, bool skip_beta_free, double2 *ou
             cn.ev_pending[si] = 1;
         }
     }
-    const int root = cn.tree.root;
-    const int nout = (int)cn.net.out_layout.size();
-    const int nfree = (int)cn.tree.nodes[root].layout.size() - nout;
-    long long nelem = 1LL << nout;
-    const void *const *rt = static_cast<const void *const *>(cn.tables.p) + cn.cp.root_tab;
-    unsigned blocks = (unsigned)((nelem + 255) / 256);
-    if (cn.elem == 8) tnk::slice_sum<float2><<<blocks, 256, 0, st>>>(rt, cn.cp.root_nver, nfree, nout, out);
-    else tnk::slice_sum<double2><<<blocks, 256, 0, st>>>(rt, cn.cp.root_nver, nfree, nout, out);
-    CK(cudaGetLastError());
-    return TN_OK;
+    return launch_slice_sum(cn, out, st);
+}
+
+// Kernel autotuning: the variant chosen for a step shape (precision and formats, fold,
+// bit counts, versions) is cached for the process and shared by every plan.
+std::mutex g_tune_mu;
+std::map<std::vector<long long>, int> g_tune;
+
+std::vector<long long> tune_key(const CNet &cn, size_t si) {
+    const Step &s = cn.steps[si];
+    return {cn.elem, cn.use_tc.empty() ? 0 : cn.use_tc[si], cn.cp.fold.empty() ? 0 : cn.cp.fold[si], cn.fmt[s.a],
+            cn.fmt[s.c], s.nbat, s.nm, s.nn, s.nk, cn.cp.nver[s.c]};
+}
+
+// Fill in every step's variant that is known (single candidate, autotuning off, or a
+// cached choice); true if some step still has to be timed.
+bool resolve_variants(CNet &cn) {
+    cn.variant.resize(cn.steps.size(), -1);
+    bool need = false;
+    std::lock_guard<std::mutex> lock(g_tune_mu);
+    for (size_t si = 0; si < cn.steps.size(); si++) {
+        if (cn.variant[si] >= 0) continue;
+        const std::vector<int> c = step_variants(cn, si);
+        if (cn.autotune >= 2 && !c.empty()) {
+            cn.variant[si] = c[(si + (size_t)(cn.autotune - 2)) % c.size()];
+            continue;
+        }
+        if (cn.autotune <= 0 || c.size() <= 1) {
+            cn.variant[si] = c.size() == 1 ? c[0] : default_variant(cn, si);
+            continue;
+        }
+        auto it = g_tune.find(tune_key(cn, si));
+        if (it != g_tune.end()) cn.variant[si] = it->second;
+        else need = true;
+    }
+    return need;
+}
+
+// One full execution that times each applicable variant of every step still unchosen
+// (one warm-up launch, then two timed launches, CUDA events on the plan's stream),
+// keeps the fastest and then runs it, so `out` is written as by execute().
+template <typename T>
+int tune_execute(CNet &cn, const uint64_t *d_closed, double2 *out, cudaStream_t st) {
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    CK(cudaEventCreate(&e0));
+    if (cudaEventCreate(&e1) != cudaSuccess) {
+        cudaEventDestroy(e0);
+        tn_set_error("cudaEventCreate failed");
+        return TN_EDEVICE;
+    }
+    int rc = TN_OK;
+    for (size_t si = 0; si < cn.steps.size() && rc == TN_OK; si++) {
+        const Step &s = cn.steps[si];
+        rc = launch_gathers(cn, si, d_closed, st);
+        if (rc == TN_OK && cn.variant[si] < 0) {
+            int best = -1;
+            float best_ms = 0;
+            for (int v : step_variants(cn, si)) {
+                rc = launch_variant<T>(cn, s, st, v);
+                if (rc == TN_OK && cudaEventRecord(e0, st) != cudaSuccess) rc = TN_EDEVICE;
+                for (int r = 0; r < 2 && rc == TN_OK; r++) rc = launch_variant<T>(cn, s, st, v);
+                float ms = 0;
+                if (rc == TN_OK && (cudaEventRecord(e1, st) != cudaSuccess || cudaEventSynchronize(e1) != cudaSuccess ||
+                                    cudaEventElapsedTime(&ms, e0, e1) != cudaSuccess)) {
+                    tn_set_error("autotune: event timing failed");
+                    rc = TN_EDEVICE;
+                }
+                if (rc != TN_OK) break;
+                if (best < 0 || ms < best_ms) { best = v; best_ms = ms; }
+            }
+            if (rc == TN_OK) {
+                cn.variant[si] = best;
+                std::lock_guard<std::mutex> lock(g_tune_mu);
+                g_tune[tune_key(cn, si)] = best;
+            }
+        }
+        if (rc == TN_OK) rc = launch_step<T>(cn, s, st);
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    RC(rc);
+    return launch_slice_sum(cn, out, st);
 }
 
 // fp16 split: the first execution runs with bf16 split operands and records every
@@ -879,6 +1060,10 @@ int execute_graphed(DevMem &mem, CNet &cn, const uint64_t *d_closed, bool skip_b
     if (cn.prec == TN_PREC_FP16X2 && !cn.calibrated) {
         RC(calibrate_fp16(mem, cn, d_closed, out, st, budget));
         skip_beta_free = false;  // the stem was recomputed in the calibration formats
+    }
+    if (resolve_variants(cn)) {
+        drop_graphs(cn);
+        return cn.elem == 8 ? tune_execute<float2>(cn, d_closed, out, st) : tune_execute<double2>(cn, d_closed, out, st);
     }
     static const bool disabled = getenv("TN_NO_GRAPH") != nullptr;
     if (cn.trace || disabled) return execute(cn, d_closed, skip_beta_free, out, st);
@@ -1003,6 +1188,7 @@ void tn_plan_opts_default(tn_plan_opts *o) {
     o->n_auto_sliced = 0;
     o->hbm_budget_bytes = 64.0 * (1ull << 30);
     o->max_norm_flops = 2e15;
+    o->autotune = 1;
 }
 
 int tn_circuit_load(const void *buf, size_t len, tn_circuit_h *out) {
@@ -1063,6 +1249,7 @@ int tn_plan(tn_circuit_h c, const int32_t *order, int32_t n_order, const tn_edge
     p->amp.E = E0;
     p->amp.compiled = true;
     p->amp.prec = o.precision;
+    p->amp.autotune = o.autotune;
     assign_formats(p->amp);
     rc = setup_leaves(p->mem, p->amp);
     if (rc) return fail(rc);
@@ -1387,14 +1574,16 @@ int tn_trace_enable(tn_plan_h p, int32_t on) {
     if (!p) { tn_set_error("null plan"); return TN_EINVAL; }
     CNet &cn = p->amp;
     const size_t ns = cn.steps.size();
-    if (on && cn.ev.empty()) {
-        cn.ev.resize(2 * ns);
+    // one entry per step plus one for the FP64 slice sum
+    if (on && cn.ev.size() != 2 * (ns + 1)) {
+        for (auto &x : cn.ev) cudaEventDestroy(x);
+        cn.ev.assign(2 * (ns + 1), nullptr);
         for (auto &x : cn.ev) CK(cudaEventCreate(&x));
     }
-    cn.ev_pending.assign(ns, 0);
-    cn.tr_launches.assign(ns, 0);
-    cn.tr_ms.assign(ns, 0.0);
-    cn.tr_kernel.assign(ns, -1);
+    cn.ev_pending.assign(ns + 1, 0);
+    cn.tr_launches.assign(ns + 1, 0);
+    cn.tr_ms.assign(ns + 1, 0.0);
+    cn.tr_kernel.assign(ns + 1, -1);
     cn.trace = on != 0;
     return TN_OK;
 }
@@ -1406,7 +1595,7 @@ int tn_trace_read(tn_plan_h p, tn_step_trace *out, int32_t cap, int32_t *n_out) 
     *n_out = ns;
     if (!cn.trace) return TN_OK;
     CK(cudaStreamSynchronize(p->mem.stream));
-    for (int si = 0; si < ns; si++)
+    for (int si = 0; si <= ns; si++)
         if (cn.ev_pending[si]) {
             float ms = 0;
             CK(cudaEventElapsedTime(&ms, cn.ev[2 * si], cn.ev[2 * si + 1]));
@@ -1415,6 +1604,23 @@ int tn_trace_read(tn_plan_h p, tn_step_trace *out, int32_t cap, int32_t *n_out) 
             cn.ev_pending[si] = 0;
         }
     const auto &nodes = cn.tree.nodes;
+    *n_out = ns + 1;
+    if (ns < cap && out) {
+        // the slice sum: 2 FP64 additions and one complex64 read per summed element
+        tn_step_trace &t = out[ns];
+        std::memset(&t, 0, sizeof(t));
+        t.step = ns;
+        t.launches = cn.tr_launches[ns];
+        t.ms = cn.tr_ms[ns];
+        const int root = cn.tree.root;
+        const double nout = std::ldexp(1.0, (int)cn.net.out_layout.size());
+        const double summed = (cn.cp.valid ? (double)cn.cp.root_nver : 1.0) *
+                              std::ldexp(1.0, (int)nodes[root].layout.size() - (int)cn.net.out_layout.size());
+        t.nver = cn.cp.valid ? cn.cp.root_nver : 1;
+        t.flops_per_launch = 2.0 * nout * summed;
+        t.bytes_per_launch = 8.0 * nout * summed + 16.0 * nout;
+        t.kernel = 2;
+    }
     for (int si = 0; si < ns && si < cap && out; si++) {
         const Step &s = cn.steps[si];
         tn_step_trace &t = out[si];
@@ -1436,6 +1642,7 @@ int tn_trace_read(tn_plan_h p, tn_step_trace *out, int32_t cap, int32_t *n_out) 
         t.nn = s.nn;
         t.nk = s.nk;
         t.kernel = cn.tr_kernel[si];
+        t.gathers = cn.cp.valid && cn.cp.gd_off[si + 1] > cn.cp.gd_off[si] ? 1 : 0;
     }
     return TN_OK;
 }

@@ -79,6 +79,7 @@ class PlanOpts(ctypes.Structure):
         ("n_auto_sliced", ctypes.c_int32),
         ("hbm_budget_bytes", ctypes.c_double),
         ("max_norm_flops", ctypes.c_double),
+        ("autotune", ctypes.c_int32),
         ("stream", ctypes.c_void_p),
         ("alloc", ALLOC_FN),
         ("free", FREE_FN),
@@ -100,7 +101,7 @@ class StepTrace(ctypes.Structure):
         ("step", ctypes.c_int32), ("launches", ctypes.c_int32), ("ms", ctypes.c_double),
         ("flops_per_launch", ctypes.c_double), ("bytes_per_launch", ctypes.c_double),
         ("nbat", ctypes.c_int32), ("nm", ctypes.c_int32), ("nn", ctypes.c_int32), ("nk", ctypes.c_int32),
-        ("nver", ctypes.c_int64), ("kernel", ctypes.c_int32),
+        ("nver", ctypes.c_int64), ("kernel", ctypes.c_int32), ("gathers", ctypes.c_int32),
     ]
 
 
@@ -231,7 +232,8 @@ def circuit_load(buf: bytes) -> Circuit:
 class Plan:
     def __init__(self, circuit: Circuit, open_qubits, sliced=None, order=None, precision=PREC_C64,
                  log2_batches=8, order_seed=0, order_trials=64, n_auto_sliced=0,
-                 hbm_budget_bytes=0.0, stream=None, use_torch_allocator=True, max_norm_flops=0.0):
+                 hbm_budget_bytes=0.0, stream=None, use_torch_allocator=True, max_norm_flops=0.0,
+                 autotune=None):
         L = lib()
         o = PlanOpts()
         L.tn_plan_opts_default(ctypes.byref(o))
@@ -244,6 +246,8 @@ class Plan:
             o.hbm_budget_bytes = hbm_budget_bytes
         if max_norm_flops:
             o.max_norm_flops = max_norm_flops
+        if autotune is not None:
+            o.autotune = int(autotune)
         o.stream = _stream_ptr(stream)
         self._alloc = None
         if use_torch_allocator:

@@ -136,6 +136,47 @@ def test_28q_bench_configuration_16384_batches(grid28, prec):
         assert err["rel_l2"] <= 1e-3, err
 
 
+@pytest.mark.parametrize("prec", ["c64", "bf16x2"])
+def test_every_kernel_variant(prec):
+    """autotune = k >= 2 runs variant (step + k - 2) mod count at every step, so nine plans
+    cover every FFMA tile, the row and staged kernels and both tensor-core tile widths
+    at the shapes of a 20-qubit plan with 1024 batches per group."""
+    P = pkg()
+    circ = cg.sycamore_grid(4, 5, 12, seed=1)
+    openq = cg.default_open_qubits(4, 5, 6)
+    C = P.circuit_load(circ.serialize())
+    cb = cg.random_closed_bits(1024, 14, seed=9)
+    ref = oracle.batch_amplitudes(oracle.simulate(circ), 20, openq, cb)
+    precision = {"c64": P.tn.PREC_C64, "bf16x2": P.tn.PREC_BF16X2}[prec]
+    for k in range(2, 11):
+        plan = P.plan(C, openq, n_auto_sliced=6, log2_batches=10, order_trials=16, precision=precision, autotune=k)
+        amps = plan.contract(np.arange(64, dtype=np.uint64), cb)
+        if prec == "c64":
+            close_c64(amps, ref)
+        else:
+            err = split_errors(amps, ref)
+            assert err["rel_l2"] <= 1e-3, (k, err)
+        del plan
+
+
+@pytest.mark.parametrize("prec", ["c64", "bf16x2"])
+def test_autotuned_equals_fixed_rules(prec):
+    """Every variant accumulates each output over k in the same order, so the timed
+    choice gives exactly the amplitudes of the fixed shape rules."""
+    P = pkg()
+    circ = cg.sycamore_grid(4, 5, 12, seed=1)
+    openq = cg.default_open_qubits(4, 5, 6)
+    C = P.circuit_load(circ.serialize())
+    cb = cg.random_closed_bits(1024, 14, seed=9)
+    precision = {"c64": P.tn.PREC_C64, "bf16x2": P.tn.PREC_BF16X2}[prec]
+    out = []
+    for mode in (0, 1):
+        plan = P.plan(C, openq, n_auto_sliced=6, log2_batches=10, order_trials=16, precision=precision, autotune=mode)
+        out.append(plan.contract(np.arange(64, dtype=np.uint64), cb))
+        del plan
+    assert np.array_equal(out[0], out[1])
+
+
 def split_errors(got, ref):
     d = np.abs(got - ref)
     rms = float(np.sqrt(np.mean(np.abs(ref) ** 2)))
