@@ -49,6 +49,7 @@ def parse():
     ap.add_argument("--precision", default="bf16x2", choices=["c64", "bf16x2"])
     ap.add_argument("--workload", default="grid4x7_m14", choices=sorted(WORKLOADS))
     ap.add_argument("--log2-batches", type=int, default=None, help="batches per step = 2^this (default: the workload's)")
+    ap.add_argument("--autotune", type=int, default=1, help="kernel autotuning (1) or the fixed shape rules (0)")
     ap.add_argument("--serve", action="store_true", help="serving run (Poisson request stream) instead of the step bench")
     ap.add_argument("--serve-window", type=float, default=60.0, help="seconds of arrivals")
     ap.add_argument("--serve-rate", type=float, default=4.0, help="requests per second")
@@ -216,7 +217,7 @@ def run_ours(args):
     C = P.circuit_load(circ.serialize())
     prec = {"c64": P.tn.PREC_C64, "bf16x2": P.tn.PREC_BF16X2}[args.precision]
     plan = P.plan(C, openq, n_auto_sliced=w["n_sliced"], log2_batches=log2_batches(args), order_trials=args.trials,
-                  order_seed=0, hbm_budget_bytes=200e9, precision=prec)
+                  order_seed=0, hbm_budget_bytes=200e9, precision=prec, autotune=args.autotune)
     info = plan.info()
     slices, F = plan.select(args.fidelity)
     T = 1 << log2_batches(args)

@@ -809,6 +809,7 @@ int launch_variant(CNet &cn, const Step &s, cudaStream_t st, int var) {
             std::swap(p.ptrA, p.ptrB);
             std::swap(p.lm, p.ln);
             for (int i = 0; i < tnk::kMaxBits; i++) std::swap(p.pos_m[i], p.pos_n[i]);
+            p.swapped = 1;
         }
         long long rows = p.nver << (p.lbat + p.lm);
         unsigned blocks = (unsigned)((rows + 255) / 256);

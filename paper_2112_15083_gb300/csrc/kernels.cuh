@@ -19,6 +19,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include "widen.h"
+
 namespace tnk {
 
 constexpr int kMaxBits = 40;
@@ -37,6 +39,8 @@ struct GemmParams {
     int lm, ln, lk, lbat;     // log2 of M, N, K, BAT
     int out_fmt;              // OutFmt of C
     float out_scale;          // multiplier applied before storing
+    int swapped;              // operands exchanged (A holds the step's B): keep the step's
+                              // operand order inside each complex multiply-add
     int8_t pos_bat[kMaxBits], pos_m[kMaxBits], pos_n[kMaxBits];
 };
 
@@ -120,10 +124,18 @@ __global__ void __launch_bounds__(256) cgemm_row(GemmParams p) {
     T acc[N];
 #pragma unroll
     for (int n = 0; n < N; n++) acc[n] = czero<T>();
-    for (int k = 0; k < K; k++) {
-        T a = A[k];
+    if (p.swapped) {
+        for (int k = 0; k < K; k++) {
+            T a = A[k];
 #pragma unroll
-        for (int n = 0; n < N; n++) acc[n] = cfma(a, __ldg(&B[(n << p.lk) + k]), acc[n]);
+            for (int n = 0; n < N; n++) acc[n] = cfma(__ldg(&B[(n << p.lk) + k]), a, acc[n]);
+        }
+    } else {
+        for (int k = 0; k < K; k++) {
+            T a = A[k];
+#pragma unroll
+            for (int n = 0; n < N; n++) acc[n] = cfma(a, __ldg(&B[(n << p.lk) + k]), acc[n]);
+        }
     }
     const long long cb = scatter_bits(bat, p.pos_bat, p.lbat) + scatter_bits(m, p.pos_m, p.lm);
 #pragma unroll
@@ -362,17 +374,36 @@ __global__ void absmax_kernel(const void *data, long long n, int fmt, int *absma
 
 // out[e] = sum over explicit root versions v (in order) and over the 2^nfree patterns f
 // of the sliced legs carried as layout bits (ascending) of root_v[(f << nout) | e], FP64.
+// complex64 inputs are widened with integer operations (exact), which leaves the FP64
+// pipe to the additions.
+__device__ __forceinline__ double slice_widen(float x) { return tn_widen(x); }
+__device__ __forceinline__ double slice_widen(double x) { return x; }
+
 template <typename T>
 __global__ void slice_sum(const void *const *ptr, long long nver, int nfree, int nout, double2 *out) {
     const long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (e >= (1LL << nout)) return;
     double re = 0.0, im = 0.0;
+    const long long nf = 1LL << nfree;
     for (long long v = 0; v < nver; v++) {
-        const T *r = static_cast<const T *>(ptr[v]);
-        for (long long f = 0; f < (1LL << nfree); f++) {
-            const T x = r[(f << nout) | e];
-            re = __dadd_rn(re, (double)x.x);
-            im = __dadd_rn(im, (double)x.y);
+        const T *r = static_cast<const T *>(ptr[v]) + e;
+        long long f = 0;
+        // loads issued four at a time; the additions stay in slice order
+        for (; f + 4 <= nf; f += 4) {
+            const T x0 = r[(f + 0) << nout], x1 = r[(f + 1) << nout], x2 = r[(f + 2) << nout], x3 = r[(f + 3) << nout];
+            re = __dadd_rn(re, slice_widen(x0.x));
+            im = __dadd_rn(im, slice_widen(x0.y));
+            re = __dadd_rn(re, slice_widen(x1.x));
+            im = __dadd_rn(im, slice_widen(x1.y));
+            re = __dadd_rn(re, slice_widen(x2.x));
+            im = __dadd_rn(im, slice_widen(x2.y));
+            re = __dadd_rn(re, slice_widen(x3.x));
+            im = __dadd_rn(im, slice_widen(x3.y));
+        }
+        for (; f < nf; f++) {
+            const T x = r[f << nout];
+            re = __dadd_rn(re, slice_widen(x.x));
+            im = __dadd_rn(im, slice_widen(x.y));
         }
     }
     out[e] = make_double2(re, im);
