@@ -425,7 +425,10 @@ def run_serve(args):
         lat = [i["t_done"] - i["t_submit"] for i in done if i["f"] == f]
         classes["f=%g" % f] = {"done": len(lat), "p50_s": pct(lat, 50), "p99_s": pct(lat, 99)}
     lat_all = [i["t_done"] - i["t_submit"] for i in done]
+    waits = [i["t_admit"] - i["t_submit"] for i in done]
+    runs = [i["t_done"] - i["t_admit"] for i in done]
     samples = sum(i["N"] for i in done)
+    slowest = sorted(done, key=lambda i: -(i["t_done"] - i["t_admit"]))[:5]
     line = {"metric": "serving: p50/p99 latency and samples/s", "value": samples / makespan, "unit": "samples/s",
             "n_gpus": 1, "higher_is_better": True, "data": "synthetic",
             "config": {"workload": "Poisson %.1f req/s for %.0f s; grids %s; cycles 8-16; N in 1k/10k/100k; "
@@ -436,6 +439,11 @@ def run_serve(args):
             "failed": sum(1 for i in infos if i["status"] == "failed"),
             "unfinished": sum(1 for i in infos if i["status"] not in ("done", "failed", "rejected")),
             "p50_s": pct(lat_all, 50), "p99_s": pct(lat_all, 99), "classes": classes,
+            "wait_p50_s": pct(waits, 50), "run_p50_s": pct(runs, 50), "run_p99_s": pct(runs, 99),
+            "slowest_runs": [{"qubits": i["qubits"], "cycles": i["cycles"], "N": i["N"], "f": i["f"],
+                              "precision": "bf16x2" if i["prec"] == P.tn.PREC_BF16X2 else "c64",
+                              "run_s": round(i["t_done"] - i["t_admit"], 2), "gflop": round(i["flops"] / 1e9, 1)}
+                             for i in slowest],
             "max_waiting": max_queue, "makespan_s": makespan}
     print(json.dumps(line), flush=True)
 

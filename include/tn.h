@@ -314,8 +314,13 @@ typedef struct {
     double hbm_budget_bytes;    /* admission budget (default 150e9) */
     int32_t max_active;         /* requests running at once (default 8) */
     int32_t planner_threads;    /* default 2 */
-    int32_t log2_batches;       /* batch group size of every request (default 8) */
-    int32_t order_trials;       /* greedy order trials per plan (default 64) */
+    int32_t log2_batches;       /* smallest batch group of a request (default 8) */
+    int32_t max_log2_batches;   /* largest: a request of N samples gets the smallest group
+                                   of at least 1.1 alpha N batches within these bounds, since
+                                   the batches of a group share their batch-independent
+                                   intermediates (default 14) */
+    int32_t order_trials;       /* order-search trials per plan (default 64); served plans
+                                   use the fixed kernel shape rules (no autotuning) */
     double max_request_seconds; /* estimated-time limit per request (default 600); it also caps
                                    the norm network of the slice selection */
     double assumed_flops;       /* rate of split-precision plans for that estimate (3e14) */

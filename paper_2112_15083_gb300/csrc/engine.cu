@@ -699,9 +699,9 @@ int default_variant(const CNet &cn, size_t si) {
     if (!cn.use_tc.empty() && cn.use_tc[si]) return kVarTc128;
     if (std::min(s.nm, s.nn) == 6 && std::max(s.nm, s.nn) == 6 && small_fits(s, (size_t)cn.elem)) return kVarSmall;
     if (std::min(s.nm, s.nn) <= 5 && s.nk <= 6) return kVarRow;
-    if (s.nm >= 7 && s.nn >= 6) return 128064;
-    if (s.nm >= 6 && s.nn >= 6) return 64064;
+    // large products: 128 x 32 tiles (the autotuner's choice on GB300 for complex64)
     if (s.nm >= 7 && s.nn >= 5) return 128032;
+    if (s.nm >= 6 && s.nn >= 6) return 64064;
     if (s.nm >= 6 && s.nn >= 5) return 64032;
     if (s.nm >= 5 && s.nn >= 5) return 32032;
     if (s.nm >= 7) return 128016;
@@ -743,6 +743,13 @@ int launch_tc(CNet &cn, const Step &s, size_t si, const tnk::GemmParams &p, cuda
     tp.nver = (int)p.nver;
     tp.fold = fold;
     tp.vidx = static_cast<const int *>(cn.vidx_dev.p) + cp.vidx_off[si];
+    // raster groups: the A panels of one group (128 rows x K, 8 bytes per element over
+    // the four planes) stay within about 48 MB of L2 while the group sweeps the n tiles
+    {
+        const double panel = 128.0 * std::ldexp(1.0, s.nk) * 8.0;
+        long long g = (long long)std::floor(48.0 * (1 << 20) / panel);
+        tp.group_m = (int)std::max<long long>(1, std::min<long long>({g, 64, tiles_m}));
+    }
     const CUtensorMap *m = &cp.maps[cp.map_off[si]];
     tnk::tc_cgemm<BN, ST><<<(unsigned)blocks, tnk::kTcThreads, Lay::kBytes, st>>>(m[0], m[BN == 128 ? 1 : 2], tp);
     CK(cudaGetLastError());
@@ -956,7 +963,10 @@ bool resolve_variants(CNet &cn) {
             cn.variant[si] = c[(si + (size_t)(cn.autotune - 2)) % c.size()];
             continue;
         }
-        if (cn.autotune <= 0 || c.size() <= 1) {
+        // steps under ~50 us (estimated) keep the shape rules: timing them costs more
+        // than any choice can gain
+        const double work = cn.steps[si].flops_per_version * (double)cn.cp.nver[cn.steps[si].c];
+        if (cn.autotune <= 0 || c.size() <= 1 || work < 1e9) {
             cn.variant[si] = c.size() == 1 ? c[0] : default_variant(cn, si);
             continue;
         }

@@ -133,7 +133,12 @@ void planner_loop(tn_server_s *s) {
             tn_plan_opts po;
             tn_plan_opts_default(&po);
             po.precision = r->precision;
-            po.log2_batches = s->o.log2_batches;
+            // the smallest group holding the request's expected batches, within the bounds
+            int lb = std::max(0, s->o.log2_batches);
+            const double want = 1.1 * r->alpha * (double)r->N;
+            while (lb < s->o.max_log2_batches && std::ldexp(1.0, lb) < want) lb++;
+            po.log2_batches = lb;
+            po.autotune = 0;
             po.order_trials = s->o.order_trials;
             po.n_auto_sliced = r->n_sliced;
             po.hbm_budget_bytes = s->o.hbm_budget_bytes;
@@ -308,6 +313,7 @@ void tn_server_opts_default(tn_server_opts *o) {
     o->max_active = 8;
     o->planner_threads = 2;
     o->log2_batches = 8;
+    o->max_log2_batches = 14;
     o->order_trials = 64;
     o->max_request_seconds = 600;
     o->assumed_flops = 3e14;

@@ -40,8 +40,31 @@ struct TcParams {
     int in_fp16;             // operands are fp16 (else bf16)
     float out_scale;         // multiply results by this before storing
     int *err;                // set to 1 if a bounded wait gives up
+    int group_m;             // m tiles per raster group (>= 1): see tc_tile
     int8_t pos_bat[kMaxBits], pos_m[kMaxBits], pos_n[kMaxBits];
 };
+
+// Tile t of a launch: (batch, version) outermost; inside, groups of group_m m tiles are
+// walked n tile by n tile with the m tiles of the group fastest, so the CTAs running
+// together share a few operand panels of both A and B in L2 (with group_m = 1 this is
+// the plain n-fastest order).
+struct TcTile {
+    int tn_i, tm_i, bat;
+    long long v;
+};
+__device__ __forceinline__ TcTile tc_tile(long long t, long long tiles_m, long long tiles_n, int lbat, int group_m) {
+    const long long per_bat = tiles_m * tiles_n;
+    const long long bv = t / per_bat, tl = t - bv * per_bat;
+    TcTile r;
+    r.bat = (int)(bv & ((1LL << lbat) - 1));
+    r.v = bv >> lbat;
+    const long long gsz = (long long)group_m * tiles_n;
+    const long long g = tl / gsz, rr = tl - g * gsz;
+    const long long gm = min((long long)group_m, tiles_m - g * group_m);
+    r.tn_i = (int)(rr / gm);
+    r.tm_i = (int)(g * group_m + rr % gm);
+    return r;
+}
 
 __device__ __forceinline__ uint32_t smem_u32(const void *p) {
     return static_cast<uint32_t>(__cvta_generic_to_shared(p));
@@ -226,10 +249,8 @@ __global__ void __launch_bounds__(kTcThreads, 1)
             long long slot = 0;
             bool ok = true;
             for (long long t = blockIdx.x; t < ntiles && ok; t += gridDim.x) {
-                const int tn_i = (int)(t % tiles_n);
-                const int tm_i = (int)((t / tiles_n) % tiles_m);
-                const int bat = (int)((t / per_bat) & ((1LL << p.lbat) - 1));
-                const int v = (int)(t / (per_bat << p.lbat));
+                const TcTile tt = tc_tile(t, tiles_m, tiles_n, p.lbat, p.group_m);
+                const int tn_i = tt.tn_i, tm_i = tt.tm_i, bat = tt.bat, v = (int)tt.v;
                 const int ia = p.fold == 1 ? p.vidx[0] + tm_i * vm : p.vidx[p.fold == 2 ? 0 : v];
                 const int ib = p.fold == 2 ? p.vidx[p.nver] + tn_i * vn : p.vidx[p.nver + (p.fold == 1 ? 0 : v)];
                 const int rowA = p.fold == 1 ? 0 : tm_i * kTcBM, rowB = p.fold == 2 ? 0 : tn_i * BN;
@@ -316,10 +337,9 @@ __global__ void __launch_bounds__(kTcThreads, 1)
             const int b = it & 1;
             if (!mbar_wait(smem_u32(&acc_full[b]), (uint32_t)((it >> 1) & 1), abort_flag, kLimit)) break;
             asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-            const int tn_i = (int)(t % tiles_n);
-            const int tm_i = (int)((t / tiles_n) % tiles_m);
-            const int bat = (int)((t / per_bat) & ((1LL << p.lbat) - 1));
-            long long vrow = t / (per_bat << p.lbat);  // this row's version
+            const TcTile tt = tc_tile(t, tiles_m, tiles_n, p.lbat, p.group_m);
+            const int tn_i = tt.tn_i, tm_i = tt.tm_i, bat = tt.bat;
+            long long vrow = tt.v;  // this row's version
             long long m;
             if (p.fold == 1) {
                 vrow = (long long)tm_i * vm + (row >> p.lm);

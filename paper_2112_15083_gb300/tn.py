@@ -34,7 +34,8 @@ REQ_STATUS = {0: "queued", 1: "planning", 2: "planned", 3: "active", 4: "done", 
 class ServerOpts(ctypes.Structure):
     _fields_ = [
         ("hbm_budget_bytes", ctypes.c_double), ("max_active", ctypes.c_int32), ("planner_threads", ctypes.c_int32),
-        ("log2_batches", ctypes.c_int32), ("order_trials", ctypes.c_int32), ("max_request_seconds", ctypes.c_double),
+        ("log2_batches", ctypes.c_int32), ("max_log2_batches", ctypes.c_int32), ("order_trials", ctypes.c_int32),
+        ("max_request_seconds", ctypes.c_double),
         ("assumed_flops", ctypes.c_double), ("assumed_flops_c64", ctypes.c_double), ("device", ctypes.c_int32),
     ]
 
@@ -391,12 +392,13 @@ class Plan:
 
 
 def plan_host(circuit: Circuit, open_qubits, sliced=None, order=None, log2_batches=8, order_seed=0,
-              order_trials=64, n_auto_sliced=0):
+              order_trials=64, n_auto_sliced=0, precision=PREC_C64):
     """Host-only planning (no GPU): (info dict, steps array (n_steps, 7), sliced edges).
     Step row: batch, m, n, k bits, log2 versions of C, A, B."""
     L = lib()
     o = PlanOpts()
     L.tn_plan_opts_default(ctypes.byref(o))
+    o.precision = precision
     o.log2_batches = log2_batches
     o.order_seed = order_seed
     o.order_trials = order_trials
@@ -488,7 +490,8 @@ class Server:
     """Continuous-batching sampling server (tn_server_*)."""
 
     def __init__(self, hbm_budget_bytes=150e9, max_active=8, planner_threads=2, log2_batches=8, order_trials=64,
-                 max_request_seconds=600.0, assumed_flops=3e14, assumed_flops_c64=3e13, device=0):
+                 max_request_seconds=600.0, assumed_flops=3e14, assumed_flops_c64=3e13, device=0,
+                 max_log2_batches=14):
         L = lib()
         o = ServerOpts()
         L.tn_server_opts_default(ctypes.byref(o))
@@ -496,6 +499,7 @@ class Server:
         o.max_active = max_active
         o.planner_threads = planner_threads
         o.log2_batches = log2_batches
+        o.max_log2_batches = max_log2_batches
         o.order_trials = order_trials
         o.max_request_seconds = max_request_seconds
         o.assumed_flops = assumed_flops

@@ -74,8 +74,14 @@ def test_same_alone_in_the_mix_and_via_tn_sample():
     assert np.array_equal(got, ref)
     assert st["done"] == 5
 
+    # the server sizes the group to the request (the smallest 2^lb >= 1.1 alpha N within
+    # [2^8, 2^14]) and uses the fixed kernel shape rules
+    lb = 8
+    while lb < 14 and (1 << lb) < 1.1 * 2.0 * N:
+        lb += 1
     C = P.circuit_load(buf)
-    plan = P.plan(C, openq, n_auto_sliced=4, log2_batches=8, order_trials=64, precision=P.tn.PREC_BF16X2)
+    plan = P.plan(C, openq, n_auto_sliced=4, log2_batches=lb, order_trials=64, precision=P.tn.PREC_BF16X2,
+                  autotune=0)
     via_plan, _ = plan.sample(1.0, N, seed=42)
     assert np.array_equal(via_plan, ref)
 
@@ -85,8 +91,8 @@ def test_admission_respects_budget():
     need_gpu()
     s = P.Server(max_active=8)
     buf, openq = request(4, 5, 10, 1)
-    rid0 = s.submit(buf, openq, N=500, n_sliced=3)
-    _, info0 = s.wait(rid0, 500, timeout=300)
+    rid0 = s.submit(buf, openq, N=2000, n_sliced=3)
+    _, info0 = s.wait(rid0, 2000, timeout=300)
     s.close()
     budget = 1.5 * info0["est_bytes"]  # room for one request at a time
     s = P.Server(hbm_budget_bytes=budget, max_active=8)
