@@ -33,6 +33,10 @@ WORKLOADS = {
 }
 WORKLOAD = WORKLOADS["grid4x7_m14"]
 METRIC = "samples/s at fixed fidelity"
+# DRAM traffic (dram__bytes_read.sum + dram__bytes_write.sum, bytes per launch) of the
+# dominant kernel from one ncu capture of this workload (profiles/tc_cgemm_dram_grid4x7_m14_b16384.md),
+# valid for the kernel source it was taken with (sha256 prefix of csrc/tc.cuh)
+MEASURED_TRAFFIC = {("tc_cgemm<128,3>", (1, 15, 14, 12)): (83.75e9, "cbda2ea2f13a3e53")}
 FFMA_PEAK_NOTE = "152 SMs x 128 FP32 lanes x 2 FLOP x 2070 MHz"
 
 
@@ -303,6 +307,13 @@ def run_ours(args):
                     "kernel": "cgemm_tile %d (bat,m,n,k bits = %d,%d,%d,%d)" % (
                         dom["kernel"], dom["nbat"], dom["nm"], dom["nn"], dom["nk"])}
     roofline["share_of_step"] = dom["ms"] / max(1e-9, sum(s["ms"] for s in trace))
+    if dom["kernel"] == 9128:
+        import hashlib
+        src = os.path.join(ROOT, "paper_2112_15083_gb300", "csrc", "tc.cuh")
+        rec = MEASURED_TRAFFIC.get(("tc_cgemm<128,3>", (dom["nbat"], dom["nm"], dom["nn"], dom["nk"])))
+        if rec and hashlib.sha256(open(src, "rb").read()).hexdigest()[:16] == rec[1]:
+            roofline["traffic"] = rec[0]
+            roofline["traffic_source"] = "ncu, profiles/tc_cgemm_dram_grid4x7_m14_b16384.md"
     roofline["measured"] = "CUDA events around each contraction launch over %d traced steps" % args.steps
     top_steps = []
     for s in sorted(trace, key=lambda s: -s["ms"])[:6]:
