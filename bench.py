@@ -55,6 +55,8 @@ def parse():
     ap.add_argument("--log2-batches", type=int, default=None, help="batches per step = 2^this (default: the workload's)")
     ap.add_argument("--autotune", type=int, default=1, help="kernel autotuning (1) or the fixed shape rules (0)")
     ap.add_argument("--serve", action="store_true", help="serving run (Poisson request stream) instead of the step bench")
+    ap.add_argument("--config4-sample", action="store_true",
+                    help="bounded sample of the 40-qubit 5x8 / 16-cycle configuration (time per slice, extrapolated)")
     ap.add_argument("--serve-window", type=float, default=60.0, help="seconds of arrivals")
     ap.add_argument("--serve-rate", type=float, default=4.0, help="requests per second")
     return ap.parse_args()
@@ -459,11 +461,86 @@ def run_serve(args):
     print(json.dumps(line), flush=True)
 
 
+def run_config4(args):
+    """Bounded sample of the 40-qubit configuration (5x8 grid, 16 cycles, 1/64 of the
+    slices retained, 100k samples): the plan slices legs until one slice's tensors fit
+    2^30 elements, Alg. 1 selects the retained slices, and the first retained slices are
+    contracted for one group of 4096 batches, alone and two at a time (shared
+    intermediates).  The full job's time is extrapolated from the measured time per
+    slice and group; nothing of it is run."""
+    import math
+    import numpy as np
+    import torch
+    import __graft_entry__
+    torch.cuda.set_device(0)
+    __graft_entry__.build()
+    import paper_2112_15083_gb300 as P
+    from paper_2112_15083_gb300 import circuits as cg
+    rows, cols, cycles, lb, f, N, alpha = 5, 8, 16, 12, 1.0 / 64, 100000, 2.0
+    circ = cg.sycamore_grid(rows, cols, cycles, seed=0)
+    openq = cg.default_open_qubits(rows, cols, 6)
+    C = P.circuit_load(circ.serialize())
+    t = time.perf_counter()
+    plan = P.plan(C, openq, log2_batches=lb, order_trials=256, order_seed=0, max_log2_tensor=30,
+                  hbm_budget_bytes=150e9, precision=P.tn.PREC_BF16X2, autotune=0, max_norm_flops=3e16)
+    plan_s = time.perf_counter() - t
+    info = plan.info()
+    line = {"metric": "config 4 bounded sample: seconds per retained slice per batch group (shared part amortised)",
+            "unit": "s",
+            "data": "synthetic", "n_gpus": 1,
+            "config": {"workload": "grid5x8_m16: 40-qubit 5x8 Sycamore-style ABCD circuit, 16 cycles, seed 0; "
+                                   "slices until one slice's tensors fit 2^30 elements; f = 1/64; %d batches of 64 "
+                                   "per group; bf16x2" % (1 << lb)},
+            "plan": {"seconds": round(plan_s, 1), "sliced_legs": info["n_sliced"],
+                     "log2_max_tensor": info["log2_max_tensor"], "flops_all_slices": info["flops_all_slices"]}}
+    t = time.perf_counter()
+    try:
+        slices, F = plan.select(f)
+        line["selection"] = {"seconds": round(time.perf_counter() - t, 1), "retained_slices": int(len(slices)),
+                             "F": F}
+    except P.TnError as e:
+        line["selection"] = {"error": str(e)}
+        print(json.dumps(line), flush=True)
+        return
+    T = 1 << lb
+    cb = np.random.default_rng(1).integers(0, 1 << 34, size=2 * T, dtype=np.int64).astype(np.uint64)
+    samples = []
+    for chunk in (1, 2):
+        sl = slices[:chunk]
+        nbytes, fl_first, fl_next = plan.estimate(sl)
+        row = {"slices": chunk, "device_bytes": nbytes, "flops_first_group": fl_first, "flops_later_group": fl_next}
+        for groups in (1, 2):
+            plan.contract(sl, cb[: groups * T])  # first execution (leaves, call plan, graphs)
+            torch.cuda.synchronize()
+            t = time.perf_counter()
+            plan.contract(sl, cb[: groups * T])
+            torch.cuda.synchronize()
+            row["seconds_%d_group%s" % (groups, "s" if groups > 1 else "")] = round(time.perf_counter() - t, 4)
+        # one group = batch-independent part + batch part; each later group adds the batch part
+        row["batch_part_s"] = round(row["seconds_2_groups"] - row["seconds_1_group"], 4)
+        row["shared_part_s"] = round(row["seconds_1_group"] - row["batch_part_s"], 4)
+        row["tflops_first_group"] = round(fl_first / row["seconds_1_group"] / 1e12, 1)
+        samples.append(row)
+    line["samples"] = samples
+    groups = math.ceil(1.1 * alpha * N / T)
+    best = min(samples, key=lambda r: (r["shared_part_s"] + groups * r["batch_part_s"]) / r["slices"])
+    per_slice = (best["shared_part_s"] + groups * best["batch_part_s"]) / best["slices"]
+    hours = per_slice * len(slices) / 3600.0
+    line["value"] = round(per_slice / groups, 4)
+    line["extrapolated"] = {"groups": groups, "retained_slices": int(len(slices)),
+                            "seconds_per_slice_all_groups": round(per_slice, 3), "hours": round(hours, 1),
+                            "note": "retained slices x (shared part + groups x batch part) per slice, from the "
+                                    "measured chunk of %d slice(s); the job itself is not run" % best["slices"]}
+    print(json.dumps(line), flush=True)
+
+
 if __name__ == "__main__":
     a = parse()
     if a.impl == "reference":
         run_reference(a)
     elif a.serve:
         run_serve(a)
+    elif a.config4_sample:
+        run_config4(a)
     else:
         run_ours(a)

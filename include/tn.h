@@ -72,6 +72,9 @@ typedef struct {
     uint64_t order_seed;     /* seed of the randomised greedy contraction order */
     int32_t order_trials;    /* greedy trials (best estimated time wins); <= 0: 64 */
     int32_t n_auto_sliced;   /* when sliced == NULL: how many edges the planner slices */
+    int32_t max_log2_tensor; /* when sliced == NULL and > 0: instead, slice edges until no
+                                tensor of one slice exceeds 2^max_log2_tensor elements
+                                (for circuits run a few slices at a time); 0: off */
     double hbm_budget_bytes; /* device working-set limit per call; <= 0: 64 GiB */
     double max_norm_flops;   /* tn_partial_norms refuses norm networks above this many
                                 algorithmic FLOPs (TN_EUNSUPPORTED); <= 0: 2e15 */

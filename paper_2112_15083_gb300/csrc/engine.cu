@@ -1232,6 +1232,7 @@ int tn_plan(tn_circuit_h c, const int32_t *order, int32_t n_order, const tn_edge
     }
     if (sliced && (n_sliced < 0 || n_sliced > 62)) { tn_set_error("n_sliced must be in [0,62]"); return TN_EINVAL; }
     if (!sliced && (o.n_auto_sliced < 0 || o.n_auto_sliced > 62)) { tn_set_error("n_auto_sliced in [0,62]"); return TN_EINVAL; }
+    if (o.max_log2_tensor < 0 || o.max_log2_tensor > 40) { tn_set_error("max_log2_tensor in [0,40]"); return TN_EINVAL; }
     int ndev = 0;
     if (cudaGetDeviceCount(&ndev) != cudaSuccess || ndev == 0) { tn_set_error("no CUDA device"); return TN_EDEVICE; }
     auto *p = new (std::nothrow) tn_plan_s;

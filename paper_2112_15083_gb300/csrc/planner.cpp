@@ -929,6 +929,44 @@ std::vector<int> tn_auto_slice(const Merged &mg, Network &net, Tree &t, int n_sl
     return picked;
 }
 
+// Slice legs until no tensor of the tree holds more than `target` network indices (the
+// per-version size, so that one slice's tensors fit in memory); each pick is the index
+// held by the most oversized tensors, weighted by 2^(excess bits).  Returns the picked
+// network ids (moved to sliced legs).
+std::vector<int> tn_width_slice(Network &net, Tree &t, int target, int max_legs) {
+    std::vector<int> picked;
+    std::vector<char> is_out(net.n_idx, 0);
+    for (int i : net.out_layout) is_out[i] = 1;
+    while ((int)picked.size() < max_legs) {
+        int maxb = 0;
+        for (auto &nd : t.nodes) maxb = std::max(maxb, nd.idx.count());
+        if (maxb <= target) break;
+        std::vector<int> cnt(net.n_idx, 0);
+        for (auto &L : net.leaves)
+            for (size_t l = 0; l < L.kind.size(); l++)
+                if (L.kind[l] == LEG_NET) cnt[L.ref[l]]++;
+        std::vector<double> score(net.n_idx, 0.0);
+        for (auto &nd : t.nodes) {
+            const int b = nd.idx.count();
+            if (b <= target) continue;
+            const double w = std::ldexp(1.0, b - target);
+            for (int id : nd.idx.list())
+                if (cnt[id] == 2 && !is_out[id]) score[id] += w;
+        }
+        int best = -1;
+        for (int id = 0; id < net.n_idx; id++)
+            if (score[id] > 0 && (best < 0 || score[id] > score[best])) best = id;
+        if (best < 0) break;
+        for (auto &L : net.leaves)
+            for (size_t l = 0; l < L.kind.size(); l++)
+                if (L.kind[l] == LEG_NET && L.ref[l] == best) { L.kind[l] = LEG_SLICED; L.ref[l] = net.n_sliced; }
+        slice_tree(t, best, net.n_sliced);
+        net.n_sliced++;
+        picked.push_back(best);
+    }
+    return picked;
+}
+
 // ------------------------------------------------------------------ compiler
 
 // Layout bits of a node: its network indices plus one bit per sliced leg below it that
@@ -1146,15 +1184,18 @@ int tn_plan_build_host(const Merged &mg, const tn_plan_opts &o, const int32_t *o
     bool have_t0 = false;
     if (sliced) {
         I.assign(sliced, sliced + n_sliced);
-    } else if (o.n_auto_sliced > 0) {
-        // order the unsliced network, slice it greedily, then re-order with the slices
+    } else if (o.n_auto_sliced > 0 || o.max_log2_tensor > 0) {
+        // order the unsliced network, slice it (by time, or down to a tensor size), then
+        // re-order with the slices (a size-targeted slicing keeps its tree)
         Network net0;
         int rc = tn_build_amp_network(mg, {}, open, o.log2_batches, net0, closed);
         if (rc) return rc;
         tn_cost_settings(net0, o);
+        if (o.max_log2_tensor > 0) net0.mem_limit_elems = 0;
         TreeCost tc0;
         tn_search_tree(net0, o.order_seed, o.order_trials > 0 ? o.order_trials : 64, t0, tc0);
-        std::vector<int> picked = tn_auto_slice(mg, net0, t0, o.n_auto_sliced);
+        std::vector<int> picked = o.max_log2_tensor > 0 ? tn_width_slice(net0, t0, o.max_log2_tensor, 62)
+                                                        : tn_auto_slice(mg, net0, t0, o.n_auto_sliced);
         for (int id : picked) {
             int seg = net0.idx_seg[id], q = 0;
             while (q + 1 < mg.n && mg.seg_base[q + 1] <= seg) q++;
@@ -1165,6 +1206,21 @@ int tn_plan_build_host(const Merged &mg, const tn_plan_opts &o, const int32_t *o
     int rc = tn_build_amp_network(mg, I, open, o.log2_batches, net, closed);
     if (rc) return rc;
     tn_cost_settings(net, o);
+    if (have_t0 && o.max_log2_tensor > 0) {
+        // keep the size-targeted tree: its per-slice tensors are what the slicing bounded
+        net.q_max = t0.q_max >= -1 ? t0.q_max : net.q_max;
+        tree = t0;
+        tn_recompute_deps(net, tree);
+        uint64_t E = net.n_sliced >= 64 ? ~0ull : ((1ull << net.n_sliced) - 1);
+        uint64_t E0 = 0;
+        rc = tn_compile(net, tree, E0, steps, o.precision != TN_PREC_C64);
+        if (rc == TN_EUNSUPPORTED) {
+            E0 = E;
+            rc = tn_compile(net, tree, E0, steps, o.precision != TN_PREC_C64);
+        }
+        if (E_used) *E_used = E0;
+        return rc;
+    }
     return tn_tree_and_compile(net, o, order, n_order, have_t0 ? &t0 : nullptr, tree, steps, E_used,
                                o.precision != TN_PREC_C64);
 }

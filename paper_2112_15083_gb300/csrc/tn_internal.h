@@ -173,6 +173,8 @@ void tn_search_tree(Network &net, uint64_t seed, int trials, Tree &best, TreeCos
 TreeCost tn_tree_cost(const Network &net, const Tree &t);
 void tn_recompute_deps(const Network &net, Tree &t);
 std::vector<int> tn_auto_slice(const Merged &mg, Network &net, Tree &t, int n_slice);
+// Slice until every tensor of one slice holds at most `target` indices (<= max_legs legs).
+std::vector<int> tn_width_slice(Network &net, Tree &t, int target, int max_legs);
 // Shapes run on the tensor cores in the split precisions: K >= 16 and M, N >= 64.
 inline bool tn_tc_shape(int nm, int nn, int nk) { return nk >= 4 && nm >= 6 && nn >= 6; }
 

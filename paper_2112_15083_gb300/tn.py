@@ -78,6 +78,7 @@ class PlanOpts(ctypes.Structure):
         ("order_seed", ctypes.c_uint64),
         ("order_trials", ctypes.c_int32),
         ("n_auto_sliced", ctypes.c_int32),
+        ("max_log2_tensor", ctypes.c_int32),
         ("hbm_budget_bytes", ctypes.c_double),
         ("max_norm_flops", ctypes.c_double),
         ("autotune", ctypes.c_int32),
@@ -234,7 +235,7 @@ class Plan:
     def __init__(self, circuit: Circuit, open_qubits, sliced=None, order=None, precision=PREC_C64,
                  log2_batches=8, order_seed=0, order_trials=64, n_auto_sliced=0,
                  hbm_budget_bytes=0.0, stream=None, use_torch_allocator=True, max_norm_flops=0.0,
-                 autotune=None):
+                 autotune=None, max_log2_tensor=0):
         L = lib()
         o = PlanOpts()
         L.tn_plan_opts_default(ctypes.byref(o))
@@ -243,6 +244,7 @@ class Plan:
         o.order_seed = order_seed
         o.order_trials = order_trials
         o.n_auto_sliced = n_auto_sliced
+        o.max_log2_tensor = max_log2_tensor
         if hbm_budget_bytes:
             o.hbm_budget_bytes = hbm_budget_bytes
         if max_norm_flops:
@@ -392,7 +394,7 @@ class Plan:
 
 
 def plan_host(circuit: Circuit, open_qubits, sliced=None, order=None, log2_batches=8, order_seed=0,
-              order_trials=64, n_auto_sliced=0, precision=PREC_C64):
+              order_trials=64, n_auto_sliced=0, precision=PREC_C64, max_log2_tensor=0):
     """Host-only planning (no GPU): (info dict, steps array (n_steps, 7), sliced edges).
     Step row: batch, m, n, k bits, log2 versions of C, A, B."""
     L = lib()
@@ -403,6 +405,7 @@ def plan_host(circuit: Circuit, open_qubits, sliced=None, order=None, log2_batch
     o.order_seed = order_seed
     o.order_trials = order_trials
     o.n_auto_sliced = n_auto_sliced
+    o.max_log2_tensor = max_log2_tensor
     openq = np.ascontiguousarray(np.asarray(open_qubits, dtype=np.int32))
     if sliced is not None:
         arr = (Edge * max(1, len(sliced)))(*[Edge(int(q), int(s)) for (q, s) in sliced])
