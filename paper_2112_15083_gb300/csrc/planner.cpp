@@ -7,6 +7,7 @@
 #include <array>
 #include <cmath>
 #include <cstring>
+#include <functional>
 #include <map>
 #include <random>
 #include <set>
@@ -517,46 +518,193 @@ void tn_recompute_deps(const Network &net, Tree &t) {
     if (t.root >= 0) seal_root(t.nodes[t.root], ic);
 }
 
-TreeCost tn_tree_cost(const Network &net, const Tree &t) {
-    TreeCost tc;
+namespace {
+
+// Estimated time, FLOPs and bytes of contracting a and b into c (see tn_tree_cost).
+struct StepEst {
+    double time, flops, bytes;
+};
+StepEst step_estimate(const Network &net, const Node &a, const Node &b, const Node &c, const Bits &closed,
+                      const Bits &beta) {
     // FFMA complex64 rate, HBM bandwidth and per-launch overhead (GB300 measurements of
     // the kernels in this library); tensor-core shaped steps at net.tc_flop_rate
     const double flop_rate = 3e13, bw = 5.5e12, launch = 4e-6;
-    Bits closed, beta;
+    // an operand with closed legs read by a batch step is gathered first
+    const bool ga = (a.ch[0] < 0 && a.beta) || (c.beta && !a.beta && (a.idx & closed).any());
+    const bool gb = (b.ch[0] < 0 && b.beta) || (c.beta && !b.beta && (b.idx & closed).any());
+    const Bits A = ga && !a.beta ? a.idx.andnot(closed) | beta : a.idx;
+    const Bits B = gb && !b.beta ? b.idx.andnot(closed) | beta : b.idx;
+    const double va = std::ldexp(1.0, __builtin_popcountll(a.dep)), vb = std::ldexp(1.0, __builtin_popcountll(b.dep));
+    const double ver = std::ldexp(1.0, __builtin_popcountll(c.dep));
+    const double fl = 8.0 * std::ldexp(1.0, (A | B).count()) * ver;
+    const double sa = 8.0 * std::ldexp(1.0, A.count()) * va, sb = 8.0 * std::ldexp(1.0, B.count()) * vb;
+    const double by = sa + sb + 8.0 * std::ldexp(1.0, c.idx.count()) * ver;
+    double gt = 0;
+    if (ga) gt += 2 * sa / bw + launch;
+    if (gb) gt += 2 * sb / bw + launch;
+    // FFMA kernels lose most of their rate when one side of the product is short
+    // (measured: ~7 TFLOP/s at 16 x 32 outputs per batch, ~1 TFLOP/s at 4 x 16)
+    const Bits &C = c.idx;
+    const int nm = (A & C).andnot(B).count(), nn = (B & C).andnot(A).count(), nk = (A & B).andnot(C).count();
+    const int lo = std::min(nm, nn), hi = std::max(nm, nn);
+    double rate = lo >= 6 ? flop_rate : hi >= 7 ? flop_rate / 2 : lo >= 4 ? flop_rate / 4 : flop_rate / 16;
+    if (net.tc_flop_rate > 0 && tn_tc_shape(hi, lo, nk)) rate = net.tc_flop_rate;
+    StepEst e;
+    e.flops = fl;
+    e.bytes = by + (ga ? 2 * sa : 0) + (gb ? 2 * sb : 0);
+    e.time = std::max(fl / rate, by / bw) + launch + gt;
+    if (net.mem_limit_elems > 0 && by / 8.0 > net.mem_limit_elems) e.time += 1e6 * (by / 8.0 / net.mem_limit_elems);
+    return e;
+}
+
+void closed_beta_masks(const Network &net, Bits &closed, Bits &beta) {
     for (int c = 0; c < net.n_closed; c++) closed.set(net.closed_base + c);
     for (int b = 0; b < net.n_beta; b++) beta.set(net.beta_base + b);
+}
+
+}  // namespace
+
+TreeCost tn_tree_cost(const Network &net, const Tree &t) {
+    TreeCost tc;
+    Bits closed, beta;
+    closed_beta_masks(net, closed, beta);
     for (auto &nd : t.nodes) {
         int l = nd.idx.count();
         tc.log2_max = std::max(tc.log2_max, l);
         tc.max_versioned = std::max(tc.max_versioned, std::ldexp(1.0, l + __builtin_popcountll(nd.dep)));
         if (nd.ch[0] < 0) continue;
-        const Node &a = t.nodes[nd.ch[0]], &b = t.nodes[nd.ch[1]];
-        // an operand with closed legs read by a batch step is gathered first
-        const bool ga = (a.ch[0] < 0 && a.beta) || (nd.beta && !a.beta && (a.idx & closed).any());
-        const bool gb = (b.ch[0] < 0 && b.beta) || (nd.beta && !b.beta && (b.idx & closed).any());
-        const Bits A = ga && !a.beta ? a.idx.andnot(closed) | beta : a.idx;
-        const Bits B = gb && !b.beta ? b.idx.andnot(closed) | beta : b.idx;
-        const double va = std::ldexp(1.0, __builtin_popcountll(a.dep)), vb = std::ldexp(1.0, __builtin_popcountll(b.dep));
-        double ver = std::ldexp(1.0, __builtin_popcountll(nd.dep));
-        double fl = 8.0 * std::ldexp(1.0, (A | B).count()) * ver;
-        double sa = 8.0 * std::ldexp(1.0, A.count()) * va, sb = 8.0 * std::ldexp(1.0, B.count()) * vb;
-        double by = sa + sb + 8.0 * std::ldexp(1.0, l) * ver;
-        double gt = 0;
-        if (ga) gt += 2 * sa / bw + launch;
-        if (gb) gt += 2 * sb / bw + launch;
-        // FFMA kernels lose most of their rate when one side of the product is short
-        // (measured: ~7 TFLOP/s at 16 x 32 outputs per batch, ~1 TFLOP/s at 4 x 16)
-        const Bits C = nd.idx;
-        const int nm = (A & C).andnot(B).count(), nn = (B & C).andnot(A).count(), nk = (A & B).andnot(C).count();
-        const int lo = std::min(nm, nn), hi = std::max(nm, nn);
-        double rate = lo >= 6 ? flop_rate : hi >= 7 ? flop_rate / 2 : lo >= 4 ? flop_rate / 4 : flop_rate / 16;
-        if (net.tc_flop_rate > 0 && tn_tc_shape(hi, lo, nk)) rate = net.tc_flop_rate;
-        tc.flops += fl;
-        tc.bytes += by + (ga ? 2 * sa : 0) + (gb ? 2 * sb : 0);
-        tc.time += std::max(fl / rate, by / bw) + launch + gt;
-        if (net.mem_limit_elems > 0 && by / 8.0 > net.mem_limit_elems) tc.time += 1e6 * (by / 8.0 / net.mem_limit_elems);
+        const StepEst e = step_estimate(net, t.nodes[nd.ch[0]], t.nodes[nd.ch[1]], nd, closed, beta);
+        tc.flops += e.flops;
+        tc.bytes += e.bytes;
+        tc.time += e.time;
     }
     return tc;
+}
+
+// Subtree reconfiguration: every subtree cut at up to `k` frontier tensors is replaced by
+// the order of least estimated time over those tensors (dynamic programming over subsets),
+// for a few passes.  The tree keeps its leaves and batch-selection threshold.
+void tn_reconfigure_tree(const Network &net, Tree &t, int k, int passes) {
+    if (t.nodes.size() < 3 || t.root < 0) return;
+    k = std::max(3, std::min(k, 10));
+    Bits closed, beta;
+    closed_beta_masks(net, closed, beta);
+    const int qmax = t.q_max >= -1 ? t.q_max : net.q_max;
+    std::vector<char> is_out(net.n_idx, 0);
+    for (int i : net.out_layout) is_out[i] = 1;
+    Bits outb;
+    for (int i : net.out_layout) outb.set(i);
+    const int NN = (int)t.nodes.size();
+    for (int pass = 0; pass < passes; pass++) {
+        bool improved = false;
+        // internal nodes, root first (breadth-first)
+        std::vector<int> order{t.root};
+        for (size_t q = 0; q < order.size(); q++)
+            for (int c : t.nodes[order[q]].ch)
+                if (c >= 0 && t.nodes[c].ch[0] >= 0) order.push_back(c);
+        for (int x : order) {
+            // frontier: expand the largest internal frontier node until k tensors
+            std::vector<int> fr{t.nodes[x].ch[0], t.nodes[x].ch[1]};
+            std::vector<int> internal{x};
+            while ((int)fr.size() < k) {
+                int bi = -1;
+                for (int i = 0; i < (int)fr.size(); i++)
+                    if (t.nodes[fr[i]].ch[0] >= 0 &&
+                        (bi < 0 || t.nodes[fr[i]].idx.count() > t.nodes[fr[bi]].idx.count()))
+                        bi = i;
+                if (bi < 0) break;
+                const int y = fr[bi];
+                internal.push_back(y);
+                fr[bi] = t.nodes[y].ch[0];
+                fr.push_back(t.nodes[y].ch[1]);
+            }
+            const int m = (int)fr.size();
+            if (m < 3) continue;
+            // current cost of the subtree
+            double cur = 0;
+            for (int y : internal)
+                cur += step_estimate(net, t.nodes[t.nodes[y].ch[0]], t.nodes[t.nodes[y].ch[1]], t.nodes[y], closed, beta).time;
+            // subset nodes
+            const Node &X = t.nodes[x];
+            const Bits ext = X.idx | closed | beta | outb;
+            const bool is_root = x == t.root;
+            const int full = (1 << m) - 1;
+            std::vector<Node> sub(full + 1);
+            std::vector<Bits> uni(full + 1);
+            for (int S = 1; S <= full; S++) {
+                const int lo = __builtin_ctz(S);
+                const int rest = S & (S - 1);
+                if (!rest) {
+                    sub[S] = t.nodes[fr[lo]];
+                    uni[S] = sub[S].idx;
+                    continue;
+                }
+                uni[S] = uni[1 << lo] | uni[rest];
+            }
+            for (int S = 1; S <= full; S++) {
+                if (!(S & (S - 1))) continue;
+                Node nd;
+                Bits others = uni[full & ~S];
+                Bits u = uni[S];
+                nd.idx = u & (ext | others);
+                nd.dep = 0;
+                bool anyb = false;
+                for (int i = 0; i < m; i++)
+                    if (S >> i & 1) {
+                        nd.dep |= t.nodes[fr[i]].dep;
+                        anyb = anyb || t.nodes[fr[i]].beta;
+                    }
+                nd.beta = anyb || (qmax >= 0 && (nd.idx & closed).count() > qmax) ||
+                          (S == full && is_root && (nd.idx & closed).any());
+                if (nd.beta) nd.idx = nd.idx.andnot(closed) | beta;
+                nd.ch[0] = 0;  // internal marker for step_estimate
+                sub[S] = nd;
+            }
+            std::vector<double> best(full + 1, 0.0);
+            std::vector<int> split(full + 1, 0);
+            for (int S = 1; S <= full; S++) {
+                if (!(S & (S - 1))) continue;
+                double bv = -1;
+                int bl = 0;
+                // each unordered split once: L holds the lowest element of S
+                const int low = S & -S;
+                for (int L = (S - 1) & S; L > 0; L = (L - 1) & S) {
+                    if (!(L & low)) continue;
+                    const int R = S ^ L;
+                    Node a = sub[L], b = sub[R];
+                    if (!(L & (L - 1))) a = t.nodes[fr[__builtin_ctz(L)]];
+                    if (!(R & (R - 1))) b = t.nodes[fr[__builtin_ctz(R)]];
+                    const double v = best[L] + best[R] + step_estimate(net, a, b, sub[S], closed, beta).time;
+                    if (bv < 0 || v < bv) { bv = v; bl = L; }
+                }
+                best[S] = bv;
+                split[S] = bl;
+            }
+            if (!(best[full] < cur * (1 - 1e-9))) continue;
+            // rebuild the subtree on the same internal node ids (x stays its root)
+            std::vector<int> pool(internal.begin() + 1, internal.end());
+            std::function<int(int, int)> build = [&](int S, int id) -> int {
+                if (!(S & (S - 1))) return fr[__builtin_ctz(S)];
+                const int L = split[S], R = S ^ L;
+                const int node = id >= 0 ? id : pool.back();
+                if (id < 0) pool.pop_back();
+                const int a = build(L, -1), b = build(R, -1);
+                Node &nd = t.nodes[node];
+                nd.idx = sub[S].idx;
+                nd.dep = sub[S].dep;
+                nd.beta = sub[S].beta;
+                nd.ch[0] = a;
+                nd.ch[1] = b;
+                nd.leaf = -1;
+                return node;
+            };
+            build(full, x);
+            improved = true;
+        }
+        if (!improved) break;
+    }
+    (void)NN;
+    (void)is_out;
 }
 
 namespace {
@@ -880,6 +1028,31 @@ void tn_search_tree(Network &net, uint64_t seed, int trials, Tree &best, TreeCos
     };
     for (size_t i = 0; i < qs.size(); i++) run(qs[i], i == 0 ? trials : std::max(1, trials / 2), seed + 131 * (qs[i] + 1));
     net.q_max = best_q;
+    // local improvement of the winner: optimal orders of its small subtrees
+    if (best.nodes.size() >= 4) {
+        Tree r = best;
+        tn_reconfigure_tree(net, r, 6, 3);
+        tn_reconfigure_tree(net, r, 8, 2);
+        std::vector<int32_t> pairs;
+        const int L = (int)net.leaves.size();
+        std::vector<int> newid(r.nodes.size(), -1);
+        for (int i = 0; i < L; i++) newid[i] = i;
+        int next = L;
+        std::function<void(int)> post = [&](int x) {
+            if (r.nodes[x].ch[0] < 0) return;
+            post(r.nodes[x].ch[0]);
+            post(r.nodes[x].ch[1]);
+            pairs.push_back(newid[r.nodes[x].ch[0]]);
+            pairs.push_back(newid[r.nodes[x].ch[1]]);
+            newid[x] = next++;
+        };
+        post(r.root);
+        Tree rebuilt;
+        if (tn_tree_from_ssa(net, pairs.data(), (int)pairs.size() / 2, rebuilt) == TN_OK) {
+            const TreeCost rc = tn_tree_cost(net, rebuilt);
+            if (rc.time < cost.time) { best = rebuilt; cost = rc; }
+        }
+    }
 }
 
 // Slice network index `id` in a tree: it leaves every tensor, and every tensor above a

@@ -170,6 +170,8 @@ void tn_greedy_tree(const Network &net, uint64_t seed, int trials, Tree &best, T
 // wins and net.q_max is set to the winner's threshold.
 void tn_bisect_tree(const Network &net, uint64_t seed, double eps, int cutoff, Tree &t);
 void tn_search_tree(Network &net, uint64_t seed, int trials, Tree &best, TreeCost &cost);
+// Replace each subtree cut at up to k frontier tensors by its cheapest order (subset DP).
+void tn_reconfigure_tree(const Network &net, Tree &t, int k, int passes);
 TreeCost tn_tree_cost(const Network &net, const Tree &t);
 void tn_recompute_deps(const Network &net, Tree &t);
 std::vector<int> tn_auto_slice(const Merged &mg, Network &net, Tree &t, int n_slice);
