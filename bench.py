@@ -481,17 +481,22 @@ def run_config4(args):
     openq = cg.default_open_qubits(rows, cols, 6)
     C = P.circuit_load(circ.serialize())
     t = time.perf_counter()
-    plan = P.plan(C, openq, log2_batches=lb, order_trials=256, order_seed=0, max_log2_tensor=30,
-                  hbm_budget_bytes=150e9, precision=P.tn.PREC_BF16X2, autotune=0, max_norm_flops=3e16)
+    # the largest tensor cap whose one-slice working set fits the budget
+    for cap in (30, 29, 28, 27, 26):
+        plan = P.plan(C, openq, log2_batches=lb, order_trials=256, order_seed=0, max_log2_tensor=cap,
+                      hbm_budget_bytes=150e9, precision=P.tn.PREC_BF16X2, autotune=0, max_norm_flops=3e16)
+        if plan.estimate(np.zeros(1, np.uint64))[0] <= 140e9:
+            break
+        del plan
     plan_s = time.perf_counter() - t
     info = plan.info()
     line = {"metric": "config 4 bounded sample: seconds per retained slice per batch group (shared part amortised)",
             "unit": "s",
             "data": "synthetic", "n_gpus": 1,
             "config": {"workload": "grid5x8_m16: 40-qubit 5x8 Sycamore-style ABCD circuit, 16 cycles, seed 0; "
-                                   "slices until one slice's tensors fit 2^30 elements; f = 1/64; %d batches of 64 "
+                                   "slices until one slice's working set fits 140 GB; f = 1/64; %d batches of 64 "
                                    "per group; bf16x2" % (1 << lb)},
-            "plan": {"seconds": round(plan_s, 1), "sliced_legs": info["n_sliced"],
+            "plan": {"seconds": round(plan_s, 1), "sliced_legs": info["n_sliced"], "max_log2_tensor_cap": cap,
                      "log2_max_tensor": info["log2_max_tensor"], "flops_all_slices": info["flops_all_slices"]}}
     t = time.perf_counter()
     try:
@@ -522,6 +527,17 @@ def run_config4(args):
         row["tflops_first_group"] = round(fl_first / row["seconds_1_group"] / 1e12, 1)
         samples.append(row)
     line["samples"] = samples
+    # per-step device times of one slice over two groups (the second reuses the shared part)
+    plan.trace(True)
+    plan.contract(slices[:1], cb[: 2 * T])
+    tr = plan.trace_read()
+    plan.trace(False)
+    tops = sorted(tr, key=lambda x: -x["ms"])[:10]
+    line["top_steps"] = [{"shape_bits": [x["nbat"], x["nm"], x["nn"], x["nk"]], "kernel": x["kernel"],
+                          "launches": x["launches"], "ms": round(x["ms"], 3),
+                          "tflops": round(x["flops_per_launch"] * x["launches"] / max(1e-9, x["ms"] / 1e3) / 1e12, 1),
+                          "gbs": round(x["bytes_per_launch"] * x["launches"] / max(1e-9, x["ms"] / 1e3) / 1e9, 1),
+                          "gathers": x["gathers"]} for x in tops]
     groups = math.ceil(1.1 * alpha * N / T)
     best = min(samples, key=lambda r: (r["shared_part_s"] + groups * r["batch_part_s"]) / r["slices"])
     per_slice = (best["shared_part_s"] + groups * best["batch_part_s"]) / best["slices"]

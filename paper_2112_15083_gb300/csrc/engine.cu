@@ -278,6 +278,8 @@ int setup_leaves(DevMem &mem, CNet &cn) {
                                 tnk::TcSmem<128, 3>::kBytes));
         CK(cudaFuncSetAttribute(tnk::tc_cgemm<64, 4>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                 tnk::TcSmem<64, 4>::kBytes));
+        CK(cudaFuncSetAttribute(tnk::tc_cgemm<32, 5>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                tnk::TcSmem<32, 5>::kBytes));
         smem_set = true;
     }
     for (auto &b : cn.leaf_src) release(mem, b);
@@ -595,15 +597,19 @@ int prepare_call(DevMem &mem, CNet &cn, const std::vector<uint64_t> &slices, dou
         CUtensorMap ma, mb;
         const void *ra = s.gat[0] ? static_cast<const char *>(cn.arena.p) + cp.goff[i][0] : region(s.a);
         const void *rb = s.gat[1] ? static_cast<const char *>(cn.arena.p) + cp.goff[i][1] : region(s.b);
-        // B for 128- and 64-column tiles (a folded B narrower than 64 columns only in the former)
-        CUtensorMap mb64;
+        // B for 128-, 64- and 32-column tiles (a folded B wider than a tile keeps the
+        // 128-column map; those variants are not offered for it)
+        CUtensorMap mb64, mb32;
         RC(encode_operand(&ma, ra, s.nk, s.nm, s.nbat, version_count(s.a), f16, cp.fold[i] == 1));
         RC(encode_operand(&mb, rb, s.nk, s.nn, s.nbat, version_count(s.b), f16, cp.fold[i] == 2));
         if (cp.fold[i] == 2 && s.nn > 6) mb64 = mb;
         else RC(encode_operand(&mb64, rb, s.nk, s.nn, s.nbat, version_count(s.b), f16, cp.fold[i] == 2, 64));
+        if (cp.fold[i] == 2 && s.nn > 5) mb32 = mb;
+        else RC(encode_operand(&mb32, rb, s.nk, s.nn, s.nbat, version_count(s.b), f16, cp.fold[i] == 2, 32));
         cp.maps.push_back(ma);
         cp.maps.push_back(mb);
         cp.maps.push_back(mb64);
+        cp.maps.push_back(mb32);
         const uint64_t Da = nodes[s.a].dep & cn.E, Db = nodes[s.b].dep & cn.E;
         for (uint64_t w : vals[s.c]) cp.vidx.push_back(version_index(s.a, w & Da));
         for (uint64_t w : vals[s.c]) cp.vidx.push_back(version_index(s.b, w & Db));
@@ -673,7 +679,7 @@ int prepare_call(DevMem &mem, CNet &cn, const std::vector<uint64_t> &slices, dou
 
 // Kernel variants of a step (ids as in tn_step_trace.kernel): 0 row kernel, 1 staged
 // small products, TM*1000+TN FFMA tile, 9128 / 9064 tensor-core tile of 128 / 64 columns.
-constexpr int kVarRow = 0, kVarSmall = 1, kVarTc128 = 9128, kVarTc64 = 9064;
+constexpr int kVarRow = 0, kVarSmall = 1, kVarTc128 = 9128, kVarTc64 = 9064, kVarTc32 = 9032;
 constexpr int kTiles[7][2] = {{128, 64}, {64, 64}, {128, 32}, {64, 32}, {32, 32}, {128, 16}, {16, 16}};
 
 bool small_fits(const Step &s, size_t esz) {
@@ -685,7 +691,11 @@ bool small_fits(const Step &s, size_t esz) {
 std::vector<int> step_variants(const CNet &cn, size_t si) {
     const Step &s = cn.steps[si];
     std::vector<int> v;
-    if (!cn.use_tc.empty() && cn.use_tc[si]) return {kVarTc128, kVarTc64};
+    if (!cn.use_tc.empty() && cn.use_tc[si]) {
+        if (s.nn <= 5) return {kVarTc32, kVarTc64};
+        if (s.nn == 6) return {kVarTc128, kVarTc64, kVarTc32};
+        return {kVarTc128, kVarTc64};
+    }
     if (std::min(s.nm, s.nn) <= 5 && s.nk <= 6) v.push_back(kVarRow);
     if (small_fits(s, (size_t)cn.elem)) v.push_back(kVarSmall);
     for (auto &t : kTiles)
@@ -696,7 +706,7 @@ std::vector<int> step_variants(const CNet &cn, size_t si) {
 // The fixed shape rules used without autotuning.
 int default_variant(const CNet &cn, size_t si) {
     const Step &s = cn.steps[si];
-    if (!cn.use_tc.empty() && cn.use_tc[si]) return kVarTc128;
+    if (!cn.use_tc.empty() && cn.use_tc[si]) return s.nn <= 5 ? kVarTc32 : kVarTc128;
     if (std::min(s.nm, s.nn) == 6 && std::max(s.nm, s.nn) == 6 && small_fits(s, (size_t)cn.elem)) return kVarSmall;
     if (std::min(s.nm, s.nn) <= 5 && s.nk <= 6) return kVarRow;
     // large products: 128 x 32 tiles (the autotuner's choice on GB300 for complex64)
@@ -751,7 +761,8 @@ int launch_tc(CNet &cn, const Step &s, size_t si, const tnk::GemmParams &p, cuda
         tp.group_m = (int)std::max<long long>(1, std::min<long long>({g, 64, tiles_m}));
     }
     const CUtensorMap *m = &cp.maps[cp.map_off[si]];
-    tnk::tc_cgemm<BN, ST><<<(unsigned)blocks, tnk::kTcThreads, Lay::kBytes, st>>>(m[0], m[BN == 128 ? 1 : 2], tp);
+    tnk::tc_cgemm<BN, ST><<<(unsigned)blocks, tnk::kTcThreads, Lay::kBytes, st>>>(m[0], m[BN == 128 ? 1 : BN == 64 ? 2 : 3],
+                                                                                 tp);
     CK(cudaGetLastError());
     return TN_OK;
 }
@@ -780,10 +791,11 @@ int launch_variant(CNet &cn, const Step &s, cudaStream_t st, int var) {
     p.out_fmt = cn.fmt[s.c];
     p.out_scale = cn.scale[s.c] / (cn.scale[s.a] * cn.scale[s.b]);
     if (cn.trace) cn.tr_kernel[si] = var;
-    if (var == kVarTc128 || var == kVarTc64) {
+    if (var == kVarTc128 || var == kVarTc64 || var == kVarTc32) {
         if constexpr (sizeof(T) == sizeof(float2)) {
             if (var == kVarTc128) return launch_tc<128, 3>(cn, s, si, p, st);
-            return launch_tc<64, 4>(cn, s, si, p, st);
+            if (var == kVarTc64) return launch_tc<64, 4>(cn, s, si, p, st);
+            return launch_tc<32, 5>(cn, s, si, p, st);
         }
         tn_set_error("tensor-core variant on a complex128 network");
         return TN_EINVAL;

@@ -548,7 +548,7 @@ StepEst step_estimate(const Network &net, const Node &a, const Node &b, const No
     const int nm = (A & C).andnot(B).count(), nn = (B & C).andnot(A).count(), nk = (A & B).andnot(C).count();
     const int lo = std::min(nm, nn), hi = std::max(nm, nn);
     double rate = lo >= 6 ? flop_rate : hi >= 7 ? flop_rate / 2 : lo >= 4 ? flop_rate / 4 : flop_rate / 16;
-    if (net.tc_flop_rate > 0 && tn_tc_shape(hi, lo, nk)) rate = net.tc_flop_rate;
+    if (net.tc_flop_rate > 0 && tn_tc_shape(hi, lo, nk)) rate = net.tc_flop_rate * (lo >= 6 ? 1.0 : 0.5);
     StepEst e;
     e.flops = fl;
     e.bytes = by + (ga ? 2 * sa : 0) + (gb ? 2 * sb : 0);
@@ -1213,7 +1213,14 @@ int tn_compile(const Network &net, Tree &t, uint64_t E, std::vector<Step> &steps
                 if (nn.has(c.layout[q])) { cn++; if (!first) first = 2; }
             }
             const bool m_low = cm > cn || (cm == cn && first == 1);
-            if (m_low != rows_side) { std::swap(a, b); std::swap(m, nn); std::swap(ga, gb); }
+            if (rows_side && tn_tc_narrow(m.count(), nn.count(), k.count())) {
+                // a 32-column tensor-core tile: the long side must be the rows
+                if (m.count() < nn.count()) { std::swap(a, b); std::swap(m, nn); std::swap(ga, gb); }
+            } else if (m_low != rows_side) {
+                std::swap(a, b);
+                std::swap(m, nn);
+                std::swap(ga, gb);
+            }
         }
         auto in_c_order = [&](const Bits &s) {
             std::vector<int> v;

@@ -2,6 +2,7 @@
 // compiled step list.  Host-only declarations (shared by planner.cpp and engine.cu).
 #pragma once
 
+#include <algorithm>
 #include <cstdint>
 #include <complex>
 #include <string>
@@ -177,8 +178,13 @@ void tn_recompute_deps(const Network &net, Tree &t);
 std::vector<int> tn_auto_slice(const Merged &mg, Network &net, Tree &t, int n_slice);
 // Slice until every tensor of one slice holds at most `target` indices (<= max_legs legs).
 std::vector<int> tn_width_slice(Network &net, Tree &t, int target, int max_legs);
-// Shapes run on the tensor cores in the split precisions: K >= 16 and M, N >= 64.
-inline bool tn_tc_shape(int nm, int nn, int nk) { return nk >= 4 && nm >= 6 && nn >= 6; }
+// Shapes run on the tensor cores in the split precisions: K >= 16 and either M, N >= 64,
+// or one side >= 128 (the rows) and the other >= 32 (32-column tiles).
+inline bool tn_tc_shape(int nm, int nn, int nk) {
+    return nk >= 4 && ((nm >= 6 && nn >= 6) || (std::max(nm, nn) >= 7 && std::min(nm, nn) >= 5));
+}
+// Tensor-core shapes whose short side needs the rows on the long side.
+inline bool tn_tc_narrow(int nm, int nn, int nk) { return tn_tc_shape(nm, nn, nk) && std::min(nm, nn) < 6; }
 
 // Compile with explicit-version legs E (bit e = I[e]); every other sliced leg below a
 // node is one more layout bit of that node (never summed until the root).  tc_roles:
