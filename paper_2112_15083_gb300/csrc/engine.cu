@@ -126,6 +126,7 @@ struct CNet {
     std::vector<float> scale;  // per node: stored value = true value * scale
     std::vector<char> use_tc;  // per step: tcgen05 kernel
     std::vector<int> variant;  // per step: kernel variant (-1: not chosen yet)
+    const uint64_t *cur_closed = nullptr;  // batch patterns of the execution being issued
     int autotune = 1;          // 1: time the applicable variants of unseen step shapes;
                                // 0: fixed shape rules; k >= 2: variant (step + k - 2) mod count
     DBuf err;                  // device error word of the bounded waits
@@ -648,6 +649,7 @@ int prepare_call(DevMem &mem, CNet &cn, const std::vector<uint64_t> &slices, dou
             for (int q = 0; q < g.nq; q++) g.q[q] = s.g_q[o][q];
             const int vw = g.esize == 2 ? 3 : g.esize == 8 ? 1 : 0;
             g.vec_log2 = lowrun >= vw ? vw : 0;
+            g.run_log2 = lowrun - g.vec_log2;
             if (g.src_plane != 1LL << (g.nbits - g.lb + g.nq)) {
                 tn_set_error("gather: stored operand size does not match its read layout");
                 return TN_EINVAL;
@@ -716,6 +718,26 @@ int default_variant(const CNet &cn, size_t si) {
     if (s.nm >= 5 && s.nn >= 5) return 32032;
     if (s.nm >= 7) return 128016;
     return 16016;
+}
+
+// The row kernel reads every gathered operand of step si through its gather (no copy)
+// when each one is a single complex version whose batch bits lie above the span the
+// kernel reads contiguously: a row (K) for the row operand, a batch's block (N x K) for
+// the other.  `swap` says whether the kernel exchanges the roles (the longer side rows).
+bool row_fuses(const CNet &cn, size_t si) {
+    const Step &s = cn.steps[si];
+    if (!(s.gat[0] || s.gat[1]) || cn.cp.gd_off.size() <= si + 1) return false;
+    const bool swap = s.nn > s.nm;
+    for (int o = 0; o < 2; o++) {
+        if (!s.gat[o]) continue;
+        const tnk::GatherDesc &g = cn.cp.gd[cn.cp.gd_off[si] + (o == 1 && s.gat[0] ? 1 : 0)];
+        if (g.nver != 1 || g.nplanes != 1 || g.esize != cn.elem || g.lb < 1) return false;
+        const int lowrun = g.pos_beta[g.lb - 1];
+        const bool is_rows = (o == 0) != swap;  // this operand plays the kernel's A (rows)
+        const int need = is_rows ? s.nk : s.nk + (swap ? s.nm : s.nn);
+        if (lowrun < need) return false;
+    }
+    return true;
 }
 
 template <int BN, int ST>
@@ -823,15 +845,23 @@ int launch_variant(CNet &cn, const Step &s, cudaStream_t st, int var) {
         tnk::cgemm_small<T><<<(unsigned)blocks, 256, smem, st>>>(p, sm);
     } else if (var == kVarRow) {
         // one thread per row of the larger side, the small side in registers (C = A B^T
-        // is symmetric in the operand roles)
+        // is symmetric in the operand roles); gathered operands read in place when possible
+        if (row_fuses(cn, si) && cn.cur_closed) {
+            const auto *gd = static_cast<const tnk::GatherDesc *>(cn.gdescs.p) + cn.cp.gd_off[si];
+            p.gA = s.gat[0] ? gd : nullptr;
+            p.gB = s.gat[1] ? gd + (s.gat[0] ? 1 : 0) : nullptr;
+            p.closed_bits = cn.cur_closed;
+        }
         if (s.nn > s.nm) {
             std::swap(p.ptrA, p.ptrB);
+            std::swap(p.gA, p.gB);
             std::swap(p.lm, p.ln);
             for (int i = 0; i < tnk::kMaxBits; i++) std::swap(p.pos_m[i], p.pos_n[i]);
             p.swapped = 1;
         }
         long long rows = p.nver << (p.lbat + p.lm);
-        unsigned blocks = (unsigned)((rows + 255) / 256);
+        // grid-stride: at most 16 resident blocks' worth per SM, each thread several rows
+        unsigned blocks = (unsigned)std::min<long long>((rows + 255) / 256, 16LL * num_sms());
         switch (p.ln) {
             case 0: tnk::cgemm_row<T, 1><<<blocks, 256, 0, st>>>(p); break;
             case 1: tnk::cgemm_row<T, 2><<<blocks, 256, 0, st>>>(p); break;
@@ -931,7 +961,9 @@ int execute(CNet &cn, const uint64_t *d_closed, bool skip_beta_free, double2 *ou
             }
             CK(cudaEventRecord(cn.ev[2 * si], st));
         }
-        RC(launch_gathers(cn, si, d_closed, st));
+        cn.cur_closed = d_closed;
+        const int var = si < cn.variant.size() && cn.variant[si] >= 0 ? cn.variant[si] : default_variant(cn, si);
+        if (!(var == kVarRow && d_closed && row_fuses(cn, si))) RC(launch_gathers(cn, si, d_closed, st));
         if (cn.elem == 8) RC(launch_step<float2>(cn, s, st));
         else RC(launch_step<double2>(cn, s, st));
         if (cn.calibrating) {
@@ -1002,6 +1034,7 @@ int tune_execute(CNet &cn, const uint64_t *d_closed, double2 *out, cudaStream_t 
         return TN_EDEVICE;
     }
     int rc = TN_OK;
+    cn.cur_closed = d_closed;
     for (size_t si = 0; si < cn.steps.size() && rc == TN_OK; si++) {
         const Step &s = cn.steps[si];
         rc = launch_gathers(cn, si, d_closed, st);

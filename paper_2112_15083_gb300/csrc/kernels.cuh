@@ -30,6 +30,41 @@ constexpr int kMaxBits = 40;
 // plane stride = the tensor's element count.  Both use 8 bytes per element.
 enum OutFmt { OUT_C64 = 0, OUT_SPLIT_BF16 = 1, OUT_SPLIT_FP16 = 2 };
 
+// A step operand whose closed output legs are selected per batch.  src stores the
+// operand with its nq closed legs as the top bits (every value of those legs, shared by
+// all batches); dst is the operand as the step reads it: nbits layout bits of which the
+// beta bits sit at pos_beta[t] and the other nbits - lb bits are src's low bits in order.
+// dst element e of batch beta = src element (sel << (nbits - lb)) | rest(e), where sel
+// packs the batch pattern's bits q[0], q[1], ... (closed positions).
+struct GatherDesc {
+    const char *src;
+    char *dst;
+    long long nver;              // versions (each: nplanes planes)
+    long long src_plane, dst_plane;  // elements per plane
+    int nplanes, esize;          // 4 x 2 B (split) or 1 x 8 B / 16 B
+    int nbits, lb, nq;
+    int vec_log2;                // log2 of elements per 16-byte chunk (0 when runs are shorter)
+    int run_log2;                // log2 of chunks per run: dst positions below the lowest beta
+                                 // position, where batch and selection stay constant
+    int8_t pos_beta[16];         // beta bit t -> dst position, sorted by descending position
+    int8_t beta_bit[16];         // ... and which beta bit sits there
+    int16_t q[32];
+};
+
+// Source element of dst element e (a run's first element in the run path).
+__device__ __forceinline__ long long gather_src(const GatherDesc &d, long long e, const uint64_t *closed_bits) {
+    long long rest = e, beta = 0;
+    for (int t = 0; t < d.lb; t++) {  // descending positions: remove each beta bit
+        const int p = d.pos_beta[t];
+        beta |= ((rest >> p) & 1) << d.beta_bit[t];
+        rest = (rest & ((1LL << p) - 1)) | ((rest >> (p + 1)) << p);
+    }
+    const uint64_t pat = closed_bits[beta];
+    long long sel = 0;
+    for (int i = 0; i < d.nq; i++) sel |= (long long)((pat >> d.q[i]) & 1) << i;
+    return (sel << (d.nbits - d.lb)) | rest;
+}
+
 struct GemmParams {
     const void *const *ptrA;  // per C-version operand base
     const void *const *ptrB;
@@ -41,6 +76,10 @@ struct GemmParams {
     float out_scale;          // multiplier applied before storing
     int swapped;              // operands exchanged (A holds the step's B): keep the step's
                               // operand order inside each complex multiply-add
+    // row kernel only: operands read through their batch gather instead of a gathered
+    // copy (null: not gathered); closed_bits are the group's batch patterns
+    const GatherDesc *gA, *gB;
+    const uint64_t *closed_bits;
     int8_t pos_bat[kMaxBits], pos_m[kMaxBits], pos_n[kMaxBits];
 };
 
@@ -107,20 +146,44 @@ template <typename T> __device__ __forceinline__ T czero();
 template <> __device__ __forceinline__ float2 czero<float2>() { return make_float2(0.f, 0.f); }
 template <> __device__ __forceinline__ double2 czero<double2>() { return make_double2(0.0, 0.0); }
 
-// One thread per output row (v, bat, m); all N (<= 16) columns in registers.  For the
+// One output row (v, bat, m) per thread and call; all N (<= 32) columns in registers.  For the
 // gate-absorption steps (small N and K), which are bound by HBM bandwidth.
+// Offset of a gathered operand's element e in its shared storage.  Lanes of a warp whose
+// elements share the batch and selection (same e >> shift) take the leader's decode.
+__device__ __forceinline__ long long gather_src_warp(const GatherDesc &d, long long e, int shift,
+                                                     const uint64_t *closed_bits) {
+    const unsigned mask = __activemask();
+    const int leader = __ffs(mask) - 1;
+    const long long e0 = __shfl_sync(mask, e, leader);
+    if (__all_sync(mask, (e >> shift) == (e0 >> shift))) {
+        long long s0 = 0;
+        if ((int)(threadIdx.x & 31) == leader) s0 = gather_src(d, e0, closed_bits);
+        s0 = __shfl_sync(mask, s0, leader);
+        return s0 + (e - e0);
+    }
+    return gather_src(d, e, closed_bits);
+}
+
 template <typename T, int N>
-__global__ void __launch_bounds__(256) cgemm_row(GemmParams p) {
-    const long long rows = p.nver << (p.lbat + p.lm);
-    const long long row = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    if (row >= rows) return;
+__device__ __forceinline__ void cgemm_row_one(const GemmParams &p, long long row) {
     const long long M = 1LL << p.lm;
     const long long m = row & (M - 1);
     const long long bat = (row >> p.lm) & ((1LL << p.lbat) - 1);
     const long long v = row >> (p.lm + p.lbat);
     const int K = 1 << p.lk;
-    const T *A = static_cast<const T *>(p.ptrA[v]) + (((bat << p.lm) | m) << p.lk);
-    const T *B = static_cast<const T *>(p.ptrB[v]) + (bat << (p.ln + p.lk));
+    const T *A, *B;
+    if (p.gA) {
+        const long long e = ((bat << p.lm) | m) << p.lk;
+        A = reinterpret_cast<const T *>(p.gA->src) + gather_src_warp(*p.gA, e, p.gA->pos_beta[p.gA->lb - 1], p.closed_bits);
+    } else {
+        A = static_cast<const T *>(p.ptrA[v]) + (((bat << p.lm) | m) << p.lk);
+    }
+    if (p.gB) {
+        const long long e = bat << (p.ln + p.lk);
+        B = reinterpret_cast<const T *>(p.gB->src) + gather_src_warp(*p.gB, e, p.gB->pos_beta[p.gB->lb - 1], p.closed_bits);
+    } else {
+        B = static_cast<const T *>(p.ptrB[v]) + (bat << (p.ln + p.lk));
+    }
     T acc[N];
 #pragma unroll
     for (int n = 0; n < N; n++) acc[n] = czero<T>();
@@ -142,6 +205,15 @@ __global__ void __launch_bounds__(256) cgemm_row(GemmParams p) {
     for (int n = 0; n < N; n++) store_c_t<T>(p, v, cb + scatter_bits(n, p.pos_n, p.ln), acc[n]);
 }
 
+// Grid-stride over rows (the grid is bounded by the launch).
+template <typename T, int N>
+__global__ void __launch_bounds__(256) cgemm_row(GemmParams p) {
+    const long long rows = p.nver << (p.lbat + p.lm);
+    for (long long row = (long long)blockIdx.x * blockDim.x + threadIdx.x; row < rows;
+         row += (long long)gridDim.x * blockDim.x)
+        cgemm_row_one<T, N>(p, row);
+}
+
 // Batched small products (M, N <= 64, K <= 64): a block stages the operands of 2^lg
 // consecutive batches in shared memory and walks that chunk's outputs in the order of
 // their positions in C (local bit i = chunk bit kind[i] / idx[i]), so consecutive threads
@@ -154,15 +226,17 @@ struct SmallMap {
 };
 
 template <typename T>
-__global__ void __launch_bounds__(256) cgemm_small(GemmParams p, SmallMap sm) {
+__global__ void __launch_bounds__(256) cgemm_small(GemmParams p, SmallMap smp) {
     extern __shared__ __align__(16) unsigned char small_smem[];
+    __shared__ SmallMap sm;  // its tables are read per output
+    if (threadIdx.x == 0) sm = smp;
     T *As = reinterpret_cast<T *>(small_smem);
-    const int M = 1 << p.lm, N = 1 << p.ln, K = 1 << p.lk, G = 1 << sm.lg;
+    const int M = 1 << p.lm, N = 1 << p.ln, K = 1 << p.lk, G = 1 << smp.lg;
     const int KP = K + 1;  // padded row: rows of consecutive outputs fall in different banks
     T *Bs = As + (size_t)G * M * KP;
-    const long long chunks = 1LL << (p.lbat - sm.lg);
+    const long long chunks = 1LL << (p.lbat - smp.lg);
     const long long v = (long long)blockIdx.x / chunks;
-    const long long bat0 = ((long long)blockIdx.x - v * chunks) << sm.lg;
+    const long long bat0 = ((long long)blockIdx.x - v * chunks) << smp.lg;
     if (v >= p.nver) return;
     const T *A = static_cast<const T *>(p.ptrA[v]) + (bat0 << (p.lm + p.lk));
     const T *B = static_cast<const T *>(p.ptrB[v]) + (bat0 << (p.ln + p.lk));
@@ -183,7 +257,7 @@ __global__ void __launch_bounds__(256) cgemm_small(GemmParams p, SmallMap sm) {
         const T *bb = Bs + (size_t)(b * N + n) * KP;
         T acc = czero<T>();
         for (int k = 0; k < K; k++) acc = cfma(a[k], bb[k], acc);
-        const long long off = cbase + scatter_bits(b, p.pos_bat, sm.lg) + scatter_bits(m, p.pos_m, p.lm) +
+        const long long off = cbase + scatter_bits(b, p.pos_bat, smp.lg) + scatter_bits(m, p.pos_m, p.lm) +
                               scatter_bits(n, p.pos_n, p.ln);
         store_c_t<T>(p, v, off, acc);
     }
@@ -302,51 +376,42 @@ __global__ void materialize(const MatDesc *descs) {
 
 // ---------------------------------------------------------------- batch gathers
 
-// A step operand whose closed output legs are selected per batch.  src stores the
-// operand with its nq closed legs as the top bits (every value of those legs, shared by
-// all batches); dst is the operand as the step reads it: nbits layout bits of which the
-// beta bits sit at pos_beta[t] and the other nbits - lb bits are src's low bits in order.
-// dst element e of batch beta = src element (sel << (nbits - lb)) | rest(e), where sel
-// packs the batch pattern's bits q[0], q[1], ... (closed positions).
-struct GatherDesc {
-    const char *src;
-    char *dst;
-    long long nver;              // versions (each: nplanes planes)
-    long long src_plane, dst_plane;  // elements per plane
-    int nplanes, esize;          // 4 x 2 B (split) or 1 x 8 B / 16 B
-    int nbits, lb, nq;
-    int vec_log2;                // log2 of elements per 16-byte chunk (0 when runs are shorter)
-    int8_t pos_beta[16];         // beta bit t -> dst position, sorted by descending position
-    int8_t beta_bit[16];         // ... and which beta bit sits there
-    int16_t q[32];
-};
+__device__ __forceinline__ void gather_copy(const GatherDesc &d, long long vp, long long e, long long se) {
+    const char *src = d.src + (vp * d.src_plane + se) * d.esize;
+    char *dst = d.dst + (vp * d.dst_plane + e) * d.esize;
+    if (d.vec_log2 > 0 || d.esize == 16) *reinterpret_cast<uint4 *>(dst) = *reinterpret_cast<const uint4 *>(src);
+    else if (d.esize == 8) *reinterpret_cast<uint2 *>(dst) = *reinterpret_cast<const uint2 *>(src);
+    else *reinterpret_cast<unsigned short *>(dst) = *reinterpret_cast<const unsigned short *>(src);
+}
 
-// grid.y = gather; threads over 16-byte chunks (or single elements) of dst.
+// grid.y = gather.  Runs of at least 32 chunks: one warp per run decodes the batch and
+// selection once and its lanes copy the run's 16-byte chunks; shorter runs: one thread
+// per chunk.  The descriptor is staged in shared memory.
 __global__ void gather_batches(const GatherDesc *descs, const uint64_t *closed_bits) {
-    const GatherDesc d = descs[blockIdx.y];
+    __shared__ GatherDesc d;
+    if (threadIdx.x == 0) d = descs[blockIdx.y];
+    __syncthreads();
     const int vl = d.vec_log2;
-    const long long per_plane = d.dst_plane >> vl;
+    const long long per_plane = d.dst_plane >> vl;  // chunks per plane
+    if (d.run_log2 >= 5) {
+        const int lr = d.run_log2, lane = threadIdx.x & 31;
+        const long long runs_plane = per_plane >> lr;
+        const long long runs = runs_plane * d.nplanes * d.nver;
+        const long long nw = ((long long)gridDim.x * blockDim.x) >> 5;
+        for (long long r = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5; r < runs; r += nw) {
+            const long long vp = r / runs_plane;
+            const long long e0 = (r - vp * runs_plane) << (lr + vl);
+            const long long se0 = gather_src(d, e0, closed_bits);
+            for (long long c = lane; c < (1LL << lr); c += 32) gather_copy(d, vp, e0 + (c << vl), se0 + (c << vl));
+        }
+        return;
+    }
     const long long total = per_plane * d.nplanes * d.nver;
-    const int nrest = d.nbits - d.lb;
     for (long long g = (long long)blockIdx.x * blockDim.x + threadIdx.x; g < total;
          g += (long long)gridDim.x * blockDim.x) {
         const long long vp = g / per_plane;
         const long long e = (g - vp * per_plane) << vl;
-        long long rest = e, beta = 0;
-        for (int t = 0; t < d.lb; t++) {  // descending positions: remove each beta bit
-            const int p = d.pos_beta[t];
-            beta |= ((rest >> p) & 1) << d.beta_bit[t];
-            rest = (rest & ((1LL << p) - 1)) | ((rest >> (p + 1)) << p);
-        }
-        const uint64_t pat = closed_bits[beta];
-        long long sel = 0;
-        for (int i = 0; i < d.nq; i++) sel |= (long long)((pat >> d.q[i]) & 1) << i;
-        const long long se = (sel << nrest) | rest;
-        const char *src = d.src + (vp * d.src_plane + se) * d.esize;
-        char *dst = d.dst + (vp * d.dst_plane + e) * d.esize;
-        if (vl > 0 || d.esize == 16) *reinterpret_cast<uint4 *>(dst) = *reinterpret_cast<const uint4 *>(src);
-        else if (d.esize == 8) *reinterpret_cast<uint2 *>(dst) = *reinterpret_cast<const uint2 *>(src);
-        else *reinterpret_cast<unsigned short *>(dst) = *reinterpret_cast<const unsigned short *>(src);
+        gather_copy(d, vp, e, gather_src(d, e, closed_bits));
     }
 }
 
