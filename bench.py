@@ -292,7 +292,8 @@ def run_ours(args):
     dom_ms = dom["ms"] / max(1, dom["launches"])
     pk = peaks()
     alg = dom["flops_per_launch"] / (dom_ms / 1e3) / 1e12
-    if dom["kernel"] == 9128:
+    shape = "(bat,m,n,k bits = %d,%d,%d,%d)" % (dom["nbat"], dom["nm"], dom["nn"], dom["nk"])
+    if dom["kernel"] in (9128, 9064, 9032):
         # tensor-core step: algorithmic complex FLOPs (8 per complex MAC) against the
         # measured dense bf16 peak; the split path issues 3x that on the tensor pipe
         peak = pk.get("bf16_tflops", 1900.0)
@@ -300,15 +301,31 @@ def run_ours(args):
                     "frac": alg / peak, "tensor_pipe_tflops": 3 * alg, "tensor_pipe_frac": 3 * alg / peak,
                     "peak_source": "measured bf16 dense burst (MEASURED_PEAKS.json)" if "bf16_tflops" in pk
                     else "fallback 1.9 PFLOP/s",
-                    "kernel": "tc_cgemm<128,3> split bf16 hi+lo (bat,m,n,k bits = %d,%d,%d,%d)" % (
-                        dom["nbat"], dom["nm"], dom["nn"], dom["nk"])}
+                    "kernel": "tc_cgemm<%d,%d> split bf16 hi+lo %s" % (
+                        dom["kernel"] - 9000, {9128: 3, 9064: 4, 9032: 5}[dom["kernel"]], shape)}
+    elif dom["kernel"] in (0, 1):
+        # short products (row kernel, staged small kernel): algorithmic bytes (operands
+        # read + result written, complex64; gathered operands at their batch size)
+        # against the measured copy bandwidth
+        gbs = dom["bytes_per_launch"] / (dom_ms / 1e3) / 1e9
+        peak = pk.get("hbm_gbs", 6800.0)
+        roofline = {"bound": "hbm", "achieved": gbs, "peak": peak, "unit": "GB/s", "traffic": None, "frac": gbs / peak,
+                    "peak_source": "measured HBM copy (MEASURED_PEAKS.json)" if "hbm_gbs" in pk else "fallback 6.8 TB/s",
+                    "kernel": "%s %s%s" % ("cgemm_row" if dom["kernel"] == 0 else "cgemm_small", shape,
+                                           " with batch gathers" if dom["gathers"] else "")}
     else:
         ffma_peak = 152 * 128 * 2 * 2.07e9 / 1e12
         roofline = {"bound": "alu", "achieved": alg, "peak": ffma_peak, "unit": "TFLOP/s", "traffic": None,
                     "frac": alg / ffma_peak, "peak_source": "derived: " + FFMA_PEAK_NOTE + " (FP32 FFMA, complex64 path)",
-                    "kernel": "cgemm_tile %d (bat,m,n,k bits = %d,%d,%d,%d)" % (
-                        dom["kernel"], dom["nbat"], dom["nm"], dom["nn"], dom["nk"])}
+                    "kernel": "cgemm_tile<%d,%d> %s" % (dom["kernel"] // 1000, dom["kernel"] % 1000, shape)}
     roofline["share_of_step"] = dom["ms"] / max(1e-9, sum(s["ms"] for s in trace))
+    # time per kernel family in the traced steps
+    fam = {}
+    for x in trace:
+        k = x["kernel"]
+        name = ("tc_cgemm" if k >= 9000 else "cgemm_row" if k == 0 else "cgemm_small" if k == 1 else "cgemm_tile")
+        fam[name] = fam.get(name, 0.0) + x["ms"] / max(1, x["launches"])
+    roofline["kernel_family_ms_per_step"] = {k: round(v, 2) for k, v in sorted(fam.items(), key=lambda kv: -kv[1])}
     if dom["kernel"] == 9128:
         import hashlib
         src = os.path.join(ROOT, "paper_2112_15083_gb300", "csrc", "tc.cuh")
