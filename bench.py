@@ -231,7 +231,8 @@ def run_ours(args):
     acc = [torch.empty(T, dtype=torch.uint8, device=dev) for _ in range(args.steps)]
     bits = [torch.empty(T, dtype=torch.int64, device=dev) for _ in range(args.steps)]
     flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
-    base_t = rank * (1 << 40)
+    from paper_2112_15083_gb300 import replicas
+    base_t = replicas.batch_t0(rank, 0, T)
     seed = args.seed
     for i in range(args.warmup):
         plan.sample_step(slices, F, seed, base_t + i * T, accept=acc[0], bits=bits[0])
@@ -267,14 +268,7 @@ def run_ours(args):
     trace = plan.trace_read()
     plan.trace(False)
     accepted = int(sum(int(a.sum().item()) for a in acc))
-    if world > 1:
-        t = torch.tensor([tot_ms, float(accepted)], dtype=torch.float64, device=dev)
-        mx = t.clone()
-        torch.distributed.all_reduce(mx, op=torch.distributed.ReduceOp.MAX)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.SUM)
-        tot_ms_max, accepted_all = float(mx[0]), float(t[1])
-    else:
-        tot_ms_max, accepted_all = tot_ms, float(accepted)
+    tot_ms_max, accepted_all = replicas.reduce_run(tot_ms, accepted, device=dev)
     value = accepted_all / (tot_ms_max / 1e3)
     # the last trace entry is the FP64 slice sum (kernel 2); the rest are contraction steps
     ssum = [s for s in trace if s["kernel"] == 2]
