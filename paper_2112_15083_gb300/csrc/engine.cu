@@ -108,6 +108,7 @@ struct CallPlan {
     std::vector<std::array<size_t, 2>> goff;   // per step: arena offsets of gathered operands
     std::vector<tnk::GatherDesc> gd;           // batch gathers (device copy in CNet::gdescs)
     std::vector<size_t> gd_off;                // per step: first gather descriptor
+    std::vector<uint64_t> gtab;                // their lookup tables (device copy in CNet::gtabs)
     bool valid = false;
 };
 
@@ -139,7 +140,7 @@ struct CNet {
     std::vector<DBuf> leaf_src, leaf_dst;
     std::vector<int> leaf_codebits;
     std::vector<std::vector<int>> leaf_sl;  // sliced legs (e) in leg order
-    DBuf arena, tables, vidx_dev, gdescs;
+    DBuf arena, tables, vidx_dev, gdescs, gtabs;
     CallPlan cp;
     std::vector<int> parent;
     size_t leaf_bytes = 0;
@@ -365,6 +366,7 @@ void free_cnet(DevMem &mem, CNet &cn) {
     for (auto &b : cn.leaf_src) release(mem, b);
     for (auto &b : cn.leaf_dst) release(mem, b);
     release(mem, cn.gdescs);
+    release(mem, cn.gtabs);
     release(mem, cn.arena);
     release(mem, cn.tables);
     release(mem, cn.vidx_dev);
@@ -659,6 +661,39 @@ int prepare_call(DevMem &mem, CNet &cn, const std::vector<uint64_t> &slices, dou
     }
     cp.gd_off[cn.steps.size()] = cp.gd.size();
     if (!cp.gd.empty()) {
+        // byte lookup tables of every gather's bit maps (see tnk::GatherDesc)
+        const size_t W = tnk::kGatherTabWords;
+        cp.gtab.assign(cp.gd.size() * W, 0ull);
+        RC(ensure(mem, cn.gtabs, cp.gtab.size() * sizeof(uint64_t)));
+        for (size_t gi = 0; gi < cp.gd.size(); gi++) {
+            tnk::GatherDesc &g = cp.gd[gi];
+            uint64_t *rest = cp.gtab.data() + gi * W;
+            uint32_t *beta = reinterpret_cast<uint32_t *>(rest + 5 * 256), *sel = beta + 5 * 256;
+            int bt[64], rank[64];
+            for (int q = 0; q < 64; q++) bt[q] = -1;
+            for (int t = 0; t < g.lb; t++) bt[g.pos_beta[t]] = g.beta_bit[t];
+            for (int q = 0, r = 0; q < 64; q++) rank[q] = bt[q] >= 0 ? -1 : r++;
+            for (int j = 0; j < 5; j++)
+                for (int x = 0; x < 256; x++)
+                    for (int b = 0; b < 8; b++) {
+                        const int q = 8 * j + b;
+                        if (!((x >> b) & 1) || q >= g.nbits) continue;
+                        if (bt[q] >= 0) beta[j * 256 + x] |= 1u << bt[q];
+                        else rest[j * 256 + x] |= 1ull << rank[q];
+                    }
+            for (int j = 0; j < 8; j++)
+                for (int x = 0; x < 256; x++)
+                    for (int i = 0; i < g.nq; i++) {
+                        const int c = g.q[i] - 8 * j;
+                        if (c >= 0 && c < 8 && ((x >> c) & 1)) sel[j * 256 + x] |= 1u << i;
+                    }
+            const uint64_t *dev = static_cast<const uint64_t *>(cn.gtabs.p) + gi * W;
+            g.rest_tab = dev;
+            g.beta_tab = reinterpret_cast<const uint32_t *>(dev + 5 * 256);
+            g.sel_tab = g.beta_tab + 5 * 256;
+        }
+        CK(cudaMemcpyAsync(cn.gtabs.p, cp.gtab.data(), cp.gtab.size() * sizeof(uint64_t), cudaMemcpyHostToDevice,
+                           mem.stream));
         RC(ensure(mem, cn.gdescs, cp.gd.size() * sizeof(tnk::GatherDesc)));
         CK(cudaMemcpyAsync(cn.gdescs.p, cp.gd.data(), cp.gd.size() * sizeof(tnk::GatherDesc), cudaMemcpyHostToDevice,
                            mem.stream));

@@ -49,20 +49,30 @@ struct GatherDesc {
     int8_t pos_beta[16];         // beta bit t -> dst position, sorted by descending position
     int8_t beta_bit[16];         // ... and which beta bit sits there
     int16_t q[32];
+    // byte lookup tables of the same maps (built on the host): for byte j of e and value x,
+    // rest_tab[j][x] and beta_tab[j][x] are the contributions of x << 8j to the source's low
+    // bits and to the batch index; sel_tab[j][x] that of byte j of the batch pattern
+    const uint64_t *rest_tab;    // [5][256]
+    const uint32_t *beta_tab;    // [5][256]
+    const uint32_t *sel_tab;     // [8][256]
 };
+constexpr int kGatherTabWords = 5 * 256 + (5 * 256 + 8 * 256) / 2;  // 64-bit words per gather
 
 // Source element of dst element e (a run's first element in the run path).
 __device__ __forceinline__ long long gather_src(const GatherDesc &d, long long e, const uint64_t *closed_bits) {
-    long long rest = e, beta = 0;
-    for (int t = 0; t < d.lb; t++) {  // descending positions: remove each beta bit
-        const int p = d.pos_beta[t];
-        beta |= ((rest >> p) & 1) << d.beta_bit[t];
-        rest = (rest & ((1LL << p) - 1)) | ((rest >> (p + 1)) << p);
+    uint64_t rest = 0;
+    uint32_t beta = 0;
+#pragma unroll
+    for (int j = 0; j < 5; j++) {
+        const uint32_t x = (uint32_t)(e >> (8 * j)) & 255u;
+        rest |= __ldg(&d.rest_tab[j * 256 + x]);
+        beta |= __ldg(&d.beta_tab[j * 256 + x]);
     }
     const uint64_t pat = closed_bits[beta];
-    long long sel = 0;
-    for (int i = 0; i < d.nq; i++) sel |= (long long)((pat >> d.q[i]) & 1) << i;
-    return (sel << (d.nbits - d.lb)) | rest;
+    uint64_t sel = 0;
+#pragma unroll
+    for (int j = 0; j < 8; j++) sel |= __ldg(&d.sel_tab[j * 256 + (uint32_t)((pat >> (8 * j)) & 255u)]);
+    return (long long)((sel << (d.nbits - d.lb)) | rest);
 }
 
 struct GemmParams {
