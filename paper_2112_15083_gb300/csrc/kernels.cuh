@@ -197,18 +197,29 @@ __device__ __forceinline__ void cgemm_row_one(const GemmParams &p, long long row
     T acc[N];
 #pragma unroll
     for (int n = 0; n < N; n++) acc[n] = czero<T>();
-    if (p.swapped) {
-        for (int k = 0; k < K; k++) {
-            T a = A[k];
+    // complex64 rows of even K are read 16 bytes (two elements) at a time; the
+    // accumulation order over k is the same either way
+    auto step = [&](const T a, int k) {
+        if (p.swapped) {
 #pragma unroll
             for (int n = 0; n < N; n++) acc[n] = cfma(__ldg(&B[(n << p.lk) + k]), a, acc[n]);
-        }
-    } else {
-        for (int k = 0; k < K; k++) {
-            T a = A[k];
+        } else {
 #pragma unroll
             for (int n = 0; n < N; n++) acc[n] = cfma(a, __ldg(&B[(n << p.lk) + k]), acc[n]);
         }
+    };
+    if constexpr (sizeof(T) == 8) {
+        if (K >= 2) {
+            for (int k = 0; k < K; k += 2) {
+                const float4 v = *reinterpret_cast<const float4 *>(A + k);
+                step(make_float2(v.x, v.y), k);
+                step(make_float2(v.z, v.w), k + 1);
+            }
+        } else {
+            step(A[0], 0);
+        }
+    } else {
+        for (int k = 0; k < K; k++) step(A[k], k);
     }
     const long long cb = scatter_bits(bat, p.pos_bat, p.lbat) + scatter_bits(m, p.pos_m, p.lm);
 #pragma unroll
