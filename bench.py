@@ -34,9 +34,12 @@ WORKLOADS = {
 WORKLOAD = WORKLOADS["grid4x7_m14"]
 METRIC = "samples/s at fixed fidelity"
 # DRAM traffic (dram__bytes_read.sum + dram__bytes_write.sum, bytes per launch) of the
-# dominant kernel from one ncu capture of this workload (profiles/tc_cgemm_dram_grid4x7_m14_b16384.md),
-# valid for the kernel source it was taken with (sha256 prefix of csrc/tc.cuh)
-MEASURED_TRAFFIC = {("tc_cgemm<128,3>", (1, 15, 14, 12)): (83.75e9, "cbda2ea2f13a3e53")}
+# dominant launch from one-pass ncu captures of this workload (profiles/*_dram_grid4x7_m14_b16384.md),
+# valid for the kernel source it was taken with (sha256 prefix of the named csrc file)
+MEASURED_TRAFFIC = {
+    ("tc_cgemm<128,3>", (1, 15, 14, 12)): (83.75e9, "tc.cuh", "cbda2ea2f13a3e53"),
+    ("cgemm_row", (23, 2, 5, 2)): (16.95e9, "kernels.cuh", "e2dc3ed40cd00353"),
+}
 FFMA_PEAK_NOTE = "152 SMs x 128 FP32 lanes x 2 FLOP x 2070 MHz"
 
 
@@ -320,13 +323,14 @@ def run_ours(args):
         name = ("tc_cgemm" if k >= 9000 else "cgemm_row" if k == 0 else "cgemm_small" if k == 1 else "cgemm_tile")
         fam[name] = fam.get(name, 0.0) + x["ms"] / max(1, x["launches"])
     roofline["kernel_family_ms_per_step"] = {k: round(v, 2) for k, v in sorted(fam.items(), key=lambda kv: -kv[1])}
-    if dom["kernel"] == 9128:
+    key = {9128: "tc_cgemm<128,3>", 0: "cgemm_row"}.get(dom["kernel"])
+    rec = MEASURED_TRAFFIC.get((key, (dom["nbat"], dom["nm"], dom["nn"], dom["nk"]))) if key else None
+    if rec:
         import hashlib
-        src = os.path.join(ROOT, "paper_2112_15083_gb300", "csrc", "tc.cuh")
-        rec = MEASURED_TRAFFIC.get(("tc_cgemm<128,3>", (dom["nbat"], dom["nm"], dom["nn"], dom["nk"])))
-        if rec and hashlib.sha256(open(src, "rb").read()).hexdigest()[:16] == rec[1]:
+        src = os.path.join(ROOT, "paper_2112_15083_gb300", "csrc", rec[1])
+        if hashlib.sha256(open(src, "rb").read()).hexdigest()[:16] == rec[2]:
             roofline["traffic"] = rec[0]
-            roofline["traffic_source"] = "ncu, profiles/tc_cgemm_dram_grid4x7_m14_b16384.md"
+            roofline["traffic_source"] = "ncu dram__bytes_read.sum + dram__bytes_write.sum, one pass, full size (profiles/)"
     roofline["measured"] = "CUDA events around each contraction launch over %d traced steps" % args.steps
     top_steps = []
     for s in sorted(trace, key=lambda s: -s["ms"])[:6]:
