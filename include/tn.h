@@ -42,7 +42,7 @@ extern "C" {
 #define TN_ENOMEM (-2)       /* host or device allocation failed, or the HBM budget is exceeded */
 #define TN_ETIMEOUT (-3)     /* a bounded device-side wait gave up */
 #define TN_EDEVICE (-4)      /* CUDA error (no device, launch failure, ...) */
-#define TN_EUNSUPPORTED (-5) /* valid request outside what this build implements */
+#define TN_EUNSUPPORTED (-5) /* valid request outside what libtn implements */
 
 /* Precision of the pairwise contractions (north-star "split precision"). */
 #define TN_PREC_C64 0    /* complex64 operands, FP32 FFMA accumulation */
