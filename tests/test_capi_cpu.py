@@ -110,3 +110,30 @@ def test_alg2_matches_oracle(grid, f):
     C = pkg.circuit_load(circ.serialize())
     got = [I[i] for i in pkg.tn.sliced_vertex_select(C, I, k0)]
     assert got == ref
+
+
+@pytest.mark.parametrize("cap", [24, 20])
+def test_width_slicing_caps_every_tensor(cap):
+    """max_log2_tensor slices legs until no tensor of one slice exceeds 2^cap elements."""
+    circ = cg.sycamore_grid(4, 6, 12, seed=3)
+    C = pkg.circuit_load(circ.serialize())
+    info, steps, sliced = pkg.tn.plan_host(C, cg.default_open_qubits(4, 6, 6), log2_batches=8, order_trials=16,
+                                           max_log2_tensor=cap, precision=pkg.tn.PREC_BF16X2)
+    assert info["log2_max_tensor"] <= cap
+    assert info["n_sliced"] == len(sliced) >= 1
+    cnt = oracle.two_qubit_counts(circ)
+    for q, s in sliced:
+        assert 1 <= s < cnt[q]
+
+
+def test_order_search_is_deterministic():
+    """The seeded order search (greedy, bisection, thresholds, subtree reconfiguration)
+    gives the same plan for the same seed, and a plan for another seed is still valid."""
+    circ = cg.sycamore_grid(4, 5, 10, seed=2)
+    C = pkg.circuit_load(circ.serialize())
+    openq = cg.default_open_qubits(4, 5, 6)
+    a = pkg.tn.plan_host(C, openq, n_auto_sliced=6, log2_batches=10, order_trials=16, order_seed=7)
+    b = pkg.tn.plan_host(C, openq, n_auto_sliced=6, log2_batches=10, order_trials=16, order_seed=7)
+    assert a[0] == b[0] and np.array_equal(a[1], b[1]) and a[2] == b[2]
+    c = pkg.tn.plan_host(C, openq, n_auto_sliced=6, log2_batches=10, order_trials=16, order_seed=8)
+    assert c[0]["n_steps"] == a[0]["n_steps"]
