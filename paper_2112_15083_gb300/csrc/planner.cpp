@@ -590,11 +590,8 @@ void tn_reconfigure_tree(const Network &net, Tree &t, int k, int passes) {
     Bits closed, beta;
     closed_beta_masks(net, closed, beta);
     const int qmax = t.q_max >= -1 ? t.q_max : net.q_max;
-    std::vector<char> is_out(net.n_idx, 0);
-    for (int i : net.out_layout) is_out[i] = 1;
     Bits outb;
     for (int i : net.out_layout) outb.set(i);
-    const int NN = (int)t.nodes.size();
     for (int pass = 0; pass < passes; pass++) {
         bool improved = false;
         // internal nodes, root first (breadth-first)
@@ -703,8 +700,6 @@ void tn_reconfigure_tree(const Network &net, Tree &t, int k, int passes) {
         }
         if (!improved) break;
     }
-    (void)NN;
-    (void)is_out;
 }
 
 namespace {

@@ -57,7 +57,7 @@ struct Bits {
 
 // ------------------------------------------------------------------ network
 // Leg kinds of a leaf tensor.
-enum LegKind { LEG_NET = 0, LEG_SLICED = 1, LEG_CLOSED = 2 };
+enum LegKind { LEG_NET = 0, LEG_SLICED = 1 };  // closed outputs are network legs (Network::closed_base)
 
 struct Leaf {
     // data index = sum_t value(leg t) << t
