@@ -2,8 +2,9 @@
 //
 // Requests (circuit, open qubits, precision, target fidelity f, N, seed) are planned on
 // planner threads (tn_plan + tn_select + tn_plan_estimate, each request on its own CUDA
-// stream), admitted by a scheduler thread while the sum of admitted device-memory
-// estimates stays within the HBM budget, and then advanced one batch group at a time:
+// stream), admitted by a scheduler thread (shortest estimated job first, aged by waiting
+// time) while the sum of admitted device-memory estimates stays within the HBM budget,
+// and then advanced one batch group at a time:
 // every active request always has one group in flight on its own stream, so the groups
 // of different requests overlap on the device and a request that arrives while others
 // run is admitted as soon as a slot and memory are free.  A request's samples depend only
@@ -38,6 +39,7 @@ struct Req {
     std::vector<unsigned char> circuit;
     std::vector<int32_t> open;
     int32_t precision = TN_PREC_C64, n_sliced = 0;
+    double est_s = 0;  // estimated GPU seconds (admission order)
     double f = 1.0, alpha = 2.0;
     int64_t N = 0;
     uint64_t seed = 0;
@@ -168,6 +170,7 @@ void planner_loop(tn_server_s *s) {
         const double groups = std::ceil(1.1 * r->alpha * (double)r->N / (double)r->T);
         const double est_s =
             (r->flops_first + std::max(0.0, groups - 1) * r->flops_next) / rate_of(s, r->precision);
+        r->est_s = est_s;
         if (est_s > s->o.max_request_seconds || (double)r->est_bytes > s->o.hbm_budget_bytes) {
             r->message = "rejected: estimated " + std::to_string(est_s) + " s / " + std::to_string(r->est_bytes) +
                          " bytes exceed the server limits";
@@ -215,7 +218,16 @@ void sched_loop(tn_server_s *s) {
             if (s->active.empty())
                 s->cv_sched.wait(lk, [&] { return s->stop || !s->planned.empty(); });
             if (s->stop && s->active.empty()) return;
-            // admission: first fit in arrival order within the budget and the slot count
+            // admission: first fit within the budget and the slot count, shortest estimated
+            // job first, a request's estimate reduced by the time it has waited (so long
+            // jobs are not starved)
+            {
+                const double tn = now_s(s->t0);
+                std::stable_sort(s->planned.begin(), s->planned.end(),
+                                 [&](const std::shared_ptr<Req> &x, const std::shared_ptr<Req> &y) {
+                                     return x->est_s - (tn - x->t_submit) < y->est_s - (tn - y->t_submit);
+                                 });
+            }
             for (auto it = s->planned.begin(); it != s->planned.end();) {
                 Req &r = **it;
                 if ((int)s->active.size() >= s->o.max_active) break;
