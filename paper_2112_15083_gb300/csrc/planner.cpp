@@ -994,60 +994,83 @@ void tn_bisect_tree(const Network &net, uint64_t seed, double eps, int cutoff, T
     t.q_max = net.q_max;
 }
 
+namespace {
+
+// The tree rebuilt in SSA order after its subtrees were reconfigured (net.q_max must be
+// the tree's threshold).
+bool reconfigured(Network &net, const Tree &t, Tree &out) {
+    Tree r = t;
+    tn_reconfigure_tree(net, r, 6, 3);
+    tn_reconfigure_tree(net, r, 8, 2);
+    std::vector<int32_t> pairs;
+    const int L = (int)net.leaves.size();
+    std::vector<int> newid(r.nodes.size(), -1);
+    for (int i = 0; i < L; i++) newid[i] = i;
+    int next = L;
+    std::function<void(int)> post = [&](int x) {
+        if (r.nodes[x].ch[0] < 0) return;
+        post(r.nodes[x].ch[0]);
+        post(r.nodes[x].ch[1]);
+        pairs.push_back(newid[r.nodes[x].ch[0]]);
+        pairs.push_back(newid[r.nodes[x].ch[1]]);
+        newid[x] = next++;
+    };
+    post(r.root);
+    return tn_tree_from_ssa(net, pairs.data(), (int)pairs.size() / 2, out) == TN_OK;
+}
+
+}  // namespace
+
 void tn_search_tree(Network &net, uint64_t seed, int trials, Tree &best, TreeCost &cost) {
-    // batch-selection thresholds to try: 0 (select at the first closed leg) up to
-    // log2 T (a batch-independent tensor never larger than its batch form)
-    // -1: leaves with closed legs in batch form from the start (full trials); then half
-    // the trials at a middle threshold and at log2 T
+    // batch-selection thresholds to try: -1 (leaves with closed legs in batch form from
+    // the start; all trials), then log2 T / 2 and log2 T (half the trials each)
     std::vector<int> qs{net.q_max};
     if (net.n_closed > 0 && net.n_beta > 0) qs = {-1, net.n_beta / 2, net.n_beta};
+    std::mt19937_64 rng(seed * 0x9E3779B97F4A7C15ull + 99991);
     bool have = false;
     int best_q = net.q_max;
-    std::mt19937_64 rng(seed * 0x9E3779B97F4A7C15ull + 99991);
-    auto run = [&](int q, int n, uint64_t sd) {
+    for (size_t qi = 0; qi < qs.size(); qi++) {
+        const int q = qs[qi], n = qi == 0 ? trials : std::max(1, trials / 2);
         net.q_max = q;
-        Tree t;
-        TreeCost c;
-        tn_greedy_tree(net, sd, n, t, c);
-        if (!have || c.time < cost.time) { best = t; cost = c; best_q = q; have = true; }
-        // networks large enough for the greedy to go wrong also get bisection trials
-        if (net.leaves.size() < 48) return;
-        for (int tr = 0; tr < n; tr++) {
-            double eps = std::uniform_real_distribution<double>(0.02, 0.6)(rng);
-            int cutoff = 4 + (int)(rng() % 24);
-            Tree tb;
-            tn_bisect_tree(net, rng(), eps, cutoff, tb);
-            TreeCost cb = tn_tree_cost(net, tb);
-            if (cb.time < cost.time) { best = tb; cost = cb; best_q = q; }
-        }
-    };
-    for (size_t i = 0; i < qs.size(); i++) run(qs[i], i == 0 ? trials : std::max(1, trials / 2), seed + 131 * (qs[i] + 1));
-    net.q_max = best_q;
-    // local improvement of the winner: optimal orders of its small subtrees
-    if (best.nodes.size() >= 4) {
-        Tree r = best;
-        tn_reconfigure_tree(net, r, 6, 3);
-        tn_reconfigure_tree(net, r, 8, 2);
-        std::vector<int32_t> pairs;
-        const int L = (int)net.leaves.size();
-        std::vector<int> newid(r.nodes.size(), -1);
-        for (int i = 0; i < L; i++) newid[i] = i;
-        int next = L;
-        std::function<void(int)> post = [&](int x) {
-            if (r.nodes[x].ch[0] < 0) return;
-            post(r.nodes[x].ch[0]);
-            post(r.nodes[x].ch[1]);
-            pairs.push_back(newid[r.nodes[x].ch[0]]);
-            pairs.push_back(newid[r.nodes[x].ch[1]]);
-            newid[x] = next++;
+        // the few best greedy and bisection trees at this threshold ...
+        std::vector<std::pair<double, Tree>> top;
+        auto keep = [&](const Tree &t, double time) {
+            if (top.size() < 3 || time < top.back().first) {
+                top.emplace_back(time, t);
+                std::sort(top.begin(), top.end(), [](const auto &x, const auto &y) { return x.first < y.first; });
+                if (top.size() > 3) top.pop_back();
+            }
         };
-        post(r.root);
-        Tree rebuilt;
-        if (tn_tree_from_ssa(net, pairs.data(), (int)pairs.size() / 2, rebuilt) == TN_OK) {
-            const TreeCost rc = tn_tree_cost(net, rebuilt);
-            if (rc.time < cost.time) { best = rebuilt; cost = rc; }
+        {
+            Tree tg;
+            TreeCost cg;
+            tn_greedy_tree(net, seed + 131 * (q + 1), n, tg, cg);
+            keep(tg, cg.time);
+        }
+        // (networks large enough for the greedy to go wrong also get bisection trials)
+        if (net.leaves.size() >= 48)
+            for (int tr = 0; tr < n; tr++) {
+                double eps = std::uniform_real_distribution<double>(0.02, 0.6)(rng);
+                int cutoff = 4 + (int)(rng() % 24);
+                Tree tb;
+                tn_bisect_tree(net, rng(), eps, cutoff, tb);
+                keep(tb, tn_tree_cost(net, tb).time);
+            }
+        // ... each improved locally (optimal orders of its small subtrees), then compared
+        for (auto &cand : top) {
+            Tree tq = cand.second;
+            TreeCost cq = tn_tree_cost(net, tq);
+            if (tq.nodes.size() >= 4) {
+                Tree r;
+                if (reconfigured(net, tq, r)) {
+                    const TreeCost cr = tn_tree_cost(net, r);
+                    if (cr.time < cq.time) { tq = r; cq = cr; }
+                }
+            }
+            if (!have || cq.time < cost.time) { best = tq; cost = cq; best_q = q; have = true; }
         }
     }
+    net.q_max = best_q;
 }
 
 // Slice network index `id` in a tree: it leaves every tensor, and every tensor above a
