@@ -112,15 +112,19 @@ def test_alg2_matches_oracle(grid, f):
     assert got == ref
 
 
-@pytest.mark.parametrize("cap", [24, 20])
+@pytest.mark.parametrize("cap", [20, 17])
 def test_width_slicing_caps_every_tensor(cap):
-    """max_log2_tensor slices legs until no tensor of one slice exceeds 2^cap elements."""
+    """max_log2_tensor slices legs until no tensor of one slice exceeds 2^cap elements
+    (and slices nothing when the unsliced plan already fits)."""
     circ = cg.sycamore_grid(4, 6, 12, seed=3)
     C = pkg.circuit_load(circ.serialize())
-    info, steps, sliced = pkg.tn.plan_host(C, cg.default_open_qubits(4, 6, 6), log2_batches=8, order_trials=16,
+    openq = cg.default_open_qubits(4, 6, 6)
+    free, _, _ = pkg.tn.plan_host(C, openq, log2_batches=8, order_trials=16, precision=pkg.tn.PREC_BF16X2)
+    info, steps, sliced = pkg.tn.plan_host(C, openq, log2_batches=8, order_trials=16,
                                            max_log2_tensor=cap, precision=pkg.tn.PREC_BF16X2)
     assert info["log2_max_tensor"] <= cap
-    assert info["n_sliced"] == len(sliced) >= 1
+    assert info["n_sliced"] == len(sliced)
+    assert (len(sliced) >= 1) == (free["log2_max_tensor"] > cap)
     cnt = oracle.two_qubit_counts(circ)
     for q, s in sliced:
         assert 1 <= s < cnt[q]
