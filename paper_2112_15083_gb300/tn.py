@@ -394,7 +394,7 @@ class Plan:
 
 
 def plan_host(circuit: Circuit, open_qubits, sliced=None, order=None, log2_batches=8, order_seed=0,
-              order_trials=64, n_auto_sliced=0, precision=PREC_C64, max_log2_tensor=0):
+              order_trials=64, n_auto_sliced=0, precision=PREC_C64, max_log2_tensor=0, hbm_budget_bytes=0.0):
     """Host-only planning (no GPU): (info dict, steps array (n_steps, 7), sliced edges).
     Step row: batch, m, n, k bits, log2 versions of C, A, B."""
     L = lib()
@@ -406,6 +406,8 @@ def plan_host(circuit: Circuit, open_qubits, sliced=None, order=None, log2_batch
     o.order_trials = order_trials
     o.n_auto_sliced = n_auto_sliced
     o.max_log2_tensor = max_log2_tensor
+    if hbm_budget_bytes:
+        o.hbm_budget_bytes = hbm_budget_bytes
     openq = np.ascontiguousarray(np.asarray(open_qubits, dtype=np.int32))
     if sliced is not None:
         arr = (Edge * max(1, len(sliced)))(*[Edge(int(q), int(s)) for (q, s) in sliced])
