@@ -542,13 +542,29 @@ StepEst step_estimate(const Network &net, const Node &a, const Node &b, const No
     double gt = 0;
     if (ga) gt += 2 * sa / bw + launch;
     if (gb) gt += 2 * sb / bw + launch;
-    // FFMA kernels lose most of their rate when one side of the product is short
-    // (measured: ~7 TFLOP/s at 16 x 32 outputs per batch, ~1 TFLOP/s at 4 x 16)
+    // the launch's GEMM dims: version bits are layout bits, batch dims when both operands
+    // carry them, rows or columns when one does
     const Bits &C = c.idx;
-    const int nm = (A & C).andnot(B).count(), nn = (B & C).andnot(A).count(), nk = (A & B).andnot(C).count();
+    const int vab = __builtin_popcountll(a.dep & b.dep);
+    const int nb = (A & B & C).count() + vab;
+    const int nm = (A & C).andnot(B).count() + __builtin_popcountll(a.dep) - vab;
+    const int nn = (B & C).andnot(A).count() + __builtin_popcountll(b.dep) - vab;
+    const int nk = (A & B).andnot(C).count();
     const int lo = std::min(nm, nn), hi = std::max(nm, nn);
-    double rate = lo >= 6 ? flop_rate : hi >= 7 ? flop_rate / 2 : lo >= 4 ? flop_rate / 4 : flop_rate / 16;
-    if (net.tc_flop_rate > 0 && tn_tc_shape(hi, lo, nk)) rate = net.tc_flop_rate * (lo >= 6 ? 1.0 : 0.5);
+    // FFMA kernels lose most of their rate when one side of the product is short
+    // (measured: ~7 TFLOP/s at 16 x 32 outputs per batch, ~5 at 4 x 32, ~1 at 4 x 16)
+    double rate = lo >= 6   ? flop_rate
+                  : hi >= 7 ? flop_rate / 2
+                  : lo >= 4 ? flop_rate / 4
+                  : hi >= 5 ? flop_rate / 6
+                            : flop_rate / 16;
+    if (net.tc_flop_rate > 0 && tn_tc_shape(hi, lo, nk)) {
+        rate = net.tc_flop_rate * (lo >= 6 ? 1.0 : 0.5);
+        // a batch of products of one or two output tiles each pays the tile's pipeline
+        // fill and epilogue per few MMAs (measured 55-90 TFLOP/s for 2^17-2^18 batches of
+        // 128-256 x 32 outputs)
+        if (nb > 0 && nm + nn <= 14) rate = net.tc_flop_rate * 0.15;
+    }
     StepEst e;
     e.flops = fl;
     e.bytes = by + (ga ? 2 * sa : 0) + (gb ? 2 * sb : 0);
