@@ -58,7 +58,7 @@ def parse():
     ap.add_argument("--log2-batches", type=int, default=None, help="batches per step = 2^this (default: the workload's)")
     ap.add_argument("--autotune", type=int, default=1, help="kernel autotuning (1) or the fixed shape rules (0)")
     ap.add_argument("--serve", action="store_true", help="serving run (Poisson request stream) instead of the step bench")
-    ap.add_argument("--config4-sample", action="store_true",
+    ap.add_argument("--grid5x8-sample", action="store_true",
                     help="bounded sample of the 40-qubit 5x8 / 16-cycle configuration (time per slice, extrapolated)")
     ap.add_argument("--serve-window", type=float, default=60.0, help="seconds of arrivals")
     ap.add_argument("--serve-rate", type=float, default=4.0, help="requests per second")
@@ -479,7 +479,7 @@ def run_serve(args):
     print(json.dumps(line), flush=True)
 
 
-def run_config4(args):
+def run_grid5x8_sample(args):
     """Bounded sample of the 40-qubit configuration (5x8 grid, 16 cycles, 1/64 of the
     slices retained, 100k samples): the plan slices legs until one slice's tensors fit
     2^30 elements, Alg. 1 selects the retained slices, and the first retained slices are
@@ -508,7 +508,7 @@ def run_config4(args):
         del plan
     plan_s = time.perf_counter() - t
     info = plan.info()
-    line = {"metric": "config 4 bounded sample: seconds per retained slice per batch group (shared part amortised)",
+    line = {"metric": "40-qubit bounded sample: seconds per retained slice per batch group (shared part amortised)",
             "unit": "s",
             "data": "synthetic", "n_gpus": 1,
             "config": {"workload": "grid5x8_m16: 40-qubit 5x8 Sycamore-style ABCD circuit, 16 cycles, seed 0; "
@@ -574,7 +574,7 @@ if __name__ == "__main__":
         run_reference(a)
     elif a.serve:
         run_serve(a)
-    elif a.config4_sample:
-        run_config4(a)
+    elif a.grid5x8_sample:
+        run_grid5x8_sample(a)
     else:
         run_ours(a)

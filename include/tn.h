@@ -44,7 +44,8 @@ extern "C" {
 #define TN_EDEVICE (-4)      /* CUDA error (no device, launch failure, ...) */
 #define TN_EUNSUPPORTED (-5) /* valid request outside what libtn implements */
 
-/* Precision of the pairwise contractions (north-star "split precision"). */
+/* Precision of the pairwise contractions: complex64, or each operand split into a hi and a
+   lo part of a narrow type whose products are summed in FP32 (hi*hi + hi*lo + lo*hi). */
 #define TN_PREC_C64 0    /* complex64 operands, FP32 FFMA accumulation */
 #define TN_PREC_BF16X2 1 /* hi+lo bf16 split operands on tcgen05, FP32 accumulation */
 #define TN_PREC_FP16X2 2 /* hi+lo fp16 split operands (scaled) on tcgen05, FP32 accumulation */

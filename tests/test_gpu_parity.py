@@ -230,8 +230,8 @@ def test_split_haar_batches_and_subsets(seed, prec):
 
 
 def test_28q_precision_report(grid28):
-    """Config 3: the same 28-qubit workload in complex64, bf16 x2 and fp16 x2 against the
-    FP64 oracle: per-amplitude error (max and RMS, relative to the RMS amplitude),
+    """The 28-qubit 4x7, 14-cycle workload at 256 batches in complex64, bf16 x2 and fp16 x2
+    against the FP64 oracle: per-amplitude error (max and RMS, relative to the RMS amplitude),
     relative L2 and the linear-XEB deviation of the computed distribution."""
     P = pkg()
     circ, psi = grid28
