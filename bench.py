@@ -57,6 +57,8 @@ def parse():
     ap.add_argument("--workload", default="grid4x7_m14", choices=sorted(WORKLOADS))
     ap.add_argument("--log2-batches", type=int, default=None, help="batches per step = 2^this (default: the workload's)")
     ap.add_argument("--autotune", type=int, default=1, help="kernel autotuning (1) or the fixed shape rules (0)")
+    ap.add_argument("--fuse-root", type=int, default=0,
+                    help="1: run a row-kernel root step fused with the FP64 slice sum (tn_plan_opts.fuse_root_sum)")
     ap.add_argument("--serve", action="store_true", help="serving run (Poisson request stream) instead of the step bench")
     ap.add_argument("--grid5x8-sample", action="store_true",
                     help="bounded sample of the 40-qubit 5x8 / 16-cycle configuration (time per slice, extrapolated)")
@@ -202,7 +204,7 @@ def workload_config(args):
                             1 << log2_batches(args)),
             "qubits": q, "cycles": w["cycles"], "sliced_legs": w["n_sliced"], "batches_per_step": 1 << log2_batches(args),
             "batch_size": 64, "fidelity_target": args.fidelity, "alpha": 2.0, "order_trials": args.trials,
-            "precision": getattr(args, "precision", "c64"),
+            "precision": getattr(args, "precision", "c64"), "fuse_root_sum": bool(getattr(args, "fuse_root", 0)),
             "l2": "flushed between timed steps; dominant operands exceed L2"}
 
 
@@ -226,7 +228,8 @@ def run_ours(args):
     C = P.circuit_load(circ.serialize())
     prec = {"c64": P.tn.PREC_C64, "bf16x2": P.tn.PREC_BF16X2}[args.precision]
     plan = P.plan(C, openq, n_auto_sliced=w["n_sliced"], log2_batches=log2_batches(args), order_trials=args.trials,
-                  order_seed=0, hbm_budget_bytes=200e9, precision=prec, autotune=args.autotune)
+                  order_seed=0, hbm_budget_bytes=200e9, precision=prec, autotune=args.autotune,
+                  fuse_root_sum=bool(args.fuse_root))
     info = plan.info()
     slices, F = plan.select(args.fidelity)
     T = 1 << log2_batches(args)
@@ -273,16 +276,19 @@ def run_ours(args):
     accepted = int(sum(int(a.sum().item()) for a in acc))
     tot_ms_max, accepted_all = replicas.reduce_run(tot_ms, accepted, device=dev)
     value = accepted_all / (tot_ms_max / 1e3)
-    # the last trace entry is the FP64 slice sum (kernel 2); the rest are contraction steps
-    ssum = [s for s in trace if s["kernel"] == 2]
-    trace = [s for s in trace if s["kernel"] != 2]
+    # the last trace entry is the FP64 slice sum (kernel 2, or 3 when it runs fused with the
+    # root step, whose own entry then has no launches); the rest are contraction steps
+    ssum = [s for s in trace if s["kernel"] in (2, 3)]
+    trace = [s for s in trace if s["kernel"] not in (2, 3)]
     flops_step = sum(s["flops_per_launch"] for s in trace)
+    trace = [s for s in trace if s["launches"] > 0]
     slice_sum = None
     if ssum and ssum[0]["launches"]:
         s0 = ssum[0]
         ms1 = s0["ms"] / s0["launches"]
         slice_sum = {"ms": round(ms1, 3), "fp64_gflops": round(s0["flops_per_launch"] / (ms1 / 1e3) / 1e9, 1),
-                     "gbs": round(s0["bytes_per_launch"] / (ms1 / 1e3) / 1e9, 1)}
+                     "gbs": round(s0["bytes_per_launch"] / (ms1 / 1e3) / 1e9, 1),
+                     "fused_root_step": s0["kernel"] == 3}
 
     # dominant kernel from the live per-step events
     dom = max(trace, key=lambda s: s["ms"])

@@ -87,6 +87,11 @@ typedef struct {
                                 (i + k - 2) mod (its variant count), so that tests can run
                                 every variant.  All variants accumulate each output over k
                                 in the same order. */
+    int32_t fuse_root_sum;   /* 1: when the root step runs the row kernel, run it fused
+                                with the FP64 slice sum (Sec. I.C step 1) in one launch
+                                whose output is bit-identical to the two launches, without
+                                writing the root's per-slice values to memory.  0
+                                (default): separate launches. */
     void *stream;            /* cudaStream_t; NULL = legacy default stream */
     tn_alloc_fn alloc;       /* optional device allocator */
     tn_free_fn free;
@@ -276,7 +281,10 @@ typedef struct {
     int32_t nbat, nm, nn, nk;
     int64_t nver;
     int32_t kernel; /* 0: row kernel, 1: staged small products, 2: FP64 slice sum,
-                       9128: tensor-core kernel, TM*1000+TN: FFMA tile kernel */
+                       3: the root step fused with the FP64 slice sum (the root step's
+                       own entry then counts no launches), 9128 / 9064 / 9032:
+                       tensor-core kernel with 128- / 64- / 32-column tiles,
+                       TM*1000+TN: FFMA tile kernel */
     int32_t gathers; /* batch-gather launches that precede the step (0 or 1) */
 } tn_step_trace;
 int tn_trace_enable(tn_plan_h p, int32_t on);

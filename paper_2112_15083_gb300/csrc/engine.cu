@@ -130,6 +130,7 @@ struct CNet {
     const uint64_t *cur_closed = nullptr;  // batch patterns of the execution being issued
     int autotune = 1;          // 1: time the applicable variants of unseen step shapes;
                                // 0: fixed shape rules; k >= 2: variant (step + k - 2) mod count
+    bool fuse_root = false;    // run a row-kernel root step fused with the slice sum
     DBuf err;                  // device error word of the bounded waits
     int *d_err = nullptr;
     // CUDA graphs of one execution (index: stem reuse off / on), valid for the current
@@ -824,11 +825,11 @@ int launch_tc(CNet &cn, const Step &s, size_t si, const tnk::GemmParams &p, cuda
     return TN_OK;
 }
 
-template <typename T>
-int launch_variant(CNet &cn, const Step &s, cudaStream_t st, int var) {
+
+// The launch parameters every kernel variant of step s starts from.
+int step_params(const CNet &cn, const Step &s, tnk::GemmParams &p) {
     const CallPlan &cp = cn.cp;
     const auto &nodes = cn.tree.nodes;
-    tnk::GemmParams p;
     std::memset(&p, 0, sizeof(p));
     const void *const *tab = static_cast<const void *const *>(cn.tables.p);
     p.ptrA = tab + cp.tab_off[&s - cn.steps.data()];
@@ -844,9 +845,36 @@ int launch_variant(CNet &cn, const Step &s, cudaStream_t st, int var) {
     for (int i = 0; i < s.nbat; i++) p.pos_bat[i] = s.pos_bat[i];
     for (int i = 0; i < s.nm; i++) p.pos_m[i] = s.pos_m[i];
     for (int i = 0; i < s.nn; i++) p.pos_n[i] = s.pos_n[i];
-    const size_t si = &s - cn.steps.data();
     p.out_fmt = cn.fmt[s.c];
     p.out_scale = cn.scale[s.c] / (cn.scale[s.a] * cn.scale[s.b]);
+    return TN_OK;
+}
+
+// The row kernel's roles: one thread per row of the larger side, the small side in
+// registers (C = A B^T is symmetric in the operand roles); gathered operands read in
+// place when possible.
+void row_roles(const CNet &cn, const Step &s, tnk::GemmParams &p) {
+    const size_t si = &s - cn.steps.data();
+    if (row_fuses(cn, si) && cn.cur_closed) {
+        const auto *gd = static_cast<const tnk::GatherDesc *>(cn.gdescs.p) + cn.cp.gd_off[si];
+        p.gA = s.gat[0] ? gd : nullptr;
+        p.gB = s.gat[1] ? gd + (s.gat[0] ? 1 : 0) : nullptr;
+        p.closed_bits = cn.cur_closed;
+    }
+    if (s.nn > s.nm) {
+        std::swap(p.ptrA, p.ptrB);
+        std::swap(p.gA, p.gB);
+        std::swap(p.lm, p.ln);
+        for (int i = 0; i < tnk::kMaxBits; i++) std::swap(p.pos_m[i], p.pos_n[i]);
+        p.swapped = 1;
+    }
+}
+
+template <typename T>
+int launch_variant(CNet &cn, const Step &s, cudaStream_t st, int var) {
+    tnk::GemmParams p;
+    RC(step_params(cn, s, p));
+    const size_t si = &s - cn.steps.data();
     if (cn.trace) cn.tr_kernel[si] = var;
     if (var == kVarTc128 || var == kVarTc64 || var == kVarTc32) {
         if constexpr (sizeof(T) == sizeof(float2)) {
@@ -879,21 +907,7 @@ int launch_variant(CNet &cn, const Step &s, cudaStream_t st, int var) {
         const size_t smem = (size_t)(per << lg) * sizeof(T);
         tnk::cgemm_small<T><<<(unsigned)blocks, 256, smem, st>>>(p, sm);
     } else if (var == kVarRow) {
-        // one thread per row of the larger side, the small side in registers (C = A B^T
-        // is symmetric in the operand roles); gathered operands read in place when possible
-        if (row_fuses(cn, si) && cn.cur_closed) {
-            const auto *gd = static_cast<const tnk::GatherDesc *>(cn.gdescs.p) + cn.cp.gd_off[si];
-            p.gA = s.gat[0] ? gd : nullptr;
-            p.gB = s.gat[1] ? gd + (s.gat[0] ? 1 : 0) : nullptr;
-            p.closed_bits = cn.cur_closed;
-        }
-        if (s.nn > s.nm) {
-            std::swap(p.ptrA, p.ptrB);
-            std::swap(p.gA, p.gB);
-            std::swap(p.lm, p.ln);
-            for (int i = 0; i < tnk::kMaxBits; i++) std::swap(p.pos_m[i], p.pos_n[i]);
-            p.swapped = 1;
-        }
+        row_roles(cn, s, p);
         long long rows = p.nver << (p.lbat + p.lm);
         // grid-stride: at most 16 resident blocks' worth per SM, each thread several rows
         unsigned blocks = (unsigned)std::min<long long>((rows + 255) / 256, 16LL * num_sms());
@@ -980,11 +994,80 @@ int launch_slice_sum(CNet &cn, double2 *out, cudaStream_t st) {
     return TN_OK;
 }
 
+// The root step's index when it runs fused with the slice sum (-1: not fused).  Fusion
+// needs the row kernel on a root stored as plain complex values, batch, row and column
+// bits that cover the root layout once each, and free patterns that fit the fused
+// kernel's byte tables; it is off while FP16 scales are calibrated (every node's maximum
+// is recorded from its stored values).
+long long fused_root_step(const CNet &cn) {
+    if (!cn.fuse_root || cn.calibrating || cn.steps.empty() || !cn.cp.valid) return -1;
+    const int root = cn.tree.root;
+    const size_t si = cn.steps.size() - 1;
+    const Step &s = cn.steps[si];
+    if (s.c != root) return -1;
+    const int var = si < cn.variant.size() && cn.variant[si] >= 0 ? cn.variant[si] : default_variant(cn, si);
+    if (var != kVarRow || cn.fmt[root] != tnk::OUT_C64) return -1;
+    const int nout = (int)cn.net.out_layout.size();
+    const int nfree = (int)cn.tree.nodes[root].layout.size() - nout;
+    if (nfree < 0 || nfree > 8 * tnk::kRootTabBytes || cn.cp.nver[root] != cn.cp.root_nver) return -1;
+    if (s.nbat + s.nm + s.nn != nout + nfree || nout + nfree > tnk::kMaxBits) return -1;
+    uint64_t seen = 0;
+    auto mark = [&](const int8_t *pos, int n) {
+        for (int i = 0; i < n; i++) {
+            if (pos[i] < 0 || pos[i] >= nout + nfree || ((seen >> pos[i]) & 1)) return false;
+            seen |= 1ull << pos[i];
+        }
+        return true;
+    };
+    if (!mark(s.pos_bat, s.nbat) || !mark(s.pos_m, s.nm) || !mark(s.pos_n, s.nn)) return -1;
+    return (long long)si;
+}
+
+// The root step (row kernel) and the FP64 slice sum in one launch: bit-identical to the
+// two launched one after the other, without the root's values passing through memory.
+int launch_root_slice_sum(CNet &cn, size_t si, double2 *out, cudaStream_t st) {
+    const int root = cn.tree.root;
+    const int nout = (int)cn.net.out_layout.size();
+    const int nfree = (int)cn.tree.nodes[root].layout.size() - nout;
+    tnk::GemmParams p;
+    RC(step_params(cn, cn.steps[si], p));
+    row_roles(cn, cn.steps[si], p);
+    const size_t ss = cn.steps.size();
+    if (cn.trace) {
+        if (cn.ev_pending[ss]) {
+            float ms = 0;
+            CK(cudaEventSynchronize(cn.ev[2 * ss + 1]));
+            CK(cudaEventElapsedTime(&ms, cn.ev[2 * ss], cn.ev[2 * ss + 1]));
+            cn.tr_ms[ss] += ms;
+            cn.tr_launches[ss]++;
+            cn.ev_pending[ss] = 0;
+        }
+        CK(cudaEventRecord(cn.ev[2 * ss], st));
+    }
+    const unsigned blocks = (unsigned)(((1LL << nout) + 255) / 256);
+    if (cn.elem == 8) tnk::root_slice_sum<float2><<<blocks, 256, 0, st>>>(p, nfree, nout, out);
+    else tnk::root_slice_sum<double2><<<blocks, 256, 0, st>>>(p, nfree, nout, out);
+    CK(cudaGetLastError());
+    if (cn.trace) {
+        CK(cudaEventRecord(cn.ev[2 * ss + 1], st));
+        cn.ev_pending[ss] = 1;
+        cn.tr_kernel[ss] = 3;
+    }
+    return TN_OK;
+}
+
 // One execution of a compiled network: batch gathers, steps, FP64 slice sum into out.
 int execute(CNet &cn, const uint64_t *d_closed, bool skip_beta_free, double2 *out, cudaStream_t st) {
+    const long long fused = fused_root_step(cn);
     for (const Step &s : cn.steps) {
         if (skip_beta_free && !cn.tree.nodes[s.c].beta) continue;
         const size_t si = &s - cn.steps.data();
+        if ((long long)si == fused) {
+            // its operands' gathers still run here unless the row kernel reads them in place
+            cn.cur_closed = d_closed;
+            if (!(d_closed && row_fuses(cn, si))) RC(launch_gathers(cn, si, d_closed, st));
+            continue;
+        }
         if (cn.trace) {
             if (cn.ev_pending[si]) {  // fold the previous measurement in before reusing the events
                 float ms = 0;
@@ -1014,6 +1097,10 @@ int execute(CNet &cn, const uint64_t *d_closed, bool skip_beta_free, double2 *ou
             CK(cudaEventRecord(cn.ev[2 * si + 1], st));
             cn.ev_pending[si] = 1;
         }
+    }
+    if (fused >= 0) {
+        cn.cur_closed = d_closed;
+        return launch_root_slice_sum(cn, (size_t)fused, out, st);
     }
     return launch_slice_sum(cn, out, st);
 }
@@ -1280,6 +1367,7 @@ void tn_plan_opts_default(tn_plan_opts *o) {
     o->hbm_budget_bytes = 64.0 * (1ull << 30);
     o->max_norm_flops = 2e15;
     o->autotune = 1;
+    o->fuse_root_sum = 0;
 }
 
 int tn_circuit_load(const void *buf, size_t len, tn_circuit_h *out) {
@@ -1342,6 +1430,7 @@ int tn_plan(tn_circuit_h c, const int32_t *order, int32_t n_order, const tn_edge
     p->amp.compiled = true;
     p->amp.prec = o.precision;
     p->amp.autotune = o.autotune;
+    p->amp.fuse_root = o.fuse_root_sum != 0;
     assign_formats(p->amp);
     rc = setup_leaves(p->mem, p->amp);
     if (rc) return fail(rc);

@@ -9,7 +9,8 @@
 //  * materialize: writes leaf tensors in the layout their consumer reads, fixing the
 //    sliced legs (one copy per slice value) and binding closed output legs to the
 //    batch pattern (the batch-indexed selector <b_B|).
-//  * slice_sum: FP64 sum over the slice set in slice order (Sec. I.C step 1).
+//  * slice_sum: FP64 sum over the slice set in slice order (Sec. I.C step 1);
+//    root_slice_sum: the same sum fused with a root step that runs the row kernel.
 //  * draw / sampler: Philox4x32-10 draws and the modified frugal rejection step
 //    (Sec. II.A), one warp per batch of 64.
 #pragma once
@@ -488,6 +489,106 @@ __global__ void slice_sum(const void *const *ptr, long long nver, int nfree, int
         }
         for (; f < nf; f++) {
             const T x = r[f << nout];
+            re = __dadd_rn(re, slice_widen(x.x));
+            im = __dadd_rn(im, slice_widen(x.y));
+        }
+    }
+    out[e] = make_double2(re, im);
+}
+
+// ---------------------------------------------------------------- root product + slice sum
+
+// The batch, row and column bits of C position pos under the row-kernel parameters p
+// (pos_* give each bit's C position; positions no bit maps to contribute nothing).
+__device__ __forceinline__ void root_split(const GemmParams &p, long long pos, long long &bat, long long &m, int &n) {
+    bat = 0;
+    m = 0;
+    n = 0;
+    for (int i = 0; i < p.lbat; i++) bat |= ((pos >> p.pos_bat[i]) & 1LL) << i;
+    for (int i = 0; i < p.lm; i++) m |= ((pos >> p.pos_m[i]) & 1LL) << i;
+    for (int i = 0; i < p.ln; i++) n |= (int)((pos >> p.pos_n[i]) & 1LL) << i;
+}
+
+// The value cgemm_row_one stores for output (v, bat, m, n), before the store: the same
+// operand rows (gathered ones read in place), k order and multiply-add operand order.
+template <typename T>
+__device__ __forceinline__ T root_value(const GemmParams &p, long long v, long long bat, long long m, int n) {
+    const T *A, *B;
+    if (p.gA) {
+        const long long e = ((bat << p.lm) | m) << p.lk;
+        A = reinterpret_cast<const T *>(p.gA->src) + gather_src_warp(*p.gA, e, p.gA->pos_beta[p.gA->lb - 1], p.closed_bits);
+    } else {
+        A = static_cast<const T *>(p.ptrA[v]) + (((bat << p.lm) | m) << p.lk);
+    }
+    if (p.gB) {
+        const long long e = bat << (p.ln + p.lk);
+        B = reinterpret_cast<const T *>(p.gB->src) + gather_src_warp(*p.gB, e, p.gB->pos_beta[p.gB->lb - 1], p.closed_bits);
+    } else {
+        B = static_cast<const T *>(p.ptrB[v]) + (bat << (p.ln + p.lk));
+    }
+    B += (long long)n << p.lk;
+    const int K = 1 << p.lk;
+    T acc = czero<T>();
+    if (p.swapped) {
+        for (int k = 0; k < K; k++) acc = cfma(__ldg(&B[k]), A[k], acc);
+    } else {
+        for (int k = 0; k < K; k++) acc = cfma(A[k], __ldg(&B[k]), acc);
+    }
+    return acc;
+}
+
+// What store_c_t applies before storing: the output scale for complex64, nothing for
+// complex128.
+__device__ __forceinline__ float2 root_scaled(const GemmParams &p, float2 x) {
+    x.x *= p.out_scale;
+    x.y *= p.out_scale;
+    return x;
+}
+__device__ __forceinline__ double2 root_scaled(const GemmParams &, double2 x) { return x; }
+
+constexpr int kRootTabBytes = 3;  // free patterns of up to 24 bits
+
+// The root step fused with the slice sum: out[e] = sum over explicit root versions v (in
+// order) and free patterns f (ascending) of the root product's value at C position
+// (f << nout) | e, p being the root step's row-kernel parameters.  Each value is formed
+// as the row kernel forms it and widened and added in FP64 in slice_sum's order, so out is
+// bit-identical to the row kernel followed by slice_sum, and the root's 2^(nout + nfree)
+// values never pass through memory.  The host checks that p's batch, row and column bits
+// cover the positions [0, nout + nfree) once each, so every (bat, m, n) below is in range.
+template <typename T>
+__global__ void __launch_bounds__(256) root_slice_sum(GemmParams p, int nfree, int nout, double2 *out) {
+    // byte tables: t*[j][b] are the batch, row and column bits of position (b << 8j) << nout
+    __shared__ long long tbat[kRootTabBytes][256], tm[kRootTabBytes][256];
+    __shared__ int tn[kRootTabBytes][256];
+    const int nbytes = (nfree + 7) >> 3;
+    for (int i = threadIdx.x; i < nbytes * 256; i += blockDim.x) {
+        const int j = i >> 8;
+        long long b, m;
+        int n;
+        root_split(p, ((long long)(i & 255) << (8 * j)) << nout, b, m, n);
+        tbat[j][i & 255] = b;
+        tm[j][i & 255] = m;
+        tn[j][i & 255] = n;
+    }
+    __syncthreads();
+    const long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= (1LL << nout)) return;
+    long long be, me;
+    int ne;
+    root_split(p, e, be, me, ne);
+    const long long nf = 1LL << nfree;
+    double re = 0.0, im = 0.0;
+    for (long long v = 0; v < p.nver; v++) {
+        for (long long f = 0; f < nf; f++) {
+            long long bat = be, m = me;
+            int n = ne;
+            for (int j = 0; j < nbytes; j++) {
+                const int b = (int)((f >> (8 * j)) & 255);
+                bat |= tbat[j][b];
+                m |= tm[j][b];
+                n |= tn[j][b];
+            }
+            const T x = root_scaled(p, root_value<T>(p, v, bat, m, n));
             re = __dadd_rn(re, slice_widen(x.x));
             im = __dadd_rn(im, slice_widen(x.y));
         }

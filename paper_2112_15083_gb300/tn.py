@@ -82,6 +82,7 @@ class PlanOpts(ctypes.Structure):
         ("hbm_budget_bytes", ctypes.c_double),
         ("max_norm_flops", ctypes.c_double),
         ("autotune", ctypes.c_int32),
+        ("fuse_root_sum", ctypes.c_int32),
         ("stream", ctypes.c_void_p),
         ("alloc", ALLOC_FN),
         ("free", FREE_FN),
@@ -235,7 +236,7 @@ class Plan:
     def __init__(self, circuit: Circuit, open_qubits, sliced=None, order=None, precision=PREC_C64,
                  log2_batches=8, order_seed=0, order_trials=64, n_auto_sliced=0,
                  hbm_budget_bytes=0.0, stream=None, use_torch_allocator=True, max_norm_flops=0.0,
-                 autotune=None, max_log2_tensor=0):
+                 autotune=None, max_log2_tensor=0, fuse_root_sum=False):
         L = lib()
         o = PlanOpts()
         L.tn_plan_opts_default(ctypes.byref(o))
@@ -251,6 +252,7 @@ class Plan:
             o.max_norm_flops = max_norm_flops
         if autotune is not None:
             o.autotune = int(autotune)
+        o.fuse_root_sum = int(bool(fuse_root_sum))
         o.stream = _stream_ptr(stream)
         self._alloc = None
         if use_torch_allocator:

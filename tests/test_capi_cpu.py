@@ -141,3 +141,34 @@ def test_order_search_is_deterministic():
     assert a[0] == b[0] and np.array_equal(a[1], b[1]) and a[2] == b[2]
     c = pkg.tn.plan_host(C, openq, n_auto_sliced=6, log2_batches=10, order_trials=16, order_seed=8)
     assert c[0]["n_steps"] == a[0]["n_steps"]
+
+
+def test_ctypes_mirrors_match_the_header(tmp_path):
+    """Every struct the binding mirrors has the header's size and field offsets (compiled
+    as C with the host compiler)."""
+    import ctypes
+    import shutil
+    import subprocess
+    from paper_2112_15083_gb300 import tn
+    cc = shutil.which("gcc") or shutil.which("cc")
+    if cc is None:
+        pytest.skip("no C compiler")
+    mirrors = {"tn_edge": tn.Edge, "tn_plan_opts": tn.PlanOpts, "tn_plan_info": tn.PlanInfo,
+               "tn_sample_stats": tn.SampleStats, "tn_step_trace": tn.StepTrace, "tn_server_opts": tn.ServerOpts,
+               "tn_request_info": tn.RequestInfo, "tn_server_stats": tn.ServerStats}
+    lines = ["#include <stddef.h>", "#include <stdio.h>", '#include "tn.h"', "int main(void) {"]
+    for cname, cls in mirrors.items():
+        lines.append('printf("%s size %%zu\\n", sizeof(%s));' % (cname, cname))
+        for f, _ in cls._fields_:
+            lines.append('printf("%s.%s %%zu\\n", offsetof(%s, %s));' % (cname, f, cname, f))
+    lines += ["return 0;", "}"]
+    src = tmp_path / "layout.c"
+    src.write_text("\n".join(lines) + "\n")
+    exe = tmp_path / "layout"
+    subprocess.run([cc, "-std=c11", "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)], check=True)
+    out = subprocess.run([str(exe)], capture_output=True, text=True, check=True).stdout
+    got = dict(line.rsplit(" ", 1) for line in out.splitlines())
+    for cname, cls in mirrors.items():
+        assert int(got[cname + " size"]) == ctypes.sizeof(cls), cname
+        for f, _ in cls._fields_:
+            assert int(got[cname + "." + f]) == getattr(cls, f).offset, (cname, f)
