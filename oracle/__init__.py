@@ -11,6 +11,7 @@ arXiv:2112.15083 (Kalachev, Panteleev, Zhou, Yung):
 * norms R[i] = ||psi_i||^2 = P(S-wires read i after C1) (Sec. I.A, Alg. 1);
 * SlicedVertexSelect (Alg. 2) and Slice selection (Alg. 1);
 * linear XEB (Eq. 1) and the modified frugal rejection sampler (Sec. II.A);
+* the XEB spoofing recipe (Sec. III, "Spoofing Linear XEB"; App. A);
 * the sampler's output law, variation distance and fidelity bound (Sec. II.B);
 * the expected rejection loss under Porter-Thomas statistics (Sec. II.C).
 
@@ -444,3 +445,37 @@ def paper_eps_bound(NA: int, NB: float, alpha: float) -> float:
     """The printed Eq. Eeps: N_B Gamma(N_A, alpha N_A)/Gamma(N_A)."""
     from scipy.special import gammaincc
     return float(NB * gammaincc(NA, alpha * NA))
+
+
+# -------------------------------------------------------------- XEB spoofing
+
+def spoof_batch_bits(N: int) -> int:
+    """Step 1 of the spoofing recipe (Sec. III, "Spoofing Linear XEB"): b = ceil(log2(10 N)),
+    the number of free outputs, so that the batch holds 2^b >= 10 N bitstrings."""
+    if N < 1:
+        raise ValueError("N must be positive")
+    b = 0
+    while (1 << b) < 10 * N:
+        b += 1
+    return b
+
+
+def spoof_select(p_approx: np.ndarray, N: int) -> np.ndarray:
+    """Step 4: the positions of the N largest approximate probabilities |psi'_i|^2 in the
+    batch, largest first; equal values go to the smaller position (the paper does not say)."""
+    p = np.asarray(p_approx, dtype=np.float64)
+    if not 0 <= N <= p.size:
+        raise ValueError("N outside [0, batch size]")
+    order = np.lexsort((np.arange(p.size), -p))  # by -p, then by position
+    return order[:N].astype(np.int64)
+
+
+def spoof_xeb(p_ideal: np.ndarray, n: int, selected) -> float:
+    """Eq. 1 over the selected strings: 2^n times the mean exact probability, minus 1."""
+    return xeb_of_samples(p_ideal, n, selected)
+
+
+def spoof_expected_xeb(f: float, r: float) -> float:
+    """Eq. spoof-xeb (App. A): for a Porter-Thomas batch computed at fidelity f, the N = r |B|
+    strings of largest approximate probability have E XEB = -f ln r, up to O(ln N / N)."""
+    return -f * math.log(r)
