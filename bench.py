@@ -306,7 +306,7 @@ def run_ours(args):
                     else "fallback 1.9 PFLOP/s",
                     "kernel": "tc_cgemm<%d,%d> split bf16 hi+lo %s" % (
                         dom["kernel"] - 9000, {9128: 3, 9064: 4, 9032: 5}[dom["kernel"]], shape)}
-    elif dom["kernel"] in (0, 1):
+    elif dom["kernel"] in (0, 1, 4):
         # short products (row kernel, staged small kernel): algorithmic bytes (operands
         # read + result written, complex64; gathered operands at their batch size)
         # against the measured copy bandwidth
@@ -314,7 +314,7 @@ def run_ours(args):
         peak = pk.get("hbm_gbs", 6800.0)
         roofline = {"bound": "hbm", "achieved": gbs, "peak": peak, "unit": "GB/s", "traffic": None, "frac": gbs / peak,
                     "peak_source": "measured HBM copy (MEASURED_PEAKS.json)" if "hbm_gbs" in pk else "fallback 6.8 TB/s",
-                    "kernel": "%s %s%s" % ("cgemm_row" if dom["kernel"] == 0 else "cgemm_small", shape,
+                    "kernel": "%s %s%s" % ({0: "cgemm_row", 1: "cgemm_small", 4: "cgemm_rowstage"}[dom["kernel"]], shape,
                                            " with batch gathers" if dom["gathers"] else "")}
     else:
         ffma_peak = 152 * 128 * 2 * 2.07e9 / 1e12
@@ -326,7 +326,7 @@ def run_ours(args):
     fam = {}
     for x in trace:
         k = x["kernel"]
-        name = ("tc_cgemm" if k >= 9000 else "cgemm_row" if k == 0 else "cgemm_small" if k == 1 else "cgemm_tile")
+        name = ("tc_cgemm" if k >= 9000 else {0: "cgemm_row", 1: "cgemm_small", 4: "cgemm_rowstage"}.get(k, "cgemm_tile"))
         fam[name] = fam.get(name, 0.0) + x["ms"] / max(1, x["launches"])
     roofline["kernel_family_ms_per_step"] = {k: round(v, 2) for k, v in sorted(fam.items(), key=lambda kv: -kv[1])}
     key = {9128: "tc_cgemm<128,3>", 0: "cgemm_row"}.get(dom["kernel"])

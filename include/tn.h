@@ -282,7 +282,8 @@ typedef struct {
     int64_t nver;
     int32_t kernel; /* 0: row kernel, 1: staged small products, 2: FP64 slice sum,
                        3: the root step fused with the FP64 slice sum (the root step's
-                       own entry then counts no launches), 9128 / 9064 / 9032:
+                       own entry then counts no launches), 4: row kernel with rows
+                       staged through shared memory, 9128 / 9064 / 9032:
                        tensor-core kernel with 128- / 64- / 32-column tiles,
                        TM*1000+TN: FFMA tile kernel */
     int32_t gathers; /* batch-gather launches that precede the step (0 or 1) */

@@ -717,7 +717,13 @@ int prepare_call(DevMem &mem, CNet &cn, const std::vector<uint64_t> &slices, dou
 
 // Kernel variants of a step (ids as in tn_step_trace.kernel): 0 row kernel, 1 staged
 // small products, TM*1000+TN FFMA tile, 9128 / 9064 tensor-core tile of 128 / 64 columns.
-constexpr int kVarRow = 0, kVarSmall = 1, kVarTc128 = 9128, kVarTc64 = 9064, kVarTc32 = 9032;
+constexpr int kVarRow = 0, kVarSmall = 1, kVarRowStage = 4, kVarTc128 = 9128, kVarTc64 = 9064, kVarTc32 = 9032;
+
+// Whether the staged row kernel can run step si: the row kernel's shapes with complex64
+// rows of 16 to 64 elements.  It is not among the autotuner's candidates yet.
+bool rowstage_fits(const CNet &cn, const Step &s) {
+    return cn.elem == 8 && std::min(s.nm, s.nn) <= 5 && s.nk >= 4 && s.nk <= 6;
+}
 constexpr int kTiles[7][2] = {{128, 64}, {64, 64}, {128, 32}, {64, 32}, {32, 32}, {128, 16}, {16, 16}};
 
 bool small_fits(const Step &s, size_t esz) {
@@ -906,6 +912,28 @@ int launch_variant(CNet &cn, const Step &s, cudaStream_t st, int var) {
         const long long blocks = p.nver << (s.nbat - lg);
         const size_t smem = (size_t)(per << lg) * sizeof(T);
         tnk::cgemm_small<T><<<(unsigned)blocks, 256, smem, st>>>(p, sm);
+    } else if (var == kVarRowStage) {
+        if (!rowstage_fits(cn, s)) { tn_set_error("staged row kernel: unsupported step shape"); return TN_EINVAL; }
+        if constexpr (sizeof(T) == sizeof(float2)) {
+            row_roles(cn, s, p);
+            const long long rows = p.nver << (p.lbat + p.lm);
+            const int per_block = 32 * tnk::kRowWarps;
+            const size_t smem = (size_t)per_block * (8 * (1 << p.lk) + tnk::kRowPad);
+            const unsigned blocks = (unsigned)std::min<long long>((rows + per_block - 1) / per_block, 3LL * num_sms());
+            auto go = [&](auto kern) -> int {
+                CK(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+                kern<<<blocks, per_block, smem, st>>>(p);
+                return TN_OK;
+            };
+            switch (p.ln) {
+                case 0: RC(go(tnk::cgemm_rowstage<1>)); break;
+                case 1: RC(go(tnk::cgemm_rowstage<2>)); break;
+                case 2: RC(go(tnk::cgemm_rowstage<4>)); break;
+                case 3: RC(go(tnk::cgemm_rowstage<8>)); break;
+                case 4: RC(go(tnk::cgemm_rowstage<16>)); break;
+                default: RC(go(tnk::cgemm_rowstage<32>)); break;
+            }
+        }
     } else if (var == kVarRow) {
         row_roles(cn, s, p);
         long long rows = p.nver << (p.lbat + p.lm);
@@ -1081,7 +1109,8 @@ int execute(CNet &cn, const uint64_t *d_closed, bool skip_beta_free, double2 *ou
         }
         cn.cur_closed = d_closed;
         const int var = si < cn.variant.size() && cn.variant[si] >= 0 ? cn.variant[si] : default_variant(cn, si);
-        if (!(var == kVarRow && d_closed && row_fuses(cn, si))) RC(launch_gathers(cn, si, d_closed, st));
+        const bool in_place = (var == kVarRow || var == kVarRowStage) && d_closed && row_fuses(cn, si);
+        if (!in_place) RC(launch_gathers(cn, si, d_closed, st));
         if (cn.elem == 8) RC(launch_step<float2>(cn, s, st));
         else RC(launch_step<double2>(cn, s, st));
         if (cn.calibrating) {

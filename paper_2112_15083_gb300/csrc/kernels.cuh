@@ -236,6 +236,91 @@ __global__ void __launch_bounds__(256) cgemm_row(GemmParams p) {
         cgemm_row_one<T, N>(p, row);
 }
 
+// The row kernel with coalesced row reads, for complex64 rows of 16 <= K <= 64: each warp
+// copies its 32 rows into shared memory (K/2 lanes per row, 16 bytes each, 64/K rows per
+// load instruction), then each lane forms its own row's N outputs exactly as cgemm_row_one
+// does (the same k order and multiply-add operand order), so the results are
+// bit-identical.  Rows sit kRowPad bytes apart beyond their length, which keeps the lanes'
+// 16-byte shared reads free of bank conflicts.
+constexpr int kRowWarps = 4;     // warps per block
+constexpr int kRowPad = 16;      // bytes between staged rows
+template <int N>
+__global__ void __launch_bounds__(32 * kRowWarps) cgemm_rowstage(GemmParams p) {
+    extern __shared__ __align__(16) unsigned char rowstage_smem[];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int K = 1 << p.lk;
+    const int rstride = 8 * K + kRowPad;  // bytes
+    unsigned char *stage = rowstage_smem + (size_t)warp * 32 * rstride;
+    const long long M = 1LL << p.lm;
+    const long long rows = p.nver << (p.lbat + p.lm);
+    const int lpr = K >> 1;         // lanes per row (16 bytes = two complex64 each)
+    const int rpi = 32 / lpr;       // rows per load instruction
+    for (long long r0 = ((long long)blockIdx.x * kRowWarps + warp) * 32; r0 < rows;
+         r0 += (long long)gridDim.x * kRowWarps * 32) {
+        // this lane's row and its operand bases
+        const long long row = r0 + lane;
+        const bool live = row < rows;
+        const long long m = row & (M - 1);
+        const long long bat = (row >> p.lm) & ((1LL << p.lbat) - 1);
+        const long long v = row >> (p.lm + p.lbat);
+        const float2 *A = nullptr, *B = nullptr;
+        if (live) {
+            if (p.gA) {
+                const long long e = ((bat << p.lm) | m) << p.lk;
+                A = reinterpret_cast<const float2 *>(p.gA->src) +
+                    gather_src_warp(*p.gA, e, p.gA->pos_beta[p.gA->lb - 1], p.closed_bits);
+            } else {
+                A = static_cast<const float2 *>(p.ptrA[v]) + (((bat << p.lm) | m) << p.lk);
+            }
+            if (p.gB) {
+                const long long e = bat << (p.ln + p.lk);
+                B = reinterpret_cast<const float2 *>(p.gB->src) +
+                    gather_src_warp(*p.gB, e, p.gB->pos_beta[p.gB->lb - 1], p.closed_bits);
+            } else {
+                B = static_cast<const float2 *>(p.ptrB[v]) + (bat << (p.ln + p.lk));
+            }
+        }
+        // stage the warp's rows: in instruction j, lane l copies chunk l % lpr of row
+        // j * rpi + l / lpr
+        const unsigned long long abase = reinterpret_cast<unsigned long long>(A);
+        for (int j = 0; j < 32; j += rpi) {
+            const int rr = j + lane / lpr;
+            const unsigned long long src = __shfl_sync(0xffffffffu, abase, rr);
+            if (r0 + rr < rows) {
+                const int c = lane % lpr;
+                const float4 x = *reinterpret_cast<const float4 *>(src + 16ull * c);
+                *reinterpret_cast<float4 *>(stage + (size_t)rr * rstride + 16 * c) = x;
+            }
+        }
+        __syncwarp();
+        if (live) {
+            const float2 *a = reinterpret_cast<const float2 *>(stage + (size_t)lane * rstride);
+            float2 acc[N];
+#pragma unroll
+            for (int n = 0; n < N; n++) acc[n] = czero<float2>();
+            for (int k = 0; k < K; k += 2) {
+                const float4 q = *reinterpret_cast<const float4 *>(a + k);
+                const float2 x0 = make_float2(q.x, q.y), x1 = make_float2(q.z, q.w);
+                if (p.swapped) {
+#pragma unroll
+                    for (int n = 0; n < N; n++) acc[n] = cfma(__ldg(&B[(n << p.lk) + k]), x0, acc[n]);
+#pragma unroll
+                    for (int n = 0; n < N; n++) acc[n] = cfma(__ldg(&B[(n << p.lk) + k + 1]), x1, acc[n]);
+                } else {
+#pragma unroll
+                    for (int n = 0; n < N; n++) acc[n] = cfma(x0, __ldg(&B[(n << p.lk) + k]), acc[n]);
+#pragma unroll
+                    for (int n = 0; n < N; n++) acc[n] = cfma(x1, __ldg(&B[(n << p.lk) + k + 1]), acc[n]);
+                }
+            }
+            const long long cb = scatter_bits(bat, p.pos_bat, p.lbat) + scatter_bits(m, p.pos_m, p.lm);
+#pragma unroll
+            for (int n = 0; n < N; n++) store_c_t<float2>(p, v, cb + scatter_bits(n, p.pos_n, p.ln), acc[n]);
+        }
+        __syncwarp();  // the stage is rewritten by the next iteration
+    }
+}
+
 // Batched small products (M, N <= 64, K <= 64): a block stages the operands of 2^lg
 // consecutive batches in shared memory and walks that chunk's outputs in the order of
 // their positions in C (local bit i = chunk bit kind[i] / idx[i]), so consecutive threads
