@@ -205,6 +205,8 @@ def workload_config(args):
             "qubits": q, "cycles": w["cycles"], "sliced_legs": w["n_sliced"], "batches_per_step": 1 << log2_batches(args),
             "batch_size": 64, "fidelity_target": args.fidelity, "alpha": 2.0, "order_trials": args.trials,
             "precision": getattr(args, "precision", "c64"), "fuse_root_sum": bool(getattr(args, "fuse_root", 0)),
+            "job": "the timed steps are the batch groups of one sampling job over one slice set: the first "
+                   "runs every contraction, the later ones reuse its batch-independent intermediates",
             "l2": "flushed between timed steps; dominant operands exceed L2"}
 
 
@@ -236,12 +238,15 @@ def run_ours(args):
     dev = torch.device("cuda", local)
     acc = [torch.empty(T, dtype=torch.uint8, device=dev) for _ in range(args.steps)]
     bits = [torch.empty(T, dtype=torch.int64, device=dev) for _ in range(args.steps)]
+    acc2 = [torch.empty(T, dtype=torch.uint8, device=dev) for _ in range(args.steps)]
+    bits2 = [torch.empty(T, dtype=torch.int64, device=dev) for _ in range(args.steps)]
     flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
     from paper_2112_15083_gb300 import replicas
     base_t = replicas.batch_t0(rank, 0, T)
     seed = args.seed
+    # warm-up: a full group, then groups that reuse its stem (both CUDA graphs captured)
     for i in range(args.warmup):
-        plan.sample_step(slices, F, seed, base_t + i * T, accept=acc[0], bits=bits[0])
+        plan.sample_step(slices, F, seed, base_t + i * T, reuse_stem=i > 0, accept=acc[0], bits=bits[0])
     torch.cuda.synchronize()
     clocks = Clocks(local)
     ev0 = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
@@ -250,38 +255,57 @@ def run_ours(args):
         torch.distributed.barrier()
     torch.cuda.synchronize()
     clocks.start()
-    # timed region: each step as deployed (one CUDA-graph replay of the contraction
-    # plus the draw and sampler launches), L2 flushed in between
+    # timed region: one sampling job of `steps` batch groups over one slice set, each group
+    # as deployed (one CUDA-graph replay of the contraction plus the draw and sampler
+    # launches), L2 flushed in between.  The job's first group runs every contraction; its
+    # later groups reuse the batch-independent intermediates (the stem) that the first
+    # left on the device (tn_sample_step reuse_stem), as tn_sample does for the groups of
+    # one call.  Warm-up leaves nothing the first timed group uses.
     for k in range(args.steps):
         flush.zero_()
         ev0[k].record()
-        plan.sample_step(slices, F, seed, base_t + (args.warmup + k) * T, accept=acc[k], bits=bits[k])
+        plan.sample_step(slices, F, seed, base_t + (args.warmup + k) * T, reuse_stem=k > 0, accept=acc[k], bits=bits[k])
+        ev1[k].record()
+    torch.cuda.synchronize()
+    if world > 1:
+        torch.distributed.barrier()
+    step_ms = [ev0[k].elapsed_time(ev1[k]) for k in range(args.steps)]
+    tot_ms = sum(step_ms)
+    # the same number of groups, each on its own (the stem recomputed in every group)
+    for k in range(args.steps):
+        flush.zero_()
+        ev0[k].record()
+        plan.sample_step(slices, F, seed, base_t + (args.warmup + args.steps + k) * T, accept=acc2[k], bits=bits2[k])
         ev1[k].record()
     torch.cuda.synchronize()
     if world > 1:
         torch.distributed.barrier()
     clk = clocks.stop()
-    step_ms = [ev0[k].elapsed_time(ev1[k]) for k in range(args.steps)]
-    tot_ms = sum(step_ms)
-    # traced region (same steps, CUDA events around every contraction launch): per-step
-    # device times for the roofline of the dominant kernel
+    solo_ms = sum(ev0[k].elapsed_time(ev1[k]) for k in range(args.steps))
+    # traced region (the job again, CUDA events around every contraction launch): per-launch
+    # device times for the roofline of the dominant kernel, and the job's launch counts
     plan.trace(True)
     acc_t = torch.empty(T, dtype=torch.uint8, device=dev)
     bits_t = torch.empty(T, dtype=torch.int64, device=dev)
     for k in range(args.steps):
         flush.zero_()
-        plan.sample_step(slices, F, seed, base_t + (args.warmup + k) * T, accept=acc_t, bits=bits_t)
+        plan.sample_step(slices, F, seed, base_t + (args.warmup + k) * T, reuse_stem=k > 0, accept=acc_t, bits=bits_t)
     trace = plan.trace_read()
     plan.trace(False)
     accepted = int(sum(int(a.sum().item()) for a in acc))
     tot_ms_max, accepted_all = replicas.reduce_run(tot_ms, accepted, device=dev)
     value = accepted_all / (tot_ms_max / 1e3)
+    accepted2 = int(sum(int(a.sum().item()) for a in acc2))
+    solo_ms_max, accepted2_all = replicas.reduce_run(solo_ms, accepted2, device=dev)
+    value_solo = accepted2_all / (solo_ms_max / 1e3)
     # the last trace entry is the FP64 slice sum (kernel 2, or 3 when it runs fused with the
     # root step, whose own entry then has no launches); the rest are contraction steps
     ssum = [s for s in trace if s["kernel"] in (2, 3)]
     trace = [s for s in trace if s["kernel"] not in (2, 3)]
-    flops_step = sum(s["flops_per_launch"] for s in trace)
+    # contraction FLOPs per group: a whole group's, and the job's average (the stem once)
+    flops_group = sum(s["flops_per_launch"] for s in trace)
     trace = [s for s in trace if s["launches"] > 0]
+    flops_step = sum(s["flops_per_launch"] * s["launches"] for s in trace) / args.steps
     slice_sum = None
     if ssum and ssum[0]["launches"]:
         s0 = ssum[0]
@@ -290,7 +314,7 @@ def run_ours(args):
                      "gbs": round(s0["bytes_per_launch"] / (ms1 / 1e3) / 1e9, 1),
                      "fused_root_step": s0["kernel"] == 3}
 
-    # dominant kernel from the live per-step events
+    # dominant kernel of the job (most device time) from the live per-launch events
     dom = max(trace, key=lambda s: s["ms"])
     dom_ms = dom["ms"] / max(1, dom["launches"])
     pk = peaks()
@@ -315,19 +339,19 @@ def run_ours(args):
         roofline = {"bound": "hbm", "achieved": gbs, "peak": peak, "unit": "GB/s", "traffic": None, "frac": gbs / peak,
                     "peak_source": "measured HBM copy (MEASURED_PEAKS.json)" if "hbm_gbs" in pk else "fallback 6.8 TB/s",
                     "kernel": "%s %s%s" % ({0: "cgemm_row", 1: "cgemm_small", 4: "cgemm_rowstage"}[dom["kernel"]], shape,
-                                           " with batch gathers" if dom["gathers"] else "")}
+                                           " after a batch-gather launch" if dom["gathers"] else "")}
     else:
         ffma_peak = 152 * 128 * 2 * 2.07e9 / 1e12
         roofline = {"bound": "alu", "achieved": alg, "peak": ffma_peak, "unit": "TFLOP/s", "traffic": None,
                     "frac": alg / ffma_peak, "peak_source": "derived: " + FFMA_PEAK_NOTE + " (FP32 FFMA, complex64 path)",
                     "kernel": "cgemm_tile<%d,%d> %s" % (dom["kernel"] // 1000, dom["kernel"] % 1000, shape)}
     roofline["share_of_step"] = dom["ms"] / max(1e-9, sum(s["ms"] for s in trace))
-    # time per kernel family in the traced steps
+    # device time per kernel family, averaged over the job's groups
     fam = {}
     for x in trace:
         k = x["kernel"]
         name = ("tc_cgemm" if k >= 9000 else {0: "cgemm_row", 1: "cgemm_small", 4: "cgemm_rowstage"}.get(k, "cgemm_tile"))
-        fam[name] = fam.get(name, 0.0) + x["ms"] / max(1, x["launches"])
+        fam[name] = fam.get(name, 0.0) + x["ms"] / args.steps
     roofline["kernel_family_ms_per_step"] = {k: round(v, 2) for k, v in sorted(fam.items(), key=lambda kv: -kv[1])}
     key = {9128: "tc_cgemm<128,3>", 0: "cgemm_row"}.get(dom["kernel"])
     rec = MEASURED_TRAFFIC.get((key, (dom["nbat"], dom["nm"], dom["nn"], dom["nk"]))) if key else None
@@ -342,28 +366,25 @@ def run_ours(args):
     for s in sorted(trace, key=lambda s: -s["ms"])[:6]:
         ms1 = s["ms"] / max(1, s["launches"])
         top_steps.append({"shape_bits": [s["nbat"], s["nm"], s["nn"], s["nk"]], "kernel": s["kernel"],
-                          "ms": round(ms1, 3), "tflops": round(s["flops_per_launch"] / (ms1 / 1e3) / 1e12, 2),
+                          "ms": round(ms1, 3), "launches_per_job": s["launches"],
+                          "tflops": round(s["flops_per_launch"] / (ms1 / 1e3) / 1e12, 2),
                           "gbs": round(s["bytes_per_launch"] / (ms1 / 1e3) / 1e9, 1)})
 
-    # end to end through the public API with host buffers (one tn_sample call per step)
+    # end to end through the public API with host buffers: the same job as one tn_sample
+    # call (selection of the slices included), about one group's expected samples
+    # (T (1 - eps) / alpha) per step
     e2e = None
     if rank == 0:
-        # a request of about one group's expected samples (T (1 - eps) / alpha), so that
-        # a call seldom needs a second, mostly unused group
-        n_per = int(0.47 * T)
+        n_job = int(0.47 * T) * args.steps
         torch.cuda.synchronize()
         t = time.perf_counter()
-        got = 0
-        groups = 0
-        for k in range(args.steps):
-            b, st = plan.sample(args.fidelity, n_per, seed=seed + 1 + k)
-            got += len(b)
-            groups += (st["steps"] + T - 1) // T
+        b, st = plan.sample(args.fidelity, n_job, seed=seed + 1)
         dt = time.perf_counter() - t
-        e2e = {"value": got / dt, "unit": "samples/s", "h2d_bytes_per_step": 0,
-               "d2h_bytes_per_step": int(groups * T * (1 + 8 + 8) / args.steps + n_per * 8),
-               "api": "tn_sample(host bitstrings), %d samples per call" % n_per,
-               "groups_per_call": round(groups / max(1, args.steps), 2)}
+        groups = (st["steps"] + T - 1) // T
+        e2e = {"value": len(b) / dt, "unit": "samples/s", "h2d_bytes_per_step": 0,
+               "d2h_bytes_per_step": int((groups * T * (1 + 8 + 8) + n_job * 8) / args.steps),
+               "api": "tn_sample(host bitstrings): one call for the job's %d samples" % n_job,
+               "groups": groups}
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -384,10 +405,14 @@ def run_ours(args):
                       if args.precision == "bf16x2" else "c64 (fp32 FFMA), fp64 slice sum/sampler"),
             "data": "synthetic", "config": workload_config(args),
             "fidelity": F, "contraction_tflops": flops_step * args.steps / (tot_ms / 1e3) / 1e12,
-            "flops_per_step": flops_step, "plan": info, "clocks": clk, "roofline": roofline,
+            "flops_per_step": flops_step, "flops_per_group_with_stem": flops_group,
+            "value_stem_each_step": value_solo, "ms_per_step_stem_each_step": solo_ms_max / args.steps,
+            "plan": info, "clocks": clk, "roofline": roofline,
             "cpu_baseline": cpu, "e2e": e2e, "top_steps": top_steps, "slice_sum": slice_sum,
-            # per step: contraction launches, batch gathers, slice sum, batch draws, sampler
-            "gpu_launches": args.steps * (len(trace) + sum(s["gathers"] for s in trace) + 3),
+            # the job's contraction launches, batch gathers and slice sums, plus a batch draw
+            # and a sampler launch per step
+            "gpu_launches": (sum(s["launches"] * (1 + s["gathers"]) for s in trace)
+                             + sum(s["launches"] for s in ssum) + 2 * args.steps),
         }
         print(json.dumps(line), flush=True)
     if world > 1:

@@ -286,7 +286,8 @@ typedef struct {
                        staged through shared memory, 9128 / 9064 / 9032:
                        tensor-core kernel with 128- / 64- / 32-column tiles,
                        TM*1000+TN: FFMA tile kernel */
-    int32_t gathers; /* batch-gather launches that precede the step (0 or 1) */
+    int32_t gathers; /* batch-gather launches that precede each launch of the step (0 or
+                        1; 0 when the row kernel reads gathered operands in place) */
 } tn_step_trace;
 int tn_trace_enable(tn_plan_h p, int32_t on);
 int tn_trace_read(tn_plan_h p, tn_step_trace *out, int32_t cap, int32_t *n_out);

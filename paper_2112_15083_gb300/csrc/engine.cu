@@ -1829,7 +1829,7 @@ int tn_trace_read(tn_plan_h p, tn_step_trace *out, int32_t cap, int32_t *n_out) 
         t.nver = cn.cp.valid ? cn.cp.root_nver : 1;
         t.flops_per_launch = 2.0 * nout * summed;
         t.bytes_per_launch = 8.0 * nout * summed + 16.0 * nout;
-        t.kernel = 2;
+        t.kernel = cn.tr_kernel.size() > (size_t)ns && cn.tr_kernel[ns] == 3 ? 3 : 2;
     }
     for (int si = 0; si < ns && si < cap && out; si++) {
         const Step &s = cn.steps[si];
@@ -1852,7 +1852,10 @@ int tn_trace_read(tn_plan_h p, tn_step_trace *out, int32_t cap, int32_t *n_out) 
         t.nn = s.nn;
         t.nk = s.nk;
         t.kernel = cn.tr_kernel[si];
-        t.gathers = cn.cp.valid && cn.cp.gd_off[si + 1] > cn.cp.gd_off[si] ? 1 : 0;
+        // a gather launch precedes the step unless the row kernels read the operands in place
+        const bool has = cn.cp.valid && cn.cp.gd_off[si + 1] > cn.cp.gd_off[si];
+        const bool in_place = (t.kernel == kVarRow || t.kernel == kVarRowStage) && row_fuses(cn, (size_t)si);
+        t.gathers = has && !in_place ? 1 : 0;
     }
     return TN_OK;
 }
