@@ -17,6 +17,7 @@
 
 #include <cudaTypedefs.h>
 
+#include "gather_tables.h"
 #include "kernels.cuh"
 #include "tc.cuh"
 #include "tn_internal.h"
@@ -670,24 +671,7 @@ int prepare_call(DevMem &mem, CNet &cn, const std::vector<uint64_t> &slices, dou
             tnk::GatherDesc &g = cp.gd[gi];
             uint64_t *rest = cp.gtab.data() + gi * W;
             uint32_t *beta = reinterpret_cast<uint32_t *>(rest + 5 * 256), *sel = beta + 5 * 256;
-            int bt[64], rank[64];
-            for (int q = 0; q < 64; q++) bt[q] = -1;
-            for (int t = 0; t < g.lb; t++) bt[g.pos_beta[t]] = g.beta_bit[t];
-            for (int q = 0, r = 0; q < 64; q++) rank[q] = bt[q] >= 0 ? -1 : r++;
-            for (int j = 0; j < 5; j++)
-                for (int x = 0; x < 256; x++)
-                    for (int b = 0; b < 8; b++) {
-                        const int q = 8 * j + b;
-                        if (!((x >> b) & 1) || q >= g.nbits) continue;
-                        if (bt[q] >= 0) beta[j * 256 + x] |= 1u << bt[q];
-                        else rest[j * 256 + x] |= 1ull << rank[q];
-                    }
-            for (int j = 0; j < 8; j++)
-                for (int x = 0; x < 256; x++)
-                    for (int i = 0; i < g.nq; i++) {
-                        const int c = g.q[i] - 8 * j;
-                        if (c >= 0 && c < 8 && ((x >> c) & 1)) sel[j * 256 + x] |= 1u << i;
-                    }
+            tn_gather_tables(g.nbits, g.lb, g.pos_beta, g.beta_bit, g.nq, g.q, rest, beta, sel);
             const uint64_t *dev = static_cast<const uint64_t *>(cn.gtabs.p) + gi * W;
             g.rest_tab = dev;
             g.beta_tab = reinterpret_cast<const uint32_t *>(dev + 5 * 256);
