@@ -230,6 +230,21 @@ int tn_plan_estimate(tn_plan_h p, const uint64_t *slices, int64_t n_slices, int6
 int tn_contract(tn_plan_h p, const uint64_t *slices, int64_t n_slices, const uint64_t *closed_bits,
                 int64_t n_batches, double *amps, int32_t flags);
 
+/*
+ * Verification (Sec. I.A, "exact amplitudes for uncorrelated bitstrings"; Eq. 1): the
+ * amplitude a(s) of each of N bitstrings summed over a slice set (unnormalised, as
+ * tn_contract computes it) and their linear XEB, xeb = 2^n / N * sum_s |a(s)|^2 - 1.
+ * A string's closed qubits select its batch and its open qubits its entry; a plan with no
+ * open qubits computes one amplitude per string.  Groups after the first reuse the
+ * batch-independent contractions.  The sum of |a|^2 = re*re + im*im (no fused
+ * multiply-add) runs in FP64 on the device in a fixed order.
+ *  bitstrings  N host values (bit q = qubit q, below the circuit's qubit count).
+ *  amps        NULL, or N host complex128 values (interleaved) receiving a(s).
+ * Errors: TN_EINVAL (bad slice or bitstring), TN_ENOMEM (budget), TN_EDEVICE.
+ */
+int tn_xeb(tn_plan_h p, const uint64_t *slices, int64_t n_slices, const uint64_t *bitstrings, int64_t N,
+           double *xeb, double *amps);
+
 typedef struct {
     double F;           /* retained fidelity sum_{i in X} R[i] (1 when f >= 1) */
     double eps_hat;     /* Sec. II.C: eps_J / |J| over the computed batches */

@@ -167,6 +167,7 @@ struct tn_plan_s {
     int log2T = 0;
     CNet amp;
     DBuf d_closed, d_amps, d_j, d_acc, d_pick, d_eps, d_bits, d_R, d_X;
+    DBuf d_xidx, d_xamps, d_xsum;  // tn_xeb: in-batch entries, the strings' amplitudes, sums
     double budget = 0;
     // norm cache
     double norm_f = -1;
@@ -1598,6 +1599,67 @@ int tn_contract(tn_plan_h p, const uint64_t *slices, int64_t n_slices, const uin
     }
     CK(cudaStreamSynchronize(st));
     return check_err(p->amp, st);
+}
+
+int tn_xeb(tn_plan_h p, const uint64_t *slices, int64_t n_slices, const uint64_t *bitstrings, int64_t N, double *xeb,
+           double *amps) {
+    if (!p || !slices || n_slices <= 0 || !bitstrings || N <= 0 || !xeb) {
+        tn_set_error("tn_xeb: bad arguments");
+        return TN_EINVAL;
+    }
+    const int nI = (int)p->I.size();
+    std::vector<uint64_t> sl(slices, slices + n_slices);
+    {
+        std::vector<uint64_t> sorted = sl;
+        std::sort(sorted.begin(), sorted.end());
+        if (std::adjacent_find(sorted.begin(), sorted.end()) != sorted.end()) { tn_set_error("duplicate slice"); return TN_EINVAL; }
+        if (nI < 64 && sorted.back() >> nI) { tn_set_error("slice sets bits beyond the sliced edges"); return TN_EINVAL; }
+    }
+    const int n = p->mg.n;
+    if (n < 64)
+        for (int64_t t = 0; t < N; t++)
+            if (bitstrings[t] >> n) { tn_set_error("tn_xeb: bitstring beyond the circuit's qubits"); return TN_EINVAL; }
+    // each string's batch (its closed qubits, ascending) and entry (its open qubits in order)
+    std::vector<uint64_t> cb((size_t)N, 0);
+    std::vector<int32_t> idx((size_t)N, 0);
+    for (int64_t t = 0; t < N; t++) {
+        for (size_t c = 0; c < p->closed.size(); c++) cb[t] |= ((bitstrings[t] >> p->closed[c]) & 1ull) << c;
+        for (size_t r = 0; r < p->open.size(); r++) idx[t] |= (int32_t)(((bitstrings[t] >> p->open[r]) & 1ull) << r);
+    }
+    cudaStream_t st = p->mem.stream;
+    RC(ensure_variant(p->mem, p->amp, explicit_legs(sl, nI)));
+    RC(prepare_call(p->mem, p->amp, sl, p->budget));
+    const long long T = 1LL << p->log2T;
+    const int nopen = (int)p->open.size();
+    RC(ensure(p->mem, p->d_closed, T * sizeof(uint64_t)));
+    RC(ensure(p->mem, p->d_amps, (T << nopen) * sizeof(double2)));
+    RC(ensure(p->mem, p->d_xidx, T * sizeof(int32_t)));
+    RC(ensure(p->mem, p->d_xamps, N * sizeof(double2)));
+    RC(ensure(p->mem, p->d_xsum, (tnk::kNormGrid + 1) * sizeof(double)));
+    double2 *xa = static_cast<double2 *>(p->d_xamps.p);
+    for (long long g0 = 0; g0 < N; g0 += T) {
+        const long long nb = std::min<long long>(T, N - g0);
+        CK(cudaMemsetAsync(p->d_closed.p, 0, T * sizeof(uint64_t), st));
+        if (!p->closed.empty())
+            CK(cudaMemcpyAsync(p->d_closed.p, cb.data() + g0, nb * sizeof(uint64_t), cudaMemcpyHostToDevice, st));
+        CK(cudaMemcpyAsync(p->d_xidx.p, idx.data() + g0, nb * sizeof(int32_t), cudaMemcpyHostToDevice, st));
+        RC(execute_graphed(p->mem, p->amp, static_cast<const uint64_t *>(p->d_closed.p), g0 > 0,
+                           static_cast<double2 *>(p->d_amps.p), st, p->budget));
+        tnk::pick_amplitudes<<<(unsigned)((nb + 255) / 256), 256, 0, st>>>(
+            static_cast<const double2 *>(p->d_amps.p), nopen, static_cast<const int32_t *>(p->d_xidx.p), nb, xa + g0);
+        CK(cudaGetLastError());
+    }
+    double *part = static_cast<double *>(p->d_xsum.p);
+    tnk::sum_norms<<<tnk::kNormGrid, 256, 0, st>>>(xa, N, part);
+    tnk::norm_total<<<1, tnk::kNormGrid, 0, st>>>(part, part + tnk::kNormGrid);
+    CK(cudaGetLastError());
+    double sum = 0.0;
+    CK(cudaMemcpyAsync(&sum, part + tnk::kNormGrid, sizeof(double), cudaMemcpyDeviceToHost, st));
+    if (amps) CK(cudaMemcpyAsync(amps, xa, N * sizeof(double2), cudaMemcpyDeviceToHost, st));
+    CK(cudaStreamSynchronize(st));
+    RC(check_err(p->amp, st));
+    *xeb = std::ldexp(sum, n) / (double)N - 1.0;
+    return TN_OK;
 }
 
 int tn_partial_norms(tn_plan_h p, double f, int32_t *s_index, int32_t *k_out, double *R, int64_t cap_R) {

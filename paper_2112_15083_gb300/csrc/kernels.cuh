@@ -681,6 +681,43 @@ __global__ void __launch_bounds__(256) root_slice_sum(GemmParams p, int nfree, i
     out[e] = make_double2(re, im);
 }
 
+// ---------------------------------------------------------------- verification XEB
+
+// The amplitude of each of nb bitstrings from its batch: out[t] = amps[(t << n_open) | idx[t]].
+__global__ void pick_amplitudes(const double2 *amps, int n_open, const int32_t *idx, long long nb, double2 *out) {
+    const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t < nb) out[t] = amps[(t << n_open) | idx[t]];
+}
+
+// FP64 sum of |a_i|^2 = re*re + im*im (rounded products, no fused multiply-add) over n
+// values in a fixed order: thread j of block b sums i = b*256 + j, then every stride of
+// kNormGrid*256, in turn; each block halves its 256 partials pairwise into partial[b].
+// norm_total then halves the kNormGrid partials the same way.
+constexpr int kNormGrid = 256;
+__global__ void __launch_bounds__(256) sum_norms(const double2 *a, long long n, double *partial) {
+    __shared__ double sh[256];
+    double acc = 0.0;
+    for (long long i = (long long)blockIdx.x * 256 + threadIdx.x; i < n; i += (long long)kNormGrid * 256)
+        acc = __dadd_rn(acc, __dadd_rn(__dmul_rn(a[i].x, a[i].x), __dmul_rn(a[i].y, a[i].y)));
+    sh[threadIdx.x] = acc;
+    __syncthreads();
+    for (int h = 128; h > 0; h >>= 1) {
+        if ((int)threadIdx.x < h) sh[threadIdx.x] = __dadd_rn(sh[threadIdx.x], sh[threadIdx.x + h]);
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) partial[blockIdx.x] = sh[0];
+}
+__global__ void __launch_bounds__(256) norm_total(const double *partial, double *out) {
+    __shared__ double sh[kNormGrid];
+    sh[threadIdx.x] = partial[threadIdx.x];
+    __syncthreads();
+    for (int h = kNormGrid / 2; h > 0; h >>= 1) {
+        if ((int)threadIdx.x < h) sh[threadIdx.x] = __dadd_rn(sh[threadIdx.x], sh[threadIdx.x + h]);
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) *out = sh[0];
+}
+
 // ---------------------------------------------------------------- Philox
 
 // Philox4x32-10 (Salmon, Moraes, Dror, Shaw, SC'11): 10 rounds of two 32x32->64

@@ -22,7 +22,7 @@ DEVICE_BUFFERS = 1
 EXPORTED = [
     "tn_plan_opts_default", "tn_circuit_load", "tn_circuit_destroy", "tn_plan", "tn_plan_destroy",
     "tn_plan_get_info", "tn_plan_sliced_edges", "tn_partial_norms", "tn_slice_cut", "tn_select",
-    "tn_contract", "tn_sample", "tn_rejection_sample", "tn_draw_batches", "tn_strerror", "tn_last_error",
+    "tn_contract", "tn_xeb", "tn_sample", "tn_rejection_sample", "tn_draw_batches", "tn_strerror", "tn_last_error",
     "tn_plan_host", "tn_sliced_vertex_select", "tn_sample_step", "tn_trace_enable", "tn_trace_read",
     "tn_slice_cut_noalloc", "tn_plan_estimate", "tn_plan_sync", "tn_server_opts_default", "tn_server_create",
     "tn_server_submit", "tn_server_query", "tn_server_wait", "tn_server_get_stats", "tn_server_destroy",
@@ -140,6 +140,7 @@ def lib():
         L.tn_slice_cut.argtypes = [vp, i32, dbl, vp, vp, ctypes.POINTER(i32), ctypes.POINTER(dbl)]
         L.tn_select.argtypes = [vp, dbl, vp, i64, ctypes.POINTER(i64), ctypes.POINTER(dbl)]
         L.tn_contract.argtypes = [vp, vp, i64, vp, i64, vp, i32]
+        L.tn_xeb.argtypes = [vp, vp, i64, vp, i64, ctypes.POINTER(dbl), vp]
         L.tn_sample.argtypes = [vp, dbl, i64, u64, dbl, vp, i32, ctypes.POINTER(SampleStats)]
         L.tn_rejection_sample.argtypes = [vp, i64, i32, dbl, u64, u64, vp, vp, vp]
         L.tn_draw_batches.argtypes = [u64, u64, i64, i32, vp, vp]
@@ -346,6 +347,18 @@ class Plan:
         rc = L.tn_contract(self.h, _np_ptr(sl), sl.size, _np_ptr(cb), nb, _np_ptr(res), 0)
         _check(rc, "tn_contract")
         return res
+
+    def xeb(self, slices, bitstrings, return_amplitudes=False):
+        """Linear XEB (Eq. 1) of the given bitstrings from their amplitudes summed over the
+        slice set; with return_amplitudes, also those amplitudes (complex128 numpy)."""
+        sl = np.ascontiguousarray(np.asarray(slices, dtype=np.uint64))
+        bs = np.ascontiguousarray(np.asarray(bitstrings, dtype=np.uint64).reshape(-1))
+        amps = np.zeros(bs.size, dtype=np.complex128) if return_amplitudes else None
+        x = ctypes.c_double()
+        rc = lib().tn_xeb(self.h, _np_ptr(sl), sl.size, _np_ptr(bs), bs.size, ctypes.byref(x),
+                          _np_ptr(amps) if amps is not None else None)
+        _check(rc, "tn_xeb")
+        return (x.value, amps) if return_amplitudes else x.value
 
     def sample_step(self, slices, F: float, seed: int, t0: int, alpha: float = 2.0, reuse_stem: bool = False,
                     accept=None, bits=None):
