@@ -92,6 +92,9 @@ typedef struct {
                                 whose output is bit-identical to the two launches, without
                                 writing the root's per-slice values to memory.  0
                                 (default): separate launches. */
+    int32_t job_groups;      /* batch groups per sampling job that the order search
+                                optimises for: a batch-independent step runs once per
+                                job, the others once per group; <= 1 (default): one */
     void *stream;            /* cudaStream_t; NULL = legacy default stream */
     tn_alloc_fn alloc;       /* optional device allocator */
     tn_free_fn free;

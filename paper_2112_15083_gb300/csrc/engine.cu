@@ -1382,6 +1382,7 @@ void tn_plan_opts_default(tn_plan_opts *o) {
     o->max_norm_flops = 2e15;
     o->autotune = 1;
     o->fuse_root_sum = 0;
+    o->job_groups = 1;
 }
 
 int tn_circuit_load(const void *buf, size_t len, tn_circuit_h *out) {

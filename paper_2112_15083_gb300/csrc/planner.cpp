@@ -570,6 +570,8 @@ StepEst step_estimate(const Network &net, const Node &a, const Node &b, const No
     e.bytes = by + (ga ? 2 * sa : 0) + (gb ? 2 * sb : 0);
     e.time = std::max(fl / rate, by / bw) + launch + gt;
     if (net.mem_limit_elems > 0 && by / 8.0 > net.mem_limit_elems) e.time += 1e6 * (by / 8.0 / net.mem_limit_elems);
+    // a batch step runs once per group of the job, a batch-independent one once per job
+    if (c.beta) e.time *= net.job_groups;
     return e;
 }
 
@@ -1356,6 +1358,7 @@ void tn_cost_settings(Network &net, const tn_plan_opts &o) {
     net.tc_flop_rate = o.precision != TN_PREC_C64 ? 4e14 : 0;
     const double budget = o.hbm_budget_bytes > 0 ? o.hbm_budget_bytes : 64.0 * (1ull << 30);
     net.mem_limit_elems = budget / 8.0 / 2.0;
+    net.job_groups = o.job_groups > 1 ? (double)o.job_groups : 1.0;
 }
 
 int tn_tree_and_compile(Network &net, const tn_plan_opts &o, const int32_t *order, int n_order,

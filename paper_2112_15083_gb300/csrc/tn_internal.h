@@ -86,6 +86,7 @@ struct Network {
     // 0: unlimited) above which a tree is treated as infeasible.
     double tc_flop_rate = 0;
     double mem_limit_elems = 0;
+    double job_groups = 1;  // batch groups per job: the cost weight of batch steps
     int n_sliced = 0;              // |I|
     std::vector<int> idx_seg;      // segment id of each network index (-1: beta / other)
 };
