@@ -1,0 +1,111 @@
+"""The compiled plans compute the right amplitudes, checked on the CPU: the host planner and
+step compiler of the library plan 12- and 16-qubit circuits (order search, slicing, lazy
+batch selection at every threshold, tensor-core operand roles, explicit and layout-bit
+versions), and a host executor of the compiled step list (tests/emulator) contracts them
+in complex128 for several batch groups, full and partial slice sets.  The amplitudes must
+equal the oracle's projector-sum state vector to 1e-10 of its largest amplitude."""
+import ctypes
+import os
+import shutil
+import subprocess
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_2112_15083_gb300 import circuits as cg
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+ROOT = os.path.dirname(HERE)
+
+
+@pytest.fixture(scope="module", autouse=True)
+def built():
+    import __graft_entry__
+    __graft_entry__.build()
+
+
+@pytest.fixture(scope="module")
+def emu(tmp_path_factory):
+    cxx = shutil.which("g++") or shutil.which("c++")
+    if cxx is None:
+        pytest.skip("no C++ compiler")
+    out = str(tmp_path_factory.mktemp("emu") / "libplanemu.so")
+    subprocess.run([cxx, "-O2", "-std=c++17", "-shared", "-fPIC",
+                    "-I", os.path.join(ROOT, "paper_2112_15083_gb300", "csrc"), "-I", os.path.join(ROOT, "include"),
+                    os.path.join(HERE, "emulator", "plan_emulator.cpp"), "-o", out], check=True)
+    L = ctypes.CDLL(out)
+    vp, i32, i64 = ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64
+    L.emu_contract.argtypes = [vp, ctypes.c_size_t, vp, i32, vp, i32, i32, vp, i32, vp, i64, vp, vp,
+                               ctypes.POINTER(i32), vp]
+    L.emu_error.restype = ctypes.c_char_p
+    return L
+
+
+def opts(log2_batches, n_sliced, precision, trials=16):
+    import paper_2112_15083_gb300 as P
+    o = P.tn.PlanOpts()
+    P.lib().tn_plan_opts_default(ctypes.byref(o))
+    o.log2_batches = log2_batches
+    o.n_auto_sliced = n_sliced
+    o.order_trials = trials
+    o.precision = precision
+    return o
+
+
+def run(emu, circ, openq, o, q_max, tc, slices, closed):
+    buf = circ.serialize()
+    openv = np.ascontiguousarray(np.asarray(openq, dtype=np.int32))
+    sl = np.ascontiguousarray(np.asarray(slices, dtype=np.uint64))
+    cb = np.ascontiguousarray(np.asarray(closed, dtype=np.uint64))
+    out = np.zeros(cb.size << len(openq), dtype=np.complex128)
+    edges = np.zeros(128, dtype=np.int32)
+    ne = ctypes.c_int32()
+    stats = np.zeros(3, dtype=np.int32)
+    rc = emu.emu_contract(buf, len(buf), openv.ctypes.data, openv.size, ctypes.byref(o), q_max, tc,
+                          sl.ctypes.data, sl.size, cb.ctypes.data, cb.size, out.ctypes.data, edges.ctypes.data,
+                          ctypes.byref(ne), stats.ctypes.data)
+    assert rc == 0, emu.emu_error().decode()
+    return out.reshape(cb.size, 1 << len(openq)), [(int(edges[2 * e]), int(edges[2 * e + 1])) for e in range(ne.value)], stats
+
+
+def slice_sets(n_sliced, rng):
+    every = np.arange(1 << n_sliced, dtype=np.uint64)
+    if n_sliced == 0:
+        return [("all", every)]
+    half = np.sort(rng.choice(every, size=max(1, every.size // 2), replace=False))
+    return [("all", every), ("half", half), ("one", every[-1:])]
+
+
+def check(emu, circ, openq, o, q_max, tc, nb, seed):
+    n = circ.n_qubits
+    rng = np.random.default_rng(seed)
+    closed = cg.random_closed_bits(nb, n - len(openq), seed=seed) if len(openq) < n else np.zeros(nb, np.uint64)
+    _, edges, _ = run(emu, circ, openq, o, q_max, tc, [0], closed[:1])
+    for name, sl in slice_sets(len(edges), rng):
+        amps, _, stats = run(emu, circ, openq, o, q_max, tc, sl, closed)
+        psi = oracle.sliced_state(circ, edges, [int(s) for s in sl]) if edges else oracle.simulate(circ)
+        ref = oracle.batch_amplitudes(psi, n, openq, closed) if len(openq) < n else np.tile(psi, (nb, 1))
+        scale = float(np.abs(ref).max())
+        assert float(np.abs(amps - ref).max()) <= 1e-10 * scale, (name, q_max, tc, stats)
+
+
+@pytest.mark.parametrize("q_max", [-2, -1, 0, 6])
+@pytest.mark.parametrize("tc", [0, 1])
+def test_12q_every_batch_threshold(emu, q_max, tc):
+    circ = cg.sycamore_grid(3, 4, 8, seed=1)
+    o = opts(log2_batches=2, n_sliced=3, precision=1 if tc else 0)
+    check(emu, circ, cg.default_open_qubits(3, 4, 6), o, q_max, tc, nb=11, seed=5)
+
+
+@pytest.mark.parametrize("n_sliced,log2_batches", [(0, 0), (2, 4), (4, 6)])
+def test_16q_slicing_and_groups(emu, n_sliced, log2_batches):
+    circ = cg.sycamore_grid(4, 4, 10, seed=2)
+    o = opts(log2_batches=log2_batches, n_sliced=n_sliced, precision=1)
+    check(emu, circ, cg.default_open_qubits(4, 4, 6), o, -2, 1, nb=(1 << log2_batches) + 3, seed=7)
+
+
+def test_12q_all_open(emu):
+    circ = cg.sycamore_grid(3, 4, 8, seed=0)
+    o = opts(log2_batches=0, n_sliced=2, precision=0)
+    check(emu, circ, list(range(12)), o, -2, 0, nb=1, seed=1)
