@@ -109,3 +109,14 @@ def test_12q_all_open(emu):
     circ = cg.sycamore_grid(3, 4, 8, seed=0)
     o = opts(log2_batches=0, n_sliced=2, precision=0)
     check(emu, circ, list(range(12)), o, -2, 0, nb=1, seed=1)
+
+
+@pytest.mark.parametrize("seed", range(4))
+def test_haar_circuits_random_pairs(emu, seed):
+    """Haar gates on random ordered qubit pairs: neither symmetric under swapping the
+    qubits nor under transposition, so layout and role mistakes show."""
+    n = 10
+    circ = cg.random_haar(n, 70, seed=seed, p_two=0.75)
+    openq = [int(q) for q in np.random.default_rng(seed).permutation(n)[:4]]
+    o = opts(log2_batches=3, n_sliced=2, precision=seed % 2)
+    check(emu, circ, openq, o, [-2, -1, 0, 6][seed], seed % 2, nb=13, seed=seed)
