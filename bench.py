@@ -530,11 +530,15 @@ def run_grid5x8_sample(args):
     circ = cg.sycamore_grid(rows, cols, cycles, seed=0)
     openq = cg.default_open_qubits(rows, cols, 6)
     C = P.circuit_load(circ.serialize())
+    # the job's batch groups: the order search weights the batch steps by them (the
+    # batch-independent ones run once per slice)
+    job_groups = math.ceil(1.1 * alpha * N / (1 << lb))
     t = time.perf_counter()
     # the largest tensor cap whose one-slice working set fits the budget
     for cap in (30, 29, 28, 27, 26):
         plan = P.plan(C, openq, log2_batches=lb, order_trials=256, order_seed=0, max_log2_tensor=cap,
-                      hbm_budget_bytes=150e9, precision=P.tn.PREC_BF16X2, autotune=0, max_norm_flops=3e16)
+                      hbm_budget_bytes=150e9, precision=P.tn.PREC_BF16X2, autotune=0, max_norm_flops=3e16,
+                      job_groups=job_groups)
         if plan.estimate(np.zeros(1, np.uint64))[0] <= 140e9:
             break
         del plan
@@ -547,6 +551,7 @@ def run_grid5x8_sample(args):
                                    "slices until one slice's working set fits 140 GB; f = 1/64; %d batches of 64 "
                                    "per group; bf16x2" % (1 << lb)},
             "plan": {"seconds": round(plan_s, 1), "sliced_legs": info["n_sliced"], "max_log2_tensor_cap": cap,
+                     "job_groups": job_groups,
                      "log2_max_tensor": info["log2_max_tensor"], "flops_all_slices": info["flops_all_slices"]}}
     t = time.perf_counter()
     try:

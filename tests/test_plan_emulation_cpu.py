@@ -120,3 +120,12 @@ def test_haar_circuits_random_pairs(emu, seed):
     openq = [int(q) for q in np.random.default_rng(seed).permutation(n)[:4]]
     o = opts(log2_batches=3, n_sliced=2, precision=seed % 2)
     check(emu, circ, openq, o, [-2, -1, 0, 6][seed], seed % 2, nb=13, seed=seed)
+
+
+@pytest.mark.parametrize("job_groups", [8, 64])
+def test_16q_plans_weighted_for_a_job(emu, job_groups):
+    """Plans whose order search weights the batch steps by the job's groups."""
+    circ = cg.sycamore_grid(4, 4, 10, seed=3)
+    o = opts(log2_batches=4, n_sliced=3, precision=1)
+    o.job_groups = job_groups
+    check(emu, circ, cg.default_open_qubits(4, 4, 6), o, -2, 1, nb=37, seed=9)
