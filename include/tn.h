@@ -248,6 +248,21 @@ int tn_contract(tn_plan_h p, const uint64_t *slices, int64_t n_slices, const uin
 int tn_xeb(tn_plan_h p, const uint64_t *slices, int64_t n_slices, const uint64_t *bitstrings, int64_t N,
            double *xeb, double *amps);
 
+/*
+ * XEB spoofing (Sec. III, "Spoofing Linear XEB"): the amplitudes of one batch (the closed
+ * qubits fixed to closed_pattern, all 2^n_open open patterns) summed over a slice set,
+ * then the N strings of largest p = re*re + im*im (FP64, no fused multiply-add; equal
+ * values: the smaller in-batch index first), selected exactly on the device (radix select
+ * of the FP64 bit patterns).  The recipe takes n_open = ceil(log2(10 N)) and the slice set
+ * of tn_select at the target fidelity; a plan with log2_batches = 0 computes that batch
+ * alone.
+ *  bitstrings  out, N entries in ascending in-batch index order (bit q = qubit q).
+ *  probs       NULL, or out: p of each selected string (unnormalised).
+ * Errors: TN_EINVAL (N outside [1, 2^n_open], n_open > 30, bad pattern or slices).
+ */
+int tn_spoof(tn_plan_h p, const uint64_t *slices, int64_t n_slices, uint64_t closed_pattern, int64_t N,
+             uint64_t *bitstrings, double *probs);
+
 typedef struct {
     double F;           /* retained fidelity sum_{i in X} R[i] (1 when f >= 1) */
     double eps_hat;     /* Sec. II.C: eps_J / |J| over the computed batches */

@@ -168,6 +168,7 @@ struct tn_plan_s {
     CNet amp;
     DBuf d_closed, d_amps, d_j, d_acc, d_pick, d_eps, d_bits, d_R, d_X;
     DBuf d_xidx, d_xamps, d_xsum;  // tn_xeb: in-batch entries, the strings' amplitudes, sums
+    DBuf d_skey, d_shist, d_sgt, d_seq, d_sbits, d_sprob;  // tn_spoof: keys, histogram, counts, output
     double budget = 0;
     // norm cache
     double norm_f = -1;
@@ -1661,6 +1662,83 @@ int tn_xeb(tn_plan_h p, const uint64_t *slices, int64_t n_slices, const uint64_t
     RC(check_err(p->amp, st));
     *xeb = std::ldexp(sum, n) / (double)N - 1.0;
     return TN_OK;
+}
+
+int tn_spoof(tn_plan_h p, const uint64_t *slices, int64_t n_slices, uint64_t closed_pattern, int64_t N,
+             uint64_t *bitstrings, double *probs) {
+    const int nopen = p ? (int)p->open.size() : 0;
+    if (!p || !slices || n_slices <= 0 || !bitstrings || N < 1 || nopen > 30 || N > (1LL << nopen) ||
+        (p->closed.size() < 64 && (closed_pattern >> p->closed.size()))) {
+        tn_set_error("tn_spoof: bad arguments");
+        return TN_EINVAL;
+    }
+    const int nI = (int)p->I.size();
+    std::vector<uint64_t> sl(slices, slices + n_slices);
+    {
+        std::vector<uint64_t> sorted = sl;
+        std::sort(sorted.begin(), sorted.end());
+        if (std::adjacent_find(sorted.begin(), sorted.end()) != sorted.end()) { tn_set_error("duplicate slice"); return TN_EINVAL; }
+        if (nI < 64 && sorted.back() >> nI) { tn_set_error("slice sets bits beyond the sliced edges"); return TN_EINVAL; }
+    }
+    cudaStream_t st = p->mem.stream;
+    RC(ensure_variant(p->mem, p->amp, explicit_legs(sl, nI)));
+    RC(prepare_call(p->mem, p->amp, sl, p->budget));
+    const long long T = 1LL << p->log2T, M = 1LL << nopen;
+    RC(ensure(p->mem, p->d_closed, T * sizeof(uint64_t)));
+    RC(ensure(p->mem, p->d_amps, (T << nopen) * sizeof(double2)));
+    // the batch is batch 0 of one group (the group's other batches take pattern 0)
+    CK(cudaMemsetAsync(p->d_closed.p, 0, T * sizeof(uint64_t), st));
+    CK(cudaMemcpyAsync(p->d_closed.p, &closed_pattern, sizeof(uint64_t), cudaMemcpyHostToDevice, st));
+    RC(execute_graphed(p->mem, p->amp, static_cast<const uint64_t *>(p->d_closed.p), false,
+                       static_cast<double2 *>(p->d_amps.p), st, p->budget));
+    const long long nblk = (M + tnk::kSelBlock - 1) / tnk::kSelBlock;
+    RC(ensure(p->mem, p->d_skey, M * sizeof(unsigned long long)));
+    RC(ensure(p->mem, p->d_shist, 256 * sizeof(unsigned int)));
+    RC(ensure(p->mem, p->d_sgt, nblk * sizeof(unsigned int)));
+    RC(ensure(p->mem, p->d_seq, nblk * sizeof(unsigned int)));
+    RC(ensure(p->mem, p->d_sbits, N * sizeof(unsigned long long)));
+    if (probs) RC(ensure(p->mem, p->d_sprob, N * sizeof(double)));
+    auto *key = static_cast<unsigned long long *>(p->d_skey.p);
+    auto *hist = static_cast<unsigned int *>(p->d_shist.p);
+    const unsigned grid = (unsigned)std::min<long long>((M + 255) / 256, 8LL * num_sms());
+    tnk::spoof_keys<<<grid, 256, 0, st>>>(static_cast<const double2 *>(p->d_amps.p), M, key);
+    CK(cudaGetLastError());
+    // radix select, most significant digit first: the N-th largest key, and how many of
+    // the keys equal to it the selection takes
+    unsigned long long prefix = 0, mask = 0;
+    long long need = N;
+    for (int shift = 56; shift >= 0; shift -= 8) {
+        CK(cudaMemsetAsync(hist, 0, 256 * sizeof(unsigned int), st));
+        tnk::digit_hist<<<grid, 256, 0, st>>>(key, M, mask, prefix, shift, hist);
+        CK(cudaGetLastError());
+        unsigned int h[256];
+        CK(cudaMemcpyAsync(h, hist, sizeof(h), cudaMemcpyDeviceToHost, st));
+        CK(cudaStreamSynchronize(st));
+        int d = 255;
+        long long above = 0;
+        while (d > 0 && above + (long long)h[d] < need) above += h[d--];
+        need -= above;
+        prefix |= (unsigned long long)d << shift;
+        mask |= 255ull << shift;
+    }
+    auto *gt = static_cast<unsigned int *>(p->d_sgt.p);
+    auto *eq = static_cast<unsigned int *>(p->d_seq.p);
+    tnk::sel_counts<<<(unsigned)nblk, tnk::kSelBlock, 0, st>>>(key, M, prefix, gt, eq);
+    tnk::sel_scan<<<1, tnk::kSelBlock, 0, st>>>(gt, eq, (int)nblk);
+    unsigned long long base = 0;
+    for (size_t c = 0; c < p->closed.size(); c++) base |= ((closed_pattern >> c) & 1ull) << p->closed[c];
+    tnk::OpenQubits oq;
+    std::memset(&oq, 0, sizeof(oq));
+    oq.n = nopen;
+    for (int r = 0; r < nopen; r++) oq.q[r] = (int8_t)p->open[r];
+    tnk::sel_write<<<(unsigned)nblk, tnk::kSelBlock, 0, st>>>(key, M, prefix, need, gt, eq, base, oq,
+                                                               static_cast<unsigned long long *>(p->d_sbits.p),
+                                                               probs ? static_cast<double *>(p->d_sprob.p) : nullptr);
+    CK(cudaGetLastError());
+    CK(cudaMemcpyAsync(bitstrings, p->d_sbits.p, N * sizeof(uint64_t), cudaMemcpyDeviceToHost, st));
+    if (probs) CK(cudaMemcpyAsync(probs, p->d_sprob.p, N * sizeof(double), cudaMemcpyDeviceToHost, st));
+    CK(cudaStreamSynchronize(st));
+    return check_err(p->amp, st);
 }
 
 int tn_partial_norms(tn_plan_h p, double f, int32_t *s_index, int32_t *k_out, double *R, int64_t cap_R) {

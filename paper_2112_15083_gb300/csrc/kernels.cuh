@@ -718,6 +718,138 @@ __global__ void __launch_bounds__(256) norm_total(const double *partial, double 
     if (threadIdx.x == 0) *out = sh[0];
 }
 
+// ---------------------------------------------------------------- top-N selection (XEB spoofing)
+
+// key[i] = the bit pattern of p_i = re*re + im*im in FP64 (rounded products, no fused
+// multiply-add): non-negative doubles order like their bit patterns.
+__global__ void spoof_keys(const double2 *a, long long n, unsigned long long *key) {
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+        const double p = __dadd_rn(__dmul_rn(a[i].x, a[i].x), __dmul_rn(a[i].y, a[i].y));
+        key[i] = (unsigned long long)__double_as_longlong(p);
+    }
+}
+
+// Histogram of the 8-bit digit at `shift` over the keys whose bits above it equal `prefix`
+// (under `mask`): one shared histogram per block, added to hist[256].
+__global__ void __launch_bounds__(256) digit_hist(const unsigned long long *key, long long n, unsigned long long mask,
+                                                  unsigned long long prefix, int shift, unsigned int *hist) {
+    __shared__ unsigned int h[256];
+    h[threadIdx.x] = 0;
+    __syncthreads();
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+        const unsigned long long k = key[i];
+        if ((k & mask) == prefix) atomicAdd(&h[(k >> shift) & 255u], 1u);
+    }
+    __syncthreads();
+    if (h[threadIdx.x]) atomicAdd(&hist[threadIdx.x], h[threadIdx.x]);
+}
+
+constexpr int kSelBlock = 1024;  // keys per selection block (one per thread)
+
+// Exclusive rank of this thread's flag among the block's flags, and the block's total.
+__device__ __forceinline__ unsigned int block_rank(bool f, unsigned int *warp_tot, unsigned int &total) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const unsigned int b = __ballot_sync(0xffffffffu, f);
+    const unsigned int in_warp = __popc(b & ((1u << lane) - 1u));
+    if (lane == 0) warp_tot[warp] = __popc(b);
+    __syncthreads();
+    unsigned int before = 0;
+    total = 0;
+    for (int w = 0; w < kSelBlock / 32; w++) {
+        if (w < warp) before += warp_tot[w];
+        total += warp_tot[w];
+    }
+    __syncthreads();  // warp_tot is reused by the next call
+    return before + in_warp;
+}
+
+// Per block of kSelBlock consecutive keys: how many exceed the threshold and how many equal it.
+__global__ void __launch_bounds__(kSelBlock) sel_counts(const unsigned long long *key, long long n,
+                                                        unsigned long long thr, unsigned int *gt, unsigned int *eq) {
+    __shared__ unsigned int wt[kSelBlock / 32];
+    const long long i = (long long)blockIdx.x * kSelBlock + threadIdx.x;
+    const unsigned long long k = i < n ? key[i] : 0ull;
+    unsigned int tg, te;
+    block_rank(i < n && k > thr, wt, tg);
+    block_rank(i < n && k == thr, wt, te);
+    if (threadIdx.x == 0) {
+        gt[blockIdx.x] = tg;
+        eq[blockIdx.x] = te;
+    }
+}
+
+// In-place exclusive prefix sums of the per-block counts, in one block, chunk by chunk.
+__global__ void __launch_bounds__(kSelBlock) sel_scan(unsigned int *gt, unsigned int *eq, int nb) {
+    __shared__ unsigned int wg[kSelBlock / 32], we[kSelBlock / 32];
+    unsigned int carry_g = 0, carry_e = 0;
+    for (int c = 0; c < nb; c += kSelBlock) {
+        const int j = c + (int)threadIdx.x;
+        const unsigned int g = j < nb ? gt[j] : 0u, e = j < nb ? eq[j] : 0u;
+        // block-wide exclusive sums of g and e by warp scans (shuffles) of the counts
+        const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+        unsigned int sg = g, se = e;
+        for (int o = 1; o < 32; o <<= 1) {
+            const unsigned int yg = __shfl_up_sync(0xffffffffu, sg, o), ye = __shfl_up_sync(0xffffffffu, se, o);
+            if (lane >= o) {
+                sg += yg;
+                se += ye;
+            }
+        }
+        if (lane == 31) {
+            wg[warp] = sg;
+            we[warp] = se;
+        }
+        __syncthreads();
+        unsigned int bg = 0, be = 0, tg = 0, te = 0;
+        for (int w = 0; w < kSelBlock / 32; w++) {
+            if (w < warp) {
+                bg += wg[w];
+                be += we[w];
+            }
+            tg += wg[w];
+            te += we[w];
+        }
+        if (j < nb) {
+            gt[j] = carry_g + bg + sg - g;
+            eq[j] = carry_e + be + se - e;
+        }
+        carry_g += tg;
+        carry_e += te;
+        __syncthreads();  // wg / we are rewritten by the next chunk
+    }
+}
+
+// The open qubits of a batch: bit r of an in-batch index is qubit q[r].
+struct OpenQubits {
+    int8_t q[64];
+    int n;
+};
+
+// Write the selected positions in ascending order: key > thr, or key == thr among the
+// first `need` equal ones (by position).  Position i goes out as the bitstring
+// base | (bit r of i at qubit open.q[r]) with its p_i.
+__global__ void __launch_bounds__(kSelBlock) sel_write(const unsigned long long *key, long long n,
+                                                       unsigned long long thr, long long need,
+                                                       const unsigned int *gt_off, const unsigned int *eq_off,
+                                                       unsigned long long base, OpenQubits open,
+                                                       unsigned long long *bits, double *prob) {
+    __shared__ unsigned int wt[kSelBlock / 32];
+    const long long i = (long long)blockIdx.x * kSelBlock + threadIdx.x;
+    const unsigned long long k = i < n ? key[i] : 0ull;
+    const bool g = i < n && k > thr, e = i < n && k == thr;
+    unsigned int t;
+    const unsigned int lg = block_rank(g, wt, t);
+    const unsigned int le = block_rank(e, wt, t);
+    const long long eq_before = (long long)eq_off[blockIdx.x] + le;
+    if (g || (e && eq_before < need)) {
+        const long long pos = (long long)gt_off[blockIdx.x] + lg + (eq_before < need ? eq_before : need);
+        unsigned long long b = base;
+        for (int r = 0; r < open.n; r++) b |= (unsigned long long)((i >> r) & 1) << open.q[r];
+        bits[pos] = b;
+        if (prob) prob[pos] = __longlong_as_double((long long)k);
+    }
+}
+
 // ---------------------------------------------------------------- Philox
 
 // Philox4x32-10 (Salmon, Moraes, Dror, Shaw, SC'11): 10 rounds of two 32x32->64

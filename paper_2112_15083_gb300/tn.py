@@ -22,7 +22,7 @@ DEVICE_BUFFERS = 1
 EXPORTED = [
     "tn_plan_opts_default", "tn_circuit_load", "tn_circuit_destroy", "tn_plan", "tn_plan_destroy",
     "tn_plan_get_info", "tn_plan_sliced_edges", "tn_partial_norms", "tn_slice_cut", "tn_select",
-    "tn_contract", "tn_xeb", "tn_sample", "tn_rejection_sample", "tn_draw_batches", "tn_strerror", "tn_last_error",
+    "tn_contract", "tn_xeb", "tn_spoof", "tn_sample", "tn_rejection_sample", "tn_draw_batches", "tn_strerror", "tn_last_error",
     "tn_plan_host", "tn_sliced_vertex_select", "tn_sample_step", "tn_trace_enable", "tn_trace_read",
     "tn_slice_cut_noalloc", "tn_plan_estimate", "tn_plan_sync", "tn_server_opts_default", "tn_server_create",
     "tn_server_submit", "tn_server_query", "tn_server_wait", "tn_server_get_stats", "tn_server_destroy",
@@ -142,6 +142,7 @@ def lib():
         L.tn_select.argtypes = [vp, dbl, vp, i64, ctypes.POINTER(i64), ctypes.POINTER(dbl)]
         L.tn_contract.argtypes = [vp, vp, i64, vp, i64, vp, i32]
         L.tn_xeb.argtypes = [vp, vp, i64, vp, i64, ctypes.POINTER(dbl), vp]
+        L.tn_spoof.argtypes = [vp, vp, i64, u64, i64, vp, vp]
         L.tn_sample.argtypes = [vp, dbl, i64, u64, dbl, vp, i32, ctypes.POINTER(SampleStats)]
         L.tn_rejection_sample.argtypes = [vp, i64, i32, dbl, u64, u64, vp, vp, vp]
         L.tn_draw_batches.argtypes = [u64, u64, i64, i32, vp, vp]
@@ -361,6 +362,18 @@ class Plan:
                           _np_ptr(amps) if amps is not None else None)
         _check(rc, "tn_xeb")
         return (x.value, amps) if return_amplitudes else x.value
+
+    def spoof(self, slices, closed_pattern: int, N: int, return_probs=False):
+        """XEB spoofing: the N strings of the batch closed_pattern with the largest |a|^2
+        over the slice set, in ascending in-batch index order (uint64 numpy); with
+        return_probs, also their |a|^2."""
+        sl = np.ascontiguousarray(np.asarray(slices, dtype=np.uint64))
+        bits = np.zeros(N, dtype=np.uint64)
+        pr = np.zeros(N, dtype=np.float64) if return_probs else None
+        rc = lib().tn_spoof(self.h, _np_ptr(sl), sl.size, int(closed_pattern), int(N), _np_ptr(bits),
+                            _np_ptr(pr) if pr is not None else None)
+        _check(rc, "tn_spoof")
+        return (bits, pr) if return_probs else bits
 
     def sample_step(self, slices, F: float, seed: int, t0: int, alpha: float = 2.0, reuse_stem: bool = False,
                     accept=None, bits=None):
