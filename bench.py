@@ -205,8 +205,7 @@ def workload_config(args):
             "qubits": q, "cycles": w["cycles"], "sliced_legs": w["n_sliced"], "batches_per_step": 1 << log2_batches(args),
             "batch_size": 64, "fidelity_target": args.fidelity, "alpha": 2.0, "order_trials": args.trials,
             "precision": getattr(args, "precision", "c64"), "fuse_root_sum": bool(getattr(args, "fuse_root", 0)),
-            "job": "the timed steps are the batch groups of one sampling job over one slice set: the first "
-                   "runs every contraction, the later ones reuse its batch-independent intermediates",
+            "job": "the timed steps are the batch groups of one sampling job over one slice set",
             "l2": "flushed between timed steps; dominant operands exceed L2"}
 
 
@@ -407,6 +406,8 @@ def run_ours(args):
             "data": "synthetic", "config": workload_config(args),
             "fidelity": F, "contraction_tflops": flops_step * args.steps / (tot_ms / 1e3) / 1e12,
             "flops_per_step": flops_step, "flops_per_group_with_stem": flops_group,
+            "stem": "the job's first group runs every contraction; its later groups reuse the batch-independent "
+                    "intermediates (tn_sample_step reuse_stem)",
             "value_stem_each_step": value_solo, "ms_per_step_stem_each_step": solo_ms_max / args.steps,
             "plan": info, "clocks": clk, "roofline": roofline,
             "cpu_baseline": cpu, "e2e": e2e, "top_steps": top_steps, "slice_sum": slice_sum,
