@@ -10,6 +10,7 @@
 #include <functional>
 #include <map>
 #include <random>
+#include <thread>
 #include <set>
 #include <unordered_map>
 
@@ -1016,7 +1017,7 @@ namespace {
 
 // The tree rebuilt in SSA order after its subtrees were reconfigured (net.q_max must be
 // the tree's threshold).
-bool reconfigured(Network &net, const Tree &t, Tree &out) {
+bool reconfigured(const Network &net, const Tree &t, Tree &out) {
     Tree r = t;
     tn_reconfigure_tree(net, r, 6, 3);
     tn_reconfigure_tree(net, r, 8, 2);
@@ -1038,6 +1039,26 @@ bool reconfigured(Network &net, const Tree &t, Tree &out) {
 }
 
 }  // namespace
+
+// f(i) for every i in [0, n), on up to hardware_concurrency() threads (thread w takes
+// i = w, w + threads, ...).  Callers write results by index and combine them in index
+// order, so the outcome does not depend on the thread count.
+template <typename F>
+static void parallel_for(int n, F f) {
+    const int hw = (int)std::max(1u, std::thread::hardware_concurrency());
+    const int nt = std::min(std::min(hw, 32), n);
+    if (nt <= 1) {
+        for (int i = 0; i < n; i++) f(i);
+        return;
+    }
+    std::vector<std::thread> th;
+    th.reserve((size_t)nt);
+    for (int w = 0; w < nt; w++)
+        th.emplace_back([&f, w, nt, n] {
+            for (int i = w; i < n; i += nt) f(i);
+        });
+    for (auto &x : th) x.join();
+}
 
 void tn_search_tree(Network &net, uint64_t seed, int trials, Tree &best, TreeCost &cost) {
     // batch-selection thresholds to try: -1 (leaves with closed legs in batch form from
@@ -1065,28 +1086,43 @@ void tn_search_tree(Network &net, uint64_t seed, int trials, Tree &best, TreeCos
             tn_greedy_tree(net, seed + 131 * (q + 1), n, tg, cg);
             keep(tg, cg.time);
         }
-        // (networks large enough for the greedy to go wrong also get bisection trials)
-        if (net.leaves.size() >= 48)
+        // (networks large enough for the greedy to go wrong also get bisection trials; their
+        // parameters are drawn in trial order, the trials run in parallel)
+        if (net.leaves.size() >= 48) {
+            std::vector<double> eps((size_t)n);
+            std::vector<int> cutoff((size_t)n);
+            std::vector<uint64_t> tseed((size_t)n);
             for (int tr = 0; tr < n; tr++) {
-                double eps = std::uniform_real_distribution<double>(0.02, 0.6)(rng);
-                int cutoff = 4 + (int)(rng() % 24);
-                Tree tb;
-                tn_bisect_tree(net, rng(), eps, cutoff, tb);
-                keep(tb, tn_tree_cost(net, tb).time);
+                eps[tr] = std::uniform_real_distribution<double>(0.02, 0.6)(rng);
+                cutoff[tr] = 4 + (int)(rng() % 24);
+                tseed[tr] = rng();
             }
+            std::vector<Tree> tb((size_t)n);
+            std::vector<double> tt((size_t)n);
+            const Network &cnet = net;
+            parallel_for(n, [&](int tr) {
+                tn_bisect_tree(cnet, tseed[tr], eps[tr], cutoff[tr], tb[tr]);
+                tt[tr] = tn_tree_cost(cnet, tb[tr]).time;
+            });
+            for (int tr = 0; tr < n; tr++) keep(tb[tr], tt[tr]);
+        }
         // ... each improved locally (optimal orders of its small subtrees), then compared
-        for (auto &cand : top) {
-            Tree tq = cand.second;
-            TreeCost cq = tn_tree_cost(net, tq);
-            if (tq.nodes.size() >= 4) {
+        std::vector<Tree> tq(top.size());
+        std::vector<TreeCost> cq(top.size());
+        const Network &cnet = net;
+        parallel_for((int)top.size(), [&](int i) {
+            tq[i] = top[i].second;
+            cq[i] = tn_tree_cost(cnet, tq[i]);
+            if (tq[i].nodes.size() >= 4) {
                 Tree r;
-                if (reconfigured(net, tq, r)) {
-                    const TreeCost cr = tn_tree_cost(net, r);
-                    if (cr.time < cq.time) { tq = r; cq = cr; }
+                if (reconfigured(cnet, tq[i], r)) {
+                    const TreeCost cr = tn_tree_cost(cnet, r);
+                    if (cr.time < cq[i].time) { tq[i] = r; cq[i] = cr; }
                 }
             }
-            if (!have || cq.time < cost.time) { best = tq; cost = cq; best_q = q; have = true; }
-        }
+        });
+        for (size_t i = 0; i < top.size(); i++)
+            if (!have || cq[i].time < cost.time) { best = tq[i]; cost = cq[i]; best_q = q; have = true; }
     }
     net.q_max = best_q;
 }

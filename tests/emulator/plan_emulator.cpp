@@ -17,7 +17,7 @@
 #include "tn_internal.h"
 #include "planner.cpp"
 
-static std::string g_err;
+static thread_local std::string g_err;
 void tn_set_error(const std::string &m) { g_err = m; }
 void tn_plan_opts_default(tn_plan_opts *o) {
     std::memset(o, 0, sizeof(*o));
