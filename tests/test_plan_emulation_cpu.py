@@ -129,3 +129,11 @@ def test_16q_plans_weighted_for_a_job(emu, job_groups):
     o = opts(log2_batches=4, n_sliced=3, precision=1)
     o.job_groups = job_groups
     check(emu, circ, cg.default_open_qubits(4, 4, 6), o, -2, 1, nb=37, seed=9)
+
+
+def test_20q_groups_of_64_batches(emu):
+    """A 20-qubit plan with 4 sliced legs and 64 batches per group (70 batches: a ragged
+    second group that reuses the stem)."""
+    circ = cg.sycamore_grid(4, 5, 10, seed=3)
+    o = opts(log2_batches=6, n_sliced=4, precision=1)
+    check(emu, circ, cg.default_open_qubits(4, 5, 6), o, -2, 1, nb=70, seed=11)
