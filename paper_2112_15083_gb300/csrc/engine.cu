@@ -90,6 +90,16 @@ void release(DevMem &mem, DBuf &b) {
     b.bytes = 0;
 }
 
+// A buffer released when the scope ends, on error returns too.
+struct ScopedBuf {
+    DevMem &mem;
+    DBuf b;
+    explicit ScopedBuf(DevMem &m) : mem(m) {}
+    ~ScopedBuf() { release(mem, b); }
+    ScopedBuf(const ScopedBuf &) = delete;
+    ScopedBuf &operator=(const ScopedBuf &) = delete;
+};
+
 // Versions and memory layout of one execution of a compiled network on a slice set.
 struct CallPlan {
     std::vector<uint64_t> slices;              // key
@@ -337,16 +347,15 @@ int setup_leaves(DevMem &mem, CNet &cn) {
     }
     // leaves are materialised once per compiled variant and format assignment
     if (!static_descs.empty()) {
-        DBuf tmp;
-        RC(ensure(mem, tmp, static_descs.size() * sizeof(tnk::MatDesc)));
-        CK(cudaMemcpyAsync(tmp.p, static_descs.data(), static_descs.size() * sizeof(tnk::MatDesc),
+        ScopedBuf tmp(mem);
+        RC(ensure(mem, tmp.b, static_descs.size() * sizeof(tnk::MatDesc)));
+        CK(cudaMemcpyAsync(tmp.b.p, static_descs.data(), static_descs.size() * sizeof(tnk::MatDesc),
                            cudaMemcpyHostToDevice, mem.stream));
         dim3 grid(4, (unsigned)static_descs.size());
-        if (cn.elem == 8) tnk::materialize<float2><<<grid, 256, 0, mem.stream>>>((const tnk::MatDesc *)tmp.p);
-        else tnk::materialize<double2><<<grid, 256, 0, mem.stream>>>((const tnk::MatDesc *)tmp.p);
+        if (cn.elem == 8) tnk::materialize<float2><<<grid, 256, 0, mem.stream>>>((const tnk::MatDesc *)tmp.b.p);
+        else tnk::materialize<double2><<<grid, 256, 0, mem.stream>>>((const tnk::MatDesc *)tmp.b.p);
         CK(cudaGetLastError());
         CK(cudaStreamSynchronize(mem.stream));
-        release(mem, tmp);
     }
     cn.cp.valid = false;
     CK(cudaStreamSynchronize(mem.stream));
@@ -1457,7 +1466,9 @@ int tn_plan(tn_circuit_h c, const int32_t *order, int32_t n_order, const tn_edge
 void tn_plan_destroy(tn_plan_h p) {
     if (!p) return;
     free_cnet(p->mem, p->amp);
-    for (DBuf *b : {&p->d_closed, &p->d_amps, &p->d_j, &p->d_acc, &p->d_pick, &p->d_eps, &p->d_bits, &p->d_R, &p->d_X})
+    for (DBuf *b : {&p->d_closed, &p->d_amps, &p->d_j, &p->d_acc, &p->d_pick, &p->d_eps, &p->d_bits, &p->d_R, &p->d_X,
+                    &p->d_xidx, &p->d_xamps, &p->d_xsum, &p->d_skey, &p->d_shist, &p->d_sgt, &p->d_seq, &p->d_sbits,
+                    &p->d_sprob})
         release(p->mem, *b);
     cudaStreamSynchronize(p->mem.stream);
     delete p;
