@@ -12,6 +12,7 @@ arXiv:2112.15083 (Kalachev, Panteleev, Zhou, Yung):
 * SlicedVertexSelect (Alg. 2) and Slice selection (Alg. 1);
 * linear XEB (Eq. 1) and the modified frugal rejection sampler (Sec. II.A);
 * the XEB spoofing recipe (Sec. III, "Spoofing Linear XEB"; App. A);
+* the cost model: C_s(f) = |X|/2^k C_s(1) (Sec. I.B) and the time estimate of Sec. III.A;
 * the sampler's output law, variation distance and fidelity bound (Sec. II.B);
 * the expected rejection loss under Porter-Thomas statistics (Sec. II.C).
 
@@ -479,3 +480,17 @@ def spoof_expected_xeb(f: float, r: float) -> float:
     """Eq. spoof-xeb (App. A): for a Porter-Thomas batch computed at fidelity f, the N = r |B|
     strings of largest approximate probability have E XEB = -f ln r, up to O(ln N / N)."""
     return -f * math.log(r)
+
+
+# ------------------------------------------------------------------ cost model
+
+def sliced_cost(c_full: float, n_retained: int, k: int) -> float:
+    """Sec. I.B: contracting the retained partial assignments X of k legs costs
+    C_s(f) = |X| / 2^k C_s(1)."""
+    return c_full * n_retained / float(1 << k)
+
+
+def sampling_time(flops_full: float, fidelity: float, peak_flops: float, efficiency: float) -> float:
+    """Sec. III.A's estimate: the full contraction's FLOPs scaled by the fidelity, over the
+    machine's peak times its efficiency (seconds)."""
+    return flops_full * fidelity / (peak_flops * efficiency)

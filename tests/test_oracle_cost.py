@@ -1,0 +1,35 @@
+"""Pins of the oracle's cost model: the paper's own arithmetic for the Zuchongzhi
+estimate (Sec. III.A), and the bound C_s(f) = |X|/2^k C_s(1) <= ceil(2^k f)/2^k C_s(1)
+< (f + 2^-k) C_s(1) (Sec. I.B) for Alg. 1's selections on random norm vectors."""
+import json
+import math
+import os
+
+import numpy as np
+import pytest
+
+import oracle
+
+GOLDEN = json.load(open(os.path.join(os.path.dirname(__file__), "golden", "paper_examples.json")))
+
+
+def test_zuchongzhi_estimate_reproduces_the_printed_time():
+    g = GOLDEN["zuchongzhi_estimate_sec_IIIA"]
+    t = oracle.sampling_time(g["flops_full"], g["fidelity"], g["peak_flops"], g["efficiency"])
+    assert abs(t - g["seconds_printed"]) < 0.01 * g["seconds_printed"]  # printed rounded to 3.6e5
+    assert round(t / 86400) == 4  # "about 4 days"
+
+
+@pytest.mark.parametrize("k", [3, 6, 9])
+@pytest.mark.parametrize("f", [0.002, 1 / 64, 0.1, 0.5])
+def test_sliced_cost_bound(k, f):
+    """Sec. I.B, with X from Alg. 1's cut of Dirichlet-random norms (they sum to 1)."""
+    assert "C_s(f)" in GOLDEN["cost_bound_sec_IB"]["_cite"]
+    rng = np.random.default_rng(k * 1000 + int(1e4 * f))
+    for _ in range(20):
+        R = rng.dirichlet(np.full(1 << k, 0.3))
+        X, F = oracle.select_slices(R, f)
+        c = oracle.sliced_cost(1.0, len(X), k)
+        assert c <= math.ceil((1 << k) * f) / (1 << k) + 1e-15
+        assert c < f + 2.0 ** -k
+        assert F >= min(f, 1.0) - 1e-12 or len(X) == (1 << k)
