@@ -33,3 +33,25 @@ def test_sliced_cost_bound(k, f):
         assert c <= math.ceil((1 << k) * f) / (1 << k) + 1e-15
         assert c < f + 2.0 ** -k
         assert F >= min(f, 1.0) - 1e-12 or len(X) == (1 << k)
+
+
+SECONDS = {"hours": 3600.0, "days": 86400.0, "months": 86400.0 * 365.25 / 12}
+
+
+def test_sampling_table_rows_share_one_peak():
+    """Sec. III.A's table: every row's time is 8 C_s over one GPU's peak times the row's
+    efficiency; the implied peak (about 14 TFLOP/s, a V100's FP32 rate) agrees across the
+    rows to 5%.  And F >= the slicing ratio |X|/2^k (Sec. I.B) and >= the target."""
+    rows = GOLDEN["sampling_complexity_table_sec_IIIA"]["rows"]
+    peaks = []
+    for r in rows:
+        t = r["time"][0] * SECONDS[r["time"][1]]
+        peaks.append(8.0 * r["C_s"] / (t * r["efficiency"]))
+        assert r["F"] >= r["ratio"] and r["F"] >= r["target"]
+    mean = sum(peaks) / len(peaks)
+    assert 13e12 < mean < 15e12
+    assert max(abs(x / mean - 1.0) for x in peaks) < 0.05
+    # the oracle's time formula at the implied peak reproduces every printed time to 5%
+    for r in rows:
+        t = oracle.sampling_time(8.0 * r["C_s"], 1.0, mean, r["efficiency"])
+        assert abs(t / (r["time"][0] * SECONDS[r["time"][1]]) - 1.0) < 0.05
