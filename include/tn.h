@@ -95,6 +95,9 @@ typedef struct {
     int32_t job_groups;      /* batch groups per sampling job that the order search
                                 optimises for: a batch-independent step runs once per
                                 job, the others once per group; <= 1 (default): one */
+    int32_t anneal_iters;    /* order search: simulated-annealing moves (tree rotations,
+                                Metropolis on the log of the estimated time) applied to
+                                the winning tree, kept only if cheaper; 0 (default): none */
     void *stream;            /* cudaStream_t; NULL = legacy default stream */
     tn_alloc_fn alloc;       /* optional device allocator */
     tn_free_fn free;

@@ -1060,6 +1060,77 @@ static void parallel_for(int n, F f) {
     for (auto &x : th) x.join();
 }
 
+// Simulated annealing of the tree's shape: rotations x = (y, z), y = (a, b) -> x = (a, (b, z))
+// or (b, (a, z)) at random internal nodes, accepted by the Metropolis rule on the log of the
+// estimated time, with the temperature falling geometrically from 0.3 to 0.003 over `iters`
+// moves.  Every candidate is rebuilt in SSA order (so its indices, batch flags and versions
+// are exact for the threshold net.q_max); the cheapest tree seen replaces t.
+void tn_anneal_tree(const Network &net, Tree &t, int iters, uint64_t seed) {
+    const int L = (int)net.leaves.size();
+    if (iters <= 0 || t.root < 0 || L < 4) return;
+    std::vector<std::array<int, 2>> ch(t.nodes.size());
+    for (size_t x = 0; x < t.nodes.size(); x++) ch[x] = {t.nodes[x].ch[0], t.nodes[x].ch[1]};
+    const int root = t.root;
+    auto rebuild = [&](Tree &out) -> bool {
+        std::vector<int> order;  // internal nodes in post-order
+        std::vector<std::pair<int, int>> stk{{root, 0}};
+        while (!stk.empty()) {
+            const int x = stk.back().first, st = stk.back().second;
+            if (x < L) { stk.pop_back(); continue; }
+            if (st < 2) {
+                stk.back().second = st + 1;
+                stk.push_back({ch[x][st], 0});
+                continue;
+            }
+            order.push_back(x);
+            stk.pop_back();
+        }
+        std::vector<int> newid(ch.size(), -1);
+        for (int i = 0; i < L; i++) newid[i] = i;
+        std::vector<int32_t> pairs;
+        int next = L;
+        for (int x : order) {
+            pairs.push_back(newid[ch[x][0]]);
+            pairs.push_back(newid[ch[x][1]]);
+            newid[x] = next++;
+        }
+        return tn_tree_from_ssa(net, pairs.data(), (int)pairs.size() / 2, out) == TN_OK;
+    };
+    std::mt19937_64 rng(seed * 0x9E3779B97F4A7C15ull + 4242);
+    std::uniform_real_distribution<double> U(0.0, 1.0);
+    double cur = tn_tree_cost(net, t).time, best_cost = cur;
+    Tree best = t;
+    const int n_int = (int)ch.size() - L;
+    for (int it = 0; it < iters; it++) {
+        const double temp = 0.3 * std::pow(0.01, (double)it / iters);
+        int x = -1;
+        for (int tries = 0; tries < 64 && x < 0; tries++) {
+            const int c = L + (int)(rng() % (uint64_t)n_int);
+            if (ch[c][0] >= L || ch[c][1] >= L) x = c;
+        }
+        if (x < 0) break;
+        int side = ch[x][0] >= L ? 0 : 1;
+        if (ch[x][0] >= L && ch[x][1] >= L) side = (int)(rng() & 1);
+        const int y = ch[x][side], z = ch[x][1 - side];
+        const int r = (int)(rng() & 1);
+        const std::array<int, 2> old_x = ch[x], old_y = ch[y];
+        ch[y] = {old_y[1 - r], z};
+        ch[x] = {old_y[r], y};
+        Tree cand;
+        const bool ok = rebuild(cand);
+        const double c = ok ? tn_tree_cost(net, cand).time : 0.0;
+        const double d = ok ? std::log(c) - std::log(cur) : 1e300;
+        if (ok && (d <= 0 || U(rng) < std::exp(-d / temp))) {
+            cur = c;
+            if (c < best_cost) { best_cost = c; best = cand; }
+        } else {
+            ch[x] = old_x;
+            ch[y] = old_y;
+        }
+    }
+    t = best;
+}
+
 void tn_search_tree(Network &net, uint64_t seed, int trials, Tree &best, TreeCost &cost) {
     // batch-selection thresholds to try: -1 (leaves with closed legs in batch form from
     // the start; all trials), then log2 T / 2 and log2 T (half the trials each)
@@ -1125,6 +1196,15 @@ void tn_search_tree(Network &net, uint64_t seed, int trials, Tree &best, TreeCos
             if (!have || cq[i].time < cost.time) { best = tq[i]; cost = cq[i]; best_q = q; have = true; }
     }
     net.q_max = best_q;
+    // optional: anneal the winner's shape, then reconfigure its small subtrees again
+    if (net.anneal_iters > 0 && have) {
+        Tree a = best;
+        tn_anneal_tree(net, a, net.anneal_iters, seed);
+        Tree r;
+        if (a.nodes.size() >= 4 && reconfigured(net, a, r) && tn_tree_cost(net, r).time < tn_tree_cost(net, a).time) a = r;
+        const TreeCost ca = tn_tree_cost(net, a);
+        if (ca.time < cost.time) { best = a; cost = ca; }
+    }
 }
 
 // Slice network index `id` in a tree: it leaves every tensor, and every tensor above a
@@ -1395,6 +1475,7 @@ void tn_cost_settings(Network &net, const tn_plan_opts &o) {
     const double budget = o.hbm_budget_bytes > 0 ? o.hbm_budget_bytes : 64.0 * (1ull << 30);
     net.mem_limit_elems = budget / 8.0 / 2.0;
     net.job_groups = o.job_groups > 1 ? (double)o.job_groups : 1.0;
+    net.anneal_iters = std::max(0, o.anneal_iters);
 }
 
 int tn_tree_and_compile(Network &net, const tn_plan_opts &o, const int32_t *order, int n_order,

@@ -87,6 +87,7 @@ struct Network {
     double tc_flop_rate = 0;
     double mem_limit_elems = 0;
     double job_groups = 1;  // batch groups per job: the cost weight of batch steps
+    int anneal_iters = 0;   // order search: annealing moves applied to the winning tree
     int n_sliced = 0;              // |I|
     std::vector<int> idx_seg;      // segment id of each network index (-1: beta / other)
 };
@@ -174,6 +175,7 @@ void tn_bisect_tree(const Network &net, uint64_t seed, double eps, int cutoff, T
 void tn_search_tree(Network &net, uint64_t seed, int trials, Tree &best, TreeCost &cost);
 // Replace each subtree cut at up to k frontier tensors by its cheapest order (subset DP).
 void tn_reconfigure_tree(const Network &net, Tree &t, int k, int passes);
+void tn_anneal_tree(const Network &net, Tree &t, int iters, uint64_t seed);
 TreeCost tn_tree_cost(const Network &net, const Tree &t);
 void tn_recompute_deps(const Network &net, Tree &t);
 std::vector<int> tn_auto_slice(const Merged &mg, Network &net, Tree &t, int n_slice);

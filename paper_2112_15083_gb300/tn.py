@@ -84,6 +84,7 @@ class PlanOpts(ctypes.Structure):
         ("autotune", ctypes.c_int32),
         ("fuse_root_sum", ctypes.c_int32),
         ("job_groups", ctypes.c_int32),
+        ("anneal_iters", ctypes.c_int32),
         ("stream", ctypes.c_void_p),
         ("alloc", ALLOC_FN),
         ("free", FREE_FN),
@@ -239,7 +240,7 @@ class Plan:
     def __init__(self, circuit: Circuit, open_qubits, sliced=None, order=None, precision=PREC_C64,
                  log2_batches=8, order_seed=0, order_trials=64, n_auto_sliced=0,
                  hbm_budget_bytes=0.0, stream=None, use_torch_allocator=True, max_norm_flops=0.0,
-                 autotune=None, max_log2_tensor=0, fuse_root_sum=False, job_groups=1):
+                 autotune=None, max_log2_tensor=0, fuse_root_sum=False, job_groups=1, anneal_iters=0):
         L = lib()
         o = PlanOpts()
         L.tn_plan_opts_default(ctypes.byref(o))
@@ -257,6 +258,7 @@ class Plan:
             o.autotune = int(autotune)
         o.fuse_root_sum = int(bool(fuse_root_sum))
         o.job_groups = int(job_groups)
+        o.anneal_iters = int(anneal_iters)
         o.stream = _stream_ptr(stream)
         self._alloc = None
         if use_torch_allocator:
@@ -425,7 +427,7 @@ class Plan:
 
 def plan_host(circuit: Circuit, open_qubits, sliced=None, order=None, log2_batches=8, order_seed=0,
               order_trials=64, n_auto_sliced=0, precision=PREC_C64, max_log2_tensor=0, hbm_budget_bytes=0.0,
-              job_groups=1):
+              job_groups=1, anneal_iters=0):
     """Host-only planning (no GPU): (info dict, steps array (n_steps, 7), sliced edges).
     Step row: batch, m, n, k bits, log2 versions of C, A, B."""
     L = lib()
@@ -440,6 +442,7 @@ def plan_host(circuit: Circuit, open_qubits, sliced=None, order=None, log2_batch
     if hbm_budget_bytes:
         o.hbm_budget_bytes = hbm_budget_bytes
     o.job_groups = int(job_groups)
+    o.anneal_iters = int(anneal_iters)
     openq = np.ascontiguousarray(np.asarray(open_qubits, dtype=np.int32))
     if sliced is not None:
         arr = (Edge * max(1, len(sliced)))(*[Edge(int(q), int(s)) for (q, s) in sliced])

@@ -137,3 +137,13 @@ def test_20q_groups_of_64_batches(emu):
     circ = cg.sycamore_grid(4, 5, 10, seed=3)
     o = opts(log2_batches=6, n_sliced=4, precision=1)
     check(emu, circ, cg.default_open_qubits(4, 5, 6), o, -2, 1, nb=70, seed=11)
+
+
+@pytest.mark.parametrize("seed", [0, 1])
+def test_annealed_plans(emu, seed):
+    """Plans whose winning tree was reshaped by simulated annealing (tree rotations): at
+    3x5, 12 cycles the annealed tree differs (5.7e7 instead of 8.3e7 FLOPs per slice)."""
+    circ = cg.sycamore_grid(3, 5, 12, seed=seed)
+    o = opts(log2_batches=4, n_sliced=3, precision=1)
+    o.anneal_iters = 3000
+    check(emu, circ, cg.default_open_qubits(3, 5, 6), o, -2, 1, nb=21, seed=seed + 40)
