@@ -1196,14 +1196,23 @@ void tn_search_tree(Network &net, uint64_t seed, int trials, Tree &best, TreeCos
             if (!have || cq[i].time < cost.time) { best = tq[i]; cost = cq[i]; best_q = q; have = true; }
     }
     net.q_max = best_q;
-    // optional: anneal the winner's shape, then reconfigure its small subtrees again
+    // optional: anneal the winner's shape from 8 independent seeds (in parallel), reconfigure
+    // each result's small subtrees again, and keep the cheapest (first in seed order on ties)
     if (net.anneal_iters > 0 && have) {
-        Tree a = best;
-        tn_anneal_tree(net, a, net.anneal_iters, seed);
-        Tree r;
-        if (a.nodes.size() >= 4 && reconfigured(net, a, r) && tn_tree_cost(net, r).time < tn_tree_cost(net, a).time) a = r;
-        const TreeCost ca = tn_tree_cost(net, a);
-        if (ca.time < cost.time) { best = a; cost = ca; }
+        constexpr int kRestarts = 8;
+        std::vector<Tree> a((size_t)kRestarts, best);
+        std::vector<double> ta((size_t)kRestarts, 0.0);
+        const Network &cnet = net;
+        parallel_for(kRestarts, [&](int i) {
+            tn_anneal_tree(cnet, a[i], cnet.anneal_iters, seed + 7919 * (uint64_t)i);
+            Tree r;
+            if (a[i].nodes.size() >= 4 && reconfigured(cnet, a[i], r) &&
+                tn_tree_cost(cnet, r).time < tn_tree_cost(cnet, a[i]).time)
+                a[i] = r;
+            ta[i] = tn_tree_cost(cnet, a[i]).time;
+        });
+        for (int i = 0; i < kRestarts; i++)
+            if (ta[i] < cost.time) { best = a[i]; cost = tn_tree_cost(net, a[i]); }
     }
 }
 
