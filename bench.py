@@ -140,14 +140,22 @@ class Clocks:
 
 # ---------------------------------------------------------------- oracle baseline
 
-def oracle_step(circ, openq, T, seed, t0, alpha=2.0):
-    """The oracle on one step of the workload: the FP64 state vector (the whole circuit),
-    then the Sec. II.A step on T batches with the same Philox draws.  Returns accepted."""
+def oracle_probs(circ):
+    """The oracle's batch-independent part of a sampling job: the FP64 state vector of the
+    whole circuit, as output probabilities."""
     import numpy as np
     import oracle
     psi = oracle.simulate(circ)
     p = np.abs(psi) ** 2
     del psi
+    return p
+
+
+def oracle_group(p, circ, openq, T, seed, t0, alpha=2.0):
+    """The oracle on one batch group: the Sec. II.A step on T batches with the same Philox
+    draws as the GPU path.  Returns the accepted count."""
+    import numpy as np
+    import oracle
     b_bits = circ.n_qubits - len(openq)
     js = oracle.batch_draws(seed, T, b_bits, t0=t0)
     pb = np.ascontiguousarray(oracle.batch_amplitudes(p, circ.n_qubits, openq, js))
@@ -173,12 +181,18 @@ def run_reference(args):
     circ = cg.sycamore_grid(w["rows"], w["cols"], w["cycles"], seed=w["seed"])
     openq = cg.default_open_qubits(w["rows"], w["cols"], w["n_open"])
     T = 1 << log2_batches(args)
+    # warm-up: a job of its own (state vector, then the warm-up groups)
+    p = oracle_probs(circ)
     for i in range(args.warmup):
-        oracle_step(circ, openq, T, args.seed, i * T)
+        oracle_group(p, circ, openq, T, args.seed, i * T)
+    del p
+    # the timed job: its state vector once, then its groups (as the GPU arm's job computes
+    # its batch-independent intermediates once)
     t = time.perf_counter()
+    p = oracle_probs(circ)
     acc = 0
     for k in range(args.steps):
-        acc += oracle_step(circ, openq, T, args.seed, (args.warmup + k) * T)
+        acc += oracle_group(p, circ, openq, T, args.seed, (args.warmup + k) * T)
     dt = time.perf_counter() - t
     val = acc / dt
     cores = cpu_cores()
@@ -188,8 +202,8 @@ def run_reference(args):
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
         "config": workload_config(args),
         "cpu_baseline": {"value": val, "unit": "samples/s", "cores": cores, "kind": "oracle",
-                         "sample": "per step: FP64 state vector of the %d-qubit circuit + the sampler on %d batches" % (
-                             circ.n_qubits, T)},
+                         "sample": "a job of %d groups: the FP64 state vector of the %d-qubit circuit once, then "
+                                   "the sampler on %d batches per group" % (args.steps, circ.n_qubits, T)},
         "e2e": {"value": val, "unit": "samples/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line), flush=True)
@@ -390,11 +404,13 @@ def run_ours(args):
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         os.environ.setdefault("OMP_NUM_THREADS", str(cpu_cores()))
         t = time.perf_counter()
-        a = oracle_step(circ, openq, T, seed, 0)
+        p = oracle_probs(circ)
+        a = sum(oracle_group(p, circ, openq, T, seed, g * T) for g in range(3))
+        del p
         dt = time.perf_counter() - t
         cpu = {"value": a / dt, "unit": "samples/s", "cores": int(os.environ["OMP_NUM_THREADS"]), "kind": "oracle",
-               "sample": "one step: FP64 state vector of the %d-qubit circuit + the sampler on %d batches "
-                         "(%d accepted in %.1f s)" % (circ.n_qubits, T, a, dt)}
+               "sample": "a job of 3 groups: the FP64 state vector of the %d-qubit circuit once, then the sampler "
+                         "on %d batches per group (%d accepted in %.1f s)" % (circ.n_qubits, T, a, dt)}
 
     if rank == 0:
         line = {
