@@ -140,6 +140,8 @@ void planner_loop(tn_server_s *s) {
             const double want = 1.1 * r->alpha * (double)r->N;
             while (lb < s->o.max_log2_batches && std::ldexp(1.0, lb) < want) lb++;
             po.log2_batches = lb;
+            // the order search minimises the request's whole job: its expected groups
+            po.job_groups = (int32_t)std::max(1.0, std::ceil(want / std::ldexp(1.0, lb)));
             po.autotune = 0;
             po.order_trials = s->o.order_trials;
             po.n_auto_sliced = r->n_sliced;

@@ -4,6 +4,8 @@ GPU tests: a request's samples are bit-identical alone, in a mix of concurrent r
 (other circuits, precisions and fidelities) and through tn_sample; admission respects the
 budget; oversized requests are rejected.  CPU test: a request that fails (no device)
 leaves the server consistent."""
+import math
+
 import numpy as np
 import pytest
 
@@ -75,14 +77,15 @@ def test_same_alone_in_the_mix_and_via_tn_sample():
     assert st["done"] == 5
 
     # the server sizes the group to the request (the smallest 2^lb >= 1.1 alpha N within
-    # [2^8, 2^14]), uses the fixed kernel shape rules, and hands its memory budget to the
-    # order search's cost model
+    # [2^8, 2^14]), uses the fixed kernel shape rules, hands its memory budget to the order
+    # search's cost model and weights the batch steps by the request's expected groups
     lb = 8
     while lb < 14 and (1 << lb) < 1.1 * 2.0 * N:
         lb += 1
+    job_groups = max(1, math.ceil(1.1 * 2.0 * N / (1 << lb)))
     C = P.circuit_load(buf)
     plan = P.plan(C, openq, n_auto_sliced=4, log2_batches=lb, order_trials=64, precision=P.tn.PREC_BF16X2,
-                  autotune=0, hbm_budget_bytes=150e9)
+                  autotune=0, hbm_budget_bytes=150e9, job_groups=job_groups)
     via_plan, _ = plan.sample(1.0, N, seed=42)
     assert np.array_equal(via_plan, ref)
 
