@@ -57,6 +57,8 @@ def parse():
     ap.add_argument("--workload", default="grid4x7_m14", choices=sorted(WORKLOADS))
     ap.add_argument("--log2-batches", type=int, default=None, help="batches per step = 2^this (default: the workload's)")
     ap.add_argument("--autotune", type=int, default=1, help="kernel autotuning (1) or the fixed shape rules (0)")
+    ap.add_argument("--anneal", type=int, default=0,
+                    help="order search: simulated-annealing moves on the winning tree (tn_plan_opts.anneal_iters)")
     ap.add_argument("--fuse-root", type=int, default=0,
                     help="1: run a row-kernel root step fused with the FP64 slice sum (tn_plan_opts.fuse_root_sum)")
     ap.add_argument("--serve", action="store_true", help="serving run (Poisson request stream) instead of the step bench")
@@ -219,6 +221,7 @@ def workload_config(args):
             "qubits": q, "cycles": w["cycles"], "sliced_legs": w["n_sliced"], "batches_per_step": 1 << log2_batches(args),
             "batch_size": 64, "fidelity_target": args.fidelity, "alpha": 2.0, "order_trials": args.trials,
             "precision": getattr(args, "precision", "c64"), "fuse_root_sum": bool(getattr(args, "fuse_root", 0)),
+            "anneal_iters": int(getattr(args, "anneal", 0)),
             "job": "the timed steps are the batch groups of one sampling job over one slice set",
             "l2": "flushed between timed steps; dominant operands exceed L2"}
 
@@ -244,7 +247,7 @@ def run_ours(args):
     prec = {"c64": P.tn.PREC_C64, "bf16x2": P.tn.PREC_BF16X2}[args.precision]
     plan = P.plan(C, openq, n_auto_sliced=w["n_sliced"], log2_batches=log2_batches(args), order_trials=args.trials,
                   order_seed=0, hbm_budget_bytes=200e9, precision=prec, autotune=args.autotune,
-                  fuse_root_sum=bool(args.fuse_root))
+                  fuse_root_sum=bool(args.fuse_root), anneal_iters=args.anneal)
     info = plan.info()
     slices, F = plan.select(args.fidelity)
     T = 1 << log2_batches(args)
