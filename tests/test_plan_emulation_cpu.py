@@ -147,3 +147,10 @@ def test_annealed_plans(emu, seed):
     o = opts(log2_batches=4, n_sliced=3, precision=1)
     o.anneal_iters = 3000
     check(emu, circ, cg.default_open_qubits(3, 5, 6), o, -2, 1, nb=21, seed=seed + 40)
+
+
+def test_12q_no_open_qubits(emu):
+    """Every qubit closed: one amplitude per batch (the verification workload's plans)."""
+    circ = cg.sycamore_grid(3, 4, 8, seed=2)
+    o = opts(log2_batches=4, n_sliced=2, precision=1)
+    check(emu, circ, [], o, -2, 1, nb=37, seed=3)
