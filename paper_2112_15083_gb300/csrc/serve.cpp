@@ -27,6 +27,7 @@
 #include <vector>
 
 #include "tn.h"
+#include "serve_policy.h"
 
 namespace {
 
@@ -220,25 +221,33 @@ void sched_loop(tn_server_s *s) {
             if (s->active.empty())
                 s->cv_sched.wait(lk, [&] { return s->stop || !s->planned.empty(); });
             if (s->stop && s->active.empty()) return;
-            // admission: first fit within the budget and the slot count, shortest estimated
-            // job first, a request's estimate reduced by the time it has waited (so long
-            // jobs are not starved)
-            {
-                const double tn = now_s(s->t0);
-                std::stable_sort(s->planned.begin(), s->planned.end(),
-                                 [&](const std::shared_ptr<Req> &x, const std::shared_ptr<Req> &y) {
-                                     return x->est_s - (tn - x->t_submit) < y->est_s - (tn - y->t_submit);
-                                 });
-            }
-            for (auto it = s->planned.begin(); it != s->planned.end();) {
-                Req &r = **it;
-                if ((int)s->active.size() >= s->o.max_active) break;
-                if (s->bytes_in_use + (double)r.est_bytes > s->o.hbm_budget_bytes) { ++it; continue; }
-                s->bytes_in_use += (double)r.est_bytes;
-                r.status = TN_REQ_ACTIVE;
-                r.t_admit = now_s(s->t0);
-                s->active.push_back(*it);
-                it = s->planned.erase(it);
+            // admission (serve_policy.h): shortest estimated job first, aged by waiting
+            // time, first fit within the budget and the slot count
+            if (!s->planned.empty()) {
+                const int n = (int)s->planned.size();
+                std::vector<double> est(n), sub(n), bytes(n);
+                for (int i = 0; i < n; i++) {
+                    est[i] = s->planned[i]->est_s;
+                    sub[i] = s->planned[i]->t_submit;
+                    bytes[i] = (double)s->planned[i]->est_bytes;
+                }
+                std::vector<int> order(n), admit(n);
+                tn_admission(n, est.data(), sub.data(), bytes.data(), now_s(s->t0), s->o.hbm_budget_bytes,
+                             s->bytes_in_use, (int)s->active.size(), s->o.max_active, order.data(), admit.data());
+                std::deque<std::shared_ptr<Req>> rest;
+                for (int k = 0; k < n; k++) {
+                    const int i = order[k];
+                    auto &rp = s->planned[i];
+                    if (admit[i]) {
+                        s->bytes_in_use += (double)rp->est_bytes;
+                        rp->status = TN_REQ_ACTIVE;
+                        rp->t_admit = now_s(s->t0);
+                        s->active.push_back(rp);
+                    } else {
+                        rest.push_back(rp);
+                    }
+                }
+                s->planned.assign(rest.begin(), rest.end());
             }
         }
         bool idle = true;
