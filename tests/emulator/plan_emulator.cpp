@@ -16,6 +16,7 @@
 
 #include "tn_internal.h"
 #include "planner.cpp"
+#include "arena.h"
 
 static thread_local std::string g_err;
 void tn_set_error(const std::string &m) { g_err = m; }
@@ -214,4 +215,94 @@ extern "C" int emu_contract(const void *circ, size_t len, const int32_t *open, i
             }
     }
     return TN_OK;
+}
+
+// The engine's arena layout for the compiled plan and slice set, checked: tensors live in
+// the same step never overlap (an internal tensor lives from the step that writes it to
+// the step that reads it, the root to the end, a gathered operand for its own step); the
+// stem kept for later batch groups overlaps no other tensor at any time; every range ends
+// within arena_bytes.  Returns the number of violations (negative: planning failed).
+extern "C" int emu_layout_check(const void *circ, size_t len, const int32_t *open, int n_open, const tn_plan_opts *o,
+                                int q_max, int tc, const uint64_t *slices, int n_slices, int64_t *arena_out) {
+    tn_circuit_s c;
+    if (tn_parse_circuit(circ, len, &c)) return -1;
+    Merged mg;
+    tn_merge(c, mg);
+    std::vector<int> openv(open, open + n_open), closed;
+    std::vector<tn_edge> I;
+    Network net;
+    Tree tree;
+    std::vector<Step> steps;
+    uint64_t E0 = 0;
+    if (tn_plan_build_host(mg, *o, nullptr, 0, nullptr, 0, openv, I, net, tree, steps, closed, &E0)) return -1;
+    if (q_max >= -1) {
+        net.q_max = q_max;
+        tree.q_max = q_max;
+        tn_recompute_deps(net, tree);
+    }
+    const std::vector<uint64_t> sv(slices, slices + n_slices);
+    const uint64_t E = emu_explicit_legs(sv, (int)I.size());
+    if (tn_compile(net, tree, E, steps, tc != 0)) return -1;
+    CallLayout L;
+    layout_call(tree, steps, E, 8, sv, L);
+    *arena_out = (int64_t)L.arena_bytes;
+    const auto &nodes = tree.nodes;
+    const int NN = (int)nodes.size(), S = (int)steps.size();
+    auto bytes_of = [&](int x) { return (size_t)L.nver[x] * (size_t(1) << nodes[x].layout.size()) * 8; };
+    auto nver_of = [&](int x) -> long long {
+        return nodes[x].ch[0] >= 0 ? L.nver[x] : 1LL << __builtin_popcountll(nodes[x].dep & E);
+    };
+    std::vector<int> born(NN, -1), dies(NN, -1);
+    std::vector<char> kept(NN, 0);
+    for (int i = 0; i < S; i++) {
+        const Step &s = steps[i];
+        born[s.c] = i;
+        for (int ch : {s.a, s.b}) {
+            dies[ch] = i;
+            if (nodes[ch].ch[0] >= 0 && !nodes[ch].beta && nodes[s.c].beta) kept[ch] = 1;
+        }
+    }
+    dies[tree.root] = S;
+    struct R { size_t lo, hi; int tag; };
+    int bad = 0;
+    auto overlap = [](const R &a, const R &b) { return a.lo < b.hi && b.lo < a.hi; };
+    std::vector<R> kept_r, other_r;
+    for (int x = 0; x < NN; x++)
+        if (nodes[x].ch[0] >= 0 && born[x] >= 0) {
+            const R r{L.off[x], L.off[x] + bytes_of(x), x};
+            if (r.hi > L.arena_bytes) bad++;
+            (kept[x] ? kept_r : other_r).push_back(r);
+        }
+    for (int i = 0; i < S; i++)
+        for (int o2 = 0; o2 < 2; o2++)
+            if (steps[i].gat[o2]) {
+                const int x = o2 ? steps[i].b : steps[i].a;
+                const R r{L.goff[i][o2], L.goff[i][o2] + (size_t)nver_of(x) * (size_t(1) << steps[i].g_nbits[o2]) * 8,
+                          -1 - i};
+                if (r.hi > L.arena_bytes) bad++;
+                other_r.push_back(r);
+            }
+    for (const R &k : kept_r) {
+        for (const R &k2 : kept_r)
+            if (k.tag < k2.tag && overlap(k, k2)) bad++;
+        for (const R &r : other_r)
+            if (overlap(k, r)) bad++;
+    }
+    // per step: the tensors and gathered operands live in it are disjoint
+    for (int i = 0; i < S; i++) {
+        std::vector<R> live;
+        for (int x = 0; x < NN; x++)
+            if (nodes[x].ch[0] >= 0 && born[x] >= 0 && !kept[x] && born[x] <= i && i <= dies[x])
+                live.push_back({L.off[x], L.off[x] + bytes_of(x), x});
+        for (int o2 = 0; o2 < 2; o2++)
+            if (steps[i].gat[o2]) {
+                const int x = o2 ? steps[i].b : steps[i].a;
+                live.push_back({L.goff[i][o2], L.goff[i][o2] + (size_t)nver_of(x) * (size_t(1) << steps[i].g_nbits[o2]) * 8,
+                                -1 - i - 1000000 * o2});
+            }
+        for (size_t u = 0; u < live.size(); u++)
+            for (size_t v = u + 1; v < live.size(); v++)
+                if (overlap(live[u], live[v])) bad++;
+    }
+    return bad;
 }

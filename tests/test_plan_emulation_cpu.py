@@ -154,3 +154,36 @@ def test_12q_no_open_qubits(emu):
     circ = cg.sycamore_grid(3, 4, 8, seed=2)
     o = opts(log2_batches=4, n_sliced=2, precision=1)
     check(emu, circ, [], o, -2, 1, nb=37, seed=3)
+
+
+def layout_violations(emu, circ, openq, o, q_max, tc, slices):
+    buf = circ.serialize()
+    openv = np.ascontiguousarray(np.asarray(openq, dtype=np.int32))
+    sl = np.ascontiguousarray(np.asarray(slices, dtype=np.uint64))
+    arena = ctypes.c_int64()
+    emu.emu_layout_check.argtypes = [ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p, ctypes.c_int32,
+                                     ctypes.c_void_p, ctypes.c_int32, ctypes.c_int32, ctypes.c_void_p,
+                                     ctypes.c_int32, ctypes.POINTER(ctypes.c_int64)]
+    bad = emu.emu_layout_check(buf, len(buf), openv.ctypes.data, openv.size, ctypes.byref(o), q_max, tc,
+                               sl.ctypes.data, sl.size, ctypes.byref(arena))
+    assert bad >= 0, emu.emu_error().decode()
+    return bad, arena.value
+
+
+ARENA_CASES = [(r, c, m, lb, ns, q) for (r, c, m, lb, ns) in [(3, 4, 8, 2, 3), (4, 4, 10, 4, 4), (4, 5, 10, 6, 4)]
+               for q in (-2, -1, 6)] + [(4, 7, 14, 14, 10, -2)]
+
+
+@pytest.mark.parametrize("rows,cols,cycles,log2_batches,n_sliced,q_max", ARENA_CASES)
+def test_arena_layout_invariants(emu, rows, cols, cycles, log2_batches, n_sliced, q_max):
+    """The engine's arena plan (arena.h) for these plans: live tensors disjoint in every
+    step, the kept stem disjoint from everything, all within the arena (up to the 28-qubit
+    bench plan, whose arena is only planned here; a threshold forced on that tree would
+    exceed the 40-bit tensor limit, so it keeps the planner's)."""
+    circ = cg.sycamore_grid(rows, cols, cycles, seed=0)
+    o = opts(log2_batches=log2_batches, n_sliced=n_sliced, precision=1, trials=16)
+    rng = np.random.default_rng(rows * 100 + cycles)
+    full = np.arange(1 << n_sliced, dtype=np.uint64)
+    for sl in (full, np.sort(rng.choice(full, size=max(1, full.size // 3), replace=False))):
+        bad, arena = layout_violations(emu, circ, cg.default_open_qubits(rows, cols, 6), o, q_max, 1, sl)
+        assert bad == 0 and arena > 0
