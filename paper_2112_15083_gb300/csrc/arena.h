@@ -17,6 +17,23 @@
 
 #include "tn_internal.h"
 
+// Sliced legs whose both values appear for every slice of the set (the set is closed
+// under flipping them): those legs become layout bits, the others explicit versions.
+inline uint64_t explicit_legs(const std::vector<uint64_t> &slices, int nI) {
+    std::unordered_map<uint64_t, char> in;
+    in.reserve(slices.size() * 2);
+    for (uint64_t s : slices) in[s] = 1;
+    uint64_t all = nI >= 64 ? ~0ull : ((1ull << nI) - 1);
+    uint64_t fr = 0;
+    for (int b = 0; b < nI; b++) {
+        bool closed = true;
+        for (uint64_t s : slices)
+            if (!in.count(s ^ (1ull << b))) { closed = false; break; }
+        if (closed) fr |= 1ull << b;
+    }
+    return all & ~fr;
+}
+
 struct CallLayout {
     std::vector<std::vector<uint64_t>> vals;             // per node: distinct versions
     std::vector<std::unordered_map<uint64_t, int>> index;

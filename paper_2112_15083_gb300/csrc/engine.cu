@@ -1213,22 +1213,6 @@ int ensure_variant(DevMem &mem, CNet &cn, uint64_t E) {
     return setup_leaves(mem, cn);
 }
 
-// Sliced legs whose both values appear for every slice of the set (the set is closed
-// under flipping them): those legs become layout bits, the others explicit versions.
-uint64_t explicit_legs(const std::vector<uint64_t> &slices, int nI) {
-    std::unordered_map<uint64_t, char> in;
-    in.reserve(slices.size() * 2);
-    for (uint64_t s : slices) in[s] = 1;
-    uint64_t all = nI >= 64 ? ~0ull : ((1ull << nI) - 1);
-    uint64_t fr = 0;
-    for (int b = 0; b < nI; b++) {
-        bool closed = true;
-        for (uint64_t s : slices)
-            if (!in.count(s ^ (1ull << b))) { closed = false; break; }
-        if (closed) fr |= 1ull << b;
-    }
-    return all & ~fr;
-}
 
 // After a synchronising call: a bounded device wait that gave up is reported once.
 int check_err(CNet &cn, cudaStream_t st) {

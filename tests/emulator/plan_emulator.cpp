@@ -29,21 +29,6 @@ void tn_plan_opts_default(tn_plan_opts *o) {
 
 extern "C" const char *emu_error() { return g_err.c_str(); }
 
-// Legs whose two values both appear with every assignment of the others stay layout bits
-// (never summed until the root); the rest become explicit versions.
-static uint64_t emu_explicit_legs(const std::vector<uint64_t> &slices, int nI) {
-    std::unordered_map<uint64_t, char> in;
-    for (uint64_t s : slices) in[s] = 1;
-    uint64_t fr = 0;
-    for (int b = 0; b < nI; b++) {
-        bool both = true;
-        for (uint64_t s : slices)
-            if (!in.count(s ^ (1ull << b))) { both = false; break; }
-        if (both) fr |= 1ull << b;
-    }
-    const uint64_t all = nI >= 64 ? ~0ull : ((1ull << nI) - 1);
-    return all & ~fr;
-}
 
 // Plan (options o, q_max forced when >= -1, tensor-core operand roles when tc != 0),
 // compile for the slice set and contract nb batches: out[2 * (t * 2^n_open + i) + {0, 1}].
@@ -76,7 +61,7 @@ extern "C" int emu_contract(const void *circ, size_t len, const int32_t *open, i
     }
     const std::vector<uint64_t> sv(slices, slices + n_slices);
     const int nI = (int)I.size();
-    const uint64_t E = emu_explicit_legs(sv, nI);
+    const uint64_t E = explicit_legs(sv, nI);
     rc = tn_compile(net, tree, E, steps, tc != 0);
     if (rc) return rc;
     const auto &nodes = tree.nodes;
@@ -241,7 +226,7 @@ extern "C" int emu_layout_check(const void *circ, size_t len, const int32_t *ope
         tn_recompute_deps(net, tree);
     }
     const std::vector<uint64_t> sv(slices, slices + n_slices);
-    const uint64_t E = emu_explicit_legs(sv, (int)I.size());
+    const uint64_t E = explicit_legs(sv, (int)I.size());
     if (tn_compile(net, tree, E, steps, tc != 0)) return -1;
     CallLayout L;
     layout_call(tree, steps, E, 8, sv, L);
