@@ -3,7 +3,7 @@
 // the library's own host planner, compiles it for the explicit legs of a slice set, and
 // runs every step of the step list as plain complex128 loops:
 //   * leaves in the layout the compiler fixed, one copy per code of their explicit legs;
-//   * operand versions selected by the slice set (first appearance order);
+//   * operand versions selected by the slice set, as the engine's layout_call lists them;
 //   * batch gathers by the bit-by-bit definition of the step's gather fields;
 //   * C[v][bat][m][n] = sum_k A[v][bat][m][k] B[v][bat][n][k], stored at the bit-scattered
 //     positions the step gives;
@@ -75,14 +75,12 @@ extern "C" int emu_contract(const void *circ, size_t len, const int32_t *open, i
     stats[1] = n_batch_steps;
     stats[2] = (int32_t)steps.size();
 
-    // versions: the distinct projections of the slice set on a node's explicit legs
-    std::vector<std::vector<uint64_t>> vals(NN);
-    std::vector<std::unordered_map<uint64_t, long long>> vidx(NN);
-    for (int x = 0; x < NN; x++)
-        for (uint64_t s : sv) {
-            const uint64_t w = s & nodes[x].dep & E;
-            if (vidx[x].emplace(w, (long long)vals[x].size()).second) vals[x].push_back(w);
-        }
+    // versions: the distinct projections of the slice set on a node's explicit legs, as the
+    // engine's layout_call orders them
+    CallLayout lay;
+    layout_call(tree, steps, E, 16, sv, lay);
+    const auto &vals = lay.vals;
+    const auto &vidx = lay.index;
     // leaves: one copy per code of their explicit sliced legs, in their layout
     std::vector<std::vector<cplx>> store(NN);
     std::vector<std::vector<int>> leaf_sl(NN);  // explicit sliced legs (e), in leg order
@@ -122,7 +120,7 @@ extern "C" int emu_contract(const void *circ, size_t len, const int32_t *open, i
             for (size_t u = 0; u < leaf_sl[x].size(); u++) code |= (long long)((w >> leaf_sl[x][u]) & 1ull) << u;
             return code;
         }
-        return vidx[x].at(w);
+        return (long long)vidx[x].at(w);
     };
     auto scatter = [](long long x, const int8_t *pos, int n) {
         long long r = 0;
