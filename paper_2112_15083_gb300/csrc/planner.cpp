@@ -535,8 +535,9 @@ StepEst step_estimate(const Network &net, const Node &a, const Node &b, const No
     const bool gb = (b.ch[0] < 0 && b.beta) || (c.beta && !b.beta && (b.idx & closed).any());
     const Bits A = ga && !a.beta ? a.idx.andnot(closed) | beta : a.idx;
     const Bits B = gb && !b.beta ? b.idx.andnot(closed) | beta : b.idx;
-    const double va = std::ldexp(1.0, __builtin_popcountll(a.dep)), vb = std::ldexp(1.0, __builtin_popcountll(b.dep));
-    const double ver = std::ldexp(1.0, __builtin_popcountll(c.dep));
+    const double va = net.per_slice ? 1.0 : std::ldexp(1.0, __builtin_popcountll(a.dep));
+    const double vb = net.per_slice ? 1.0 : std::ldexp(1.0, __builtin_popcountll(b.dep));
+    const double ver = net.per_slice ? 1.0 : std::ldexp(1.0, __builtin_popcountll(c.dep));
     const double fl = 8.0 * std::ldexp(1.0, (A | B).count()) * ver;
     const double sa = 8.0 * std::ldexp(1.0, A.count()) * va, sb = 8.0 * std::ldexp(1.0, B.count()) * vb;
     const double by = sa + sb + 8.0 * std::ldexp(1.0, c.idx.count()) * ver;
@@ -573,6 +574,10 @@ StepEst step_estimate(const Network &net, const Node &a, const Node &b, const No
     if (net.mem_limit_elems > 0 && by / 8.0 > net.mem_limit_elems) e.time += 1e6 * (by / 8.0 / net.mem_limit_elems);
     // a batch step runs once per group of the job, a batch-independent one once per job
     if (c.beta) e.time *= net.job_groups;
+    if (net.cap_bits > 0) {
+        const int over = std::max({a.idx.count(), b.idx.count(), c.idx.count()}) - net.cap_bits;
+        if (over > 0) e.time += 1e6 * over;
+    }
     return e;
 }
 
@@ -1554,6 +1559,20 @@ int tn_plan_build_host(const Merged &mg, const tn_plan_opts &o, const int32_t *o
         net.q_max = t0.q_max >= -1 ? t0.q_max : net.q_max;
         tree = t0;
         tn_recompute_deps(net, tree);
+        // optionally anneal it for the per-slice cost under the size cap (kept only when
+        // cheaper with every tensor within the cap)
+        if (net.anneal_iters > 0) {
+            net.per_slice = true;
+            net.cap_bits = o.max_log2_tensor;
+            Tree a = tree;
+            tn_anneal_tree(net, a, net.anneal_iters, o.order_seed);
+            int widest = 0;
+            for (const Node &nd : a.nodes) widest = std::max(widest, nd.idx.count());
+            if (widest <= o.max_log2_tensor && tn_tree_cost(net, a).time < tn_tree_cost(net, tree).time) tree = a;
+            net.per_slice = false;
+            net.cap_bits = 0;
+            tn_recompute_deps(net, tree);
+        }
         uint64_t E = net.n_sliced >= 64 ? ~0ull : ((1ull << net.n_sliced) - 1);
         uint64_t E0 = 0;
         rc = tn_compile(net, tree, E0, steps, o.precision != TN_PREC_C64);

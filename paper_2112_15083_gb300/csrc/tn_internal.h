@@ -88,6 +88,10 @@ struct Network {
     double mem_limit_elems = 0;
     double job_groups = 1;  // batch groups per job: the cost weight of batch steps
     int anneal_iters = 0;   // order search: annealing moves applied to the winning tree
+    // per-slice costing (size-targeted slicing: slices run a few at a time): sliced legs
+    // add no version multiplicity, and a tensor above 2^cap_bits elements is penalised
+    bool per_slice = false;
+    int cap_bits = 0;
     int n_sliced = 0;              // |I|
     std::vector<int> idx_seg;      // segment id of each network index (-1: beta / other)
 };
