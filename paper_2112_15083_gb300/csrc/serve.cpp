@@ -101,10 +101,10 @@ void release(Req &r) {
 }
 
 void fail(tn_server_s *s, Req &r, int code, int32_t status) {
-    r.error = code;
     r.message = tn_last_error();
     release(r);
     std::lock_guard<std::mutex> lk(s->mu);
+    r.error = code;
     r.status = status;
     r.t_done = now_s(s->t0);
     s->cv_done.notify_all();
@@ -207,7 +207,6 @@ int launch_group(Req &r) {
         cudaMemcpyAsync(r.h_bits, r.d_bits, r.T * sizeof(uint64_t), cudaMemcpyDeviceToHost, r.stream) != cudaSuccess ||
         cudaEventRecord(r.ev, r.stream) != cudaSuccess)
         return TN_EDEVICE;
-    r.flops_done += r.group == 0 ? r.flops_first : r.flops_next;
     r.inflight = true;
     r.group++;
     return TN_OK;
@@ -274,12 +273,17 @@ void sched_loop(tn_server_s *s) {
                     continue;
                 }
                 const int64_t take = std::min<int64_t>(r.T, r.max_steps - r.steps);
+                int64_t acc = 0;
                 for (int64_t i = 0; i < take; i++)
                     if (r.h_acc[i]) {
-                        r.accepted++;
+                        acc++;
                         if ((int64_t)r.result.size() < r.N) r.result.push_back(r.h_bits[i]);
                     }
-                r.steps += take;
+                {  // progress counters are read by tn_server_query under the lock
+                    std::lock_guard<std::mutex> lk(s->mu);
+                    r.accepted += acc;
+                    r.steps += take;
+                }
                 r.t_next += r.T;
                 if ((int64_t)r.result.size() >= r.N || r.steps >= r.max_steps) {
                     finished.push_back(rp);
@@ -287,10 +291,14 @@ void sched_loop(tn_server_s *s) {
                 }
             }
             idle = false;
+            const double fl = r.group == 0 ? r.flops_first : r.flops_next;
             int rc = launch_group(r);
             if (rc) {
                 r.error = rc;
                 finished.push_back(rp);
+            } else {
+                std::lock_guard<std::mutex> lk(s->mu);
+                r.flops_done += fl;
             }
         }
         for (auto &rp : finished) {
@@ -311,15 +319,19 @@ void sched_loop(tn_server_s *s) {
     }
 }
 
+// Called with the server's lock held.  The planner thread writes a request's plan fields
+// without the lock and publishes them with its status change, so they are read only past
+// planning; the scheduler updates the progress counters under the lock.
 void fill_info(const Req &r, tn_request_info *info) {
     std::memset(info, 0, sizeof(*info));
     info->status = r.status;
     info->error = r.error;
-    info->F = r.F;
+    const bool planned = r.status != TN_REQ_QUEUED && r.status != TN_REQ_PLANNING;
+    info->F = planned ? r.F : 0.0;
     info->steps = r.steps;
     info->accepted = r.accepted;
-    info->n_slices = (int64_t)r.slices.size();
-    info->est_bytes = r.est_bytes;
+    info->n_slices = planned ? (int64_t)r.slices.size() : 0;
+    info->est_bytes = planned ? r.est_bytes : 0;
     info->flops = r.flops_done;
     info->t_submit = r.t_submit;
     info->t_admit = r.t_admit;
