@@ -98,6 +98,10 @@ typedef struct {
     int32_t anneal_iters;    /* order search: simulated-annealing moves (tree rotations,
                                 Metropolis on the log of the estimated time) applied to
                                 the winning tree, kept only if cheaper; 0 (default): none */
+    int32_t parallel_search; /* 1: the greedy trials draw from per-trial generators and run
+                                on host threads (faster planning; other trees than the
+                                default, equally seeded and reproducible); 0 (default):
+                                one sequential generator */
     void *stream;            /* cudaStream_t; NULL = legacy default stream */
     tn_alloc_fn alloc;       /* optional device allocator */
     tn_free_fn free;

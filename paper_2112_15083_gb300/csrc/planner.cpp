@@ -794,7 +794,30 @@ void greedy_once(const Network &net, std::mt19937_64 &rng, double costmod, doubl
 
 }  // namespace
 
+template <typename F>
+static void parallel_for(int n, F f);
+
 void tn_greedy_tree(const Network &net, uint64_t seed, int trials, Tree &best, TreeCost &cost) {
+    if (net.parallel_greedy && trials > 1) {
+        // each trial draws from its own generator (seed, trial), so the trials run in
+        // parallel and the result does not depend on the thread count
+        const int n = trials;
+        std::vector<Tree> tt((size_t)n);
+        std::vector<double> tc((size_t)n);
+        parallel_for(n, [&](int tr) {
+            std::mt19937_64 r(seed * 0x9E3779B97F4A7C15ull + 12345 + 0x632BE59BD9B4E019ull * (uint64_t)tr);
+            const double costmod = tr == 0 ? 1.0 : std::uniform_real_distribution<double>(0.3, 2.0)(r);
+            const double temp = tr == 0 ? 0.0 : std::uniform_real_distribution<double>(0.0, 1.5)(r);
+            greedy_once(net, r, costmod, temp, tt[tr]);
+            tc[tr] = tn_tree_cost(net, tt[tr]).time;
+        });
+        int bi = 0;
+        for (int tr = 1; tr < n; tr++)
+            if (tc[tr] < tc[bi]) bi = tr;
+        best = tt[bi];
+        cost = tn_tree_cost(net, best);
+        return;
+    }
     std::mt19937_64 rng(seed * 0x9E3779B97F4A7C15ull + 12345);
     bool have = false;
     for (int tr = 0; tr < std::max(1, trials); tr++) {
@@ -1490,6 +1513,7 @@ void tn_cost_settings(Network &net, const tn_plan_opts &o) {
     net.mem_limit_elems = budget / 8.0 / 2.0;
     net.job_groups = o.job_groups > 1 ? (double)o.job_groups : 1.0;
     net.anneal_iters = std::max(0, o.anneal_iters);
+    net.parallel_greedy = o.parallel_search != 0;
 }
 
 int tn_tree_and_compile(Network &net, const tn_plan_opts &o, const int32_t *order, int n_order,

@@ -92,6 +92,7 @@ struct Network {
     // add no version multiplicity, and a tensor above 2^cap_bits elements is penalised
     bool per_slice = false;
     int cap_bits = 0;
+    bool parallel_greedy = false;  // greedy trials with their own generators, on threads
     int n_sliced = 0;              // |I|
     std::vector<int> idx_seg;      // segment id of each network index (-1: beta / other)
 };

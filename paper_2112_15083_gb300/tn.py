@@ -85,6 +85,7 @@ class PlanOpts(ctypes.Structure):
         ("fuse_root_sum", ctypes.c_int32),
         ("job_groups", ctypes.c_int32),
         ("anneal_iters", ctypes.c_int32),
+        ("parallel_search", ctypes.c_int32),
         ("stream", ctypes.c_void_p),
         ("alloc", ALLOC_FN),
         ("free", FREE_FN),
@@ -240,7 +241,8 @@ class Plan:
     def __init__(self, circuit: Circuit, open_qubits, sliced=None, order=None, precision=PREC_C64,
                  log2_batches=8, order_seed=0, order_trials=64, n_auto_sliced=0,
                  hbm_budget_bytes=0.0, stream=None, use_torch_allocator=True, max_norm_flops=0.0,
-                 autotune=None, max_log2_tensor=0, fuse_root_sum=False, job_groups=1, anneal_iters=0):
+                 autotune=None, max_log2_tensor=0, fuse_root_sum=False, job_groups=1, anneal_iters=0,
+                 parallel_search=False):
         L = lib()
         o = PlanOpts()
         L.tn_plan_opts_default(ctypes.byref(o))
@@ -259,6 +261,7 @@ class Plan:
         o.fuse_root_sum = int(bool(fuse_root_sum))
         o.job_groups = int(job_groups)
         o.anneal_iters = int(anneal_iters)
+        o.parallel_search = int(bool(parallel_search))
         o.stream = _stream_ptr(stream)
         self._alloc = None
         if use_torch_allocator:
@@ -427,7 +430,7 @@ class Plan:
 
 def plan_host(circuit: Circuit, open_qubits, sliced=None, order=None, log2_batches=8, order_seed=0,
               order_trials=64, n_auto_sliced=0, precision=PREC_C64, max_log2_tensor=0, hbm_budget_bytes=0.0,
-              job_groups=1, anneal_iters=0):
+              job_groups=1, anneal_iters=0, parallel_search=False):
     """Host-only planning (no GPU): (info dict, steps array (n_steps, 7), sliced edges).
     Step row: batch, m, n, k bits, log2 versions of C, A, B."""
     L = lib()
@@ -443,6 +446,7 @@ def plan_host(circuit: Circuit, open_qubits, sliced=None, order=None, log2_batch
         o.hbm_budget_bytes = hbm_budget_bytes
     o.job_groups = int(job_groups)
     o.anneal_iters = int(anneal_iters)
+    o.parallel_search = int(bool(parallel_search))
     openq = np.ascontiguousarray(np.asarray(open_qubits, dtype=np.int32))
     if sliced is not None:
         arr = (Edge * max(1, len(sliced)))(*[Edge(int(q), int(s)) for (q, s) in sliced])

@@ -187,3 +187,12 @@ def test_arena_layout_invariants(emu, rows, cols, cycles, log2_batches, n_sliced
     for sl in (full, np.sort(rng.choice(full, size=max(1, full.size // 3), replace=False))):
         bad, arena = layout_violations(emu, circ, cg.default_open_qubits(rows, cols, 6), o, q_max, 1, sl)
         assert bad == 0 and arena > 0
+
+
+def test_plans_from_the_parallel_search(emu):
+    """Greedy trials with per-trial generators on threads (tn_plan_opts.parallel_search):
+    the 12-qubit all-open plan differs from the sequential search's; both must be right."""
+    circ = cg.sycamore_grid(3, 4, 8, seed=0)
+    o = opts(log2_batches=0, n_sliced=2, precision=0, trials=64)
+    o.parallel_search = 1
+    check(emu, circ, list(range(12)), o, -2, 0, nb=1, seed=2)
