@@ -241,7 +241,7 @@ int tn_contract(tn_plan_h p, const uint64_t *slices, int64_t n_slices, const uin
                 int64_t n_batches, double *amps, int32_t flags);
 
 /*
- * Verification (Sec. I.A, "exact amplitudes for uncorrelated bitstrings"; Eq. 1): the
+ * Verification (linear XEB, Eq. 1): the
  * amplitude a(s) of each of N bitstrings summed over a slice set (unnormalised, as
  * tn_contract computes it) and their linear XEB, xeb = 2^n / N * sum_s |a(s)|^2 - 1.
  * A string's closed qubits select its batch and its open qubits its entry; a plan with no
