@@ -5,8 +5,9 @@ arXiv:2112.15083 (Kalachev, Panteleev, Zhou, Yung):
 
 * amplitudes: the state vector C|0> (Sec. I.A, |psi> = C2 C1 |0>), applied gate by
   gate in ``oracle.c``;
-* slices: a sliced leg fixed to v is the projector |v><v| on that wire (App. B,
-  "delta_{S=i} is a projector"); the sum over all slices is the unsliced state;
+* slices: a sliced leg fixed to v is the projector |v><v| on that wire (App. B: the
+  slicing delta acts on the wire as a projection); the sum over all slices is the
+  unsliced state;
 * partial slicing: |psi_X> = C2 Pi_X C1 |0> = sum_{i in X} |psi_i> (Sec. I.A);
 * norms R[i] = ||psi_i||^2 = P(S-wires read i after C1) (Sec. I.A, Alg. 1);
 * SlicedVertexSelect (Alg. 2) and Slice selection (Alg. 1);

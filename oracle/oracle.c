@@ -6,7 +6,7 @@
  *     (definition of the amplitudes <b|C|0>, paper Sec. I eq. for |psi>);
  *   - sliced amplitudes: fixing a sliced tensor leg (qubit q between two gates) to
  *     value v is the projector |v><v| inserted on that wire at that point
- *     (Appendix B: delta_{S=i} is a projector);
+ *     (Appendix B: the slicing delta acts on the wire as a projection);
  *   - psi_X = C2 Pi_X C1 |0> for a set X of partial-slice values (Sec. I.A,
  *     |psi_X> = sum_{i in X} |psi_i>, |psi_i> = sum_j C2|ji><ji|C1|0>);
  *   - marginals of a state on a subset of qubits (R[i] = ||psi_i||^2, Sec. I.A);
