@@ -192,7 +192,9 @@ int tn_partial_norms(tn_plan_h p, double f, int32_t *s_index, int32_t *k, double
  * Slice cut (Alg. 1 steps 4-5) on the GPU: sort R descending (ties: index ascending),
  * sum in that order in FP64, keep the minimal prefix whose sum reaches f (all of it if
  * rounding keeps the total below f).  R: host array of 2^k doubles.  X: out, host,
- * the kept indices in sorted order (cap 2^k); F: the kept sum.  k <= 20.
+ * the kept indices in sorted order (cap 2^k); F: the kept sum.  k <= 12 (one block sorts
+ * the 2^k norms in shared memory); larger k returns TN_EINVAL.  The device scratch is
+ * allocated and freed on the stream inside the call, which synchronises the stream.
  */
 int tn_slice_cut(const double *R, int32_t k, double f, void *stream, int32_t *X,
                  int32_t *n_x, double *F);
@@ -202,12 +204,15 @@ int tn_slice_cut(const double *R, int32_t k, double f, void *stream, int32_t *X,
  * deployment variant).  For callers that cannot allocate device memory from their call
  * path: processes whose device memory is owned up front by another allocator, and code
  * that must not enter the CUDA allocator (which can wait on other device work and can
- * fail under fragmentation).  Same arguments and results as tn_slice_cut, but the device
- * scratch is a 64 KiB static array in libtn that every GPU loading the library holds
- * until the process exits; k above 12 is rejected with TN_EINVAL.  The first call on a
- * device looks up the array's device address (cudaGetSymbolAddress) with that device
- * current; make that first call before any stream capture.  All calls share the one
- * array per device: calls whose work overlaps on the GPU race with each other.
+ * fail under fragmentation).  Same arguments, results and limit (k <= 12, TN_EINVAL
+ * above) as tn_slice_cut.  The device scratch is a static array in libtn of 48 KiB +
+ * 256 B (2^12 doubles, 2^12 int32, the count and the sum) that every GPU loading the
+ * library holds until the process exits.  The first call on a device looks up the
+ * array's device address (cudaGetSymbolAddress) with that device current and caches it
+ * per device ordinal; the cache is not valid across cudaDeviceReset.  The call
+ * synchronises the stream, so it cannot be made while the stream is being captured.
+ * All calls share the one array per device: calls whose work overlaps on the GPU race
+ * with each other.
  */
 int tn_slice_cut_noalloc(const double *R, int32_t k, double f, void *stream, int32_t *X,
                          int32_t *n_x, double *F);

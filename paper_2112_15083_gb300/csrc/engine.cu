@@ -613,7 +613,7 @@ int prepare_call(DevMem &mem, CNet &cn, const std::vector<uint64_t> &slices, dou
 constexpr int kVarRow = 0, kVarSmall = 1, kVarRowStage = 4, kVarTc128 = 9128, kVarTc64 = 9064, kVarTc32 = 9032;
 
 // Whether the staged row kernel can run step si: the row kernel's shapes with complex64
-// rows of 16 to 64 elements.  It is not among the autotuner's candidates yet.
+// rows of 16 to 64 elements.
 bool rowstage_fits(const CNet &cn, const Step &s) {
     return cn.elem == 8 && std::min(s.nm, s.nn) <= 5 && s.nk >= 4 && s.nk <= 6;
 }
@@ -634,6 +634,7 @@ std::vector<int> step_variants(const CNet &cn, size_t si) {
         return {kVarTc128, kVarTc64};
     }
     if (std::min(s.nm, s.nn) <= 5 && s.nk <= 6) v.push_back(kVarRow);
+    if (rowstage_fits(cn, s)) v.push_back(kVarRowStage);
     if (small_fits(s, (size_t)cn.elem)) v.push_back(kVarSmall);
     for (auto &t : kTiles)
         if (t[0] == 16 || ((2LL << s.nm) >= t[0] && (2LL << s.nn) >= t[1])) v.push_back(t[0] * 1000 + t[1]);
@@ -1694,25 +1695,35 @@ int tn_slice_cut(const double *R, int32_t k, double f, void *stream, int32_t *X,
     if (!R || !X || !n_x || !F || k < 0 || k > 12) { tn_set_error("tn_slice_cut: bad arguments (k <= 12)"); return TN_EINVAL; }
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     const int n = 1 << k;
-    void *dR = nullptr, *dX = nullptr, *dn = nullptr, *dF = nullptr;
-    CK(cudaMallocAsync(&dR, n * sizeof(double), st));
-    CK(cudaMallocAsync(&dX, n * sizeof(int32_t), st));
-    CK(cudaMallocAsync(&dn, sizeof(int32_t), st));
-    CK(cudaMallocAsync(&dF, sizeof(double), st));
-    CK(cudaMemcpyAsync(dR, R, n * sizeof(double), cudaMemcpyHostToDevice, st));
-    size_t smem = (size_t)n * (sizeof(double) + sizeof(int));
-    tnk::slice_cut<<<1, 256, smem, st>>>((const double *)dR, k, f, (int32_t *)dX, (int32_t *)dn, (double *)dF);
-    CK(cudaGetLastError());
-    CK(cudaMemcpyAsync(n_x, dn, sizeof(int32_t), cudaMemcpyDeviceToHost, st));
-    CK(cudaMemcpyAsync(F, dF, sizeof(double), cudaMemcpyDeviceToHost, st));
-    CK(cudaStreamSynchronize(st));
-    CK(cudaMemcpyAsync(X, dX, (size_t)(*n_x) * sizeof(int32_t), cudaMemcpyDeviceToHost, st));
-    CK(cudaFreeAsync(dR, st));
-    CK(cudaFreeAsync(dX, st));
-    CK(cudaFreeAsync(dn, st));
-    CK(cudaFreeAsync(dF, st));
-    CK(cudaStreamSynchronize(st));
-    return TN_OK;
+    void *buf[4] = {nullptr, nullptr, nullptr, nullptr};
+    const size_t sz[4] = {n * sizeof(double), n * sizeof(int32_t), sizeof(int32_t), sizeof(double)};
+    // every buffer taken is returned to the stream's pool on every exit path
+    auto run = [&]() -> int {
+        for (int i = 0; i < 4; i++) CK(cudaMallocAsync(&buf[i], sz[i], st));
+        double *dR = static_cast<double *>(buf[0]);
+        int32_t *dX = static_cast<int32_t *>(buf[1]), *dn = static_cast<int32_t *>(buf[2]);
+        double *dF = static_cast<double *>(buf[3]);
+        CK(cudaMemcpyAsync(dR, R, n * sizeof(double), cudaMemcpyHostToDevice, st));
+        size_t smem = (size_t)n * (sizeof(double) + sizeof(int));
+        tnk::slice_cut<<<1, 256, smem, st>>>(dR, k, f, dX, dn, dF);
+        CK(cudaGetLastError());
+        CK(cudaMemcpyAsync(n_x, dn, sizeof(int32_t), cudaMemcpyDeviceToHost, st));
+        CK(cudaMemcpyAsync(F, dF, sizeof(double), cudaMemcpyDeviceToHost, st));
+        CK(cudaStreamSynchronize(st));
+        CK(cudaMemcpyAsync(X, dX, (size_t)(*n_x) * sizeof(int32_t), cudaMemcpyDeviceToHost, st));
+        return TN_OK;
+    };
+    int rc = run();
+    for (int i = 0; i < 4; i++)
+        if (buf[i] && cudaFreeAsync(buf[i], st) != cudaSuccess && rc == TN_OK) {
+            tn_set_error("tn_slice_cut: cudaFreeAsync failed");
+            rc = TN_EDEVICE;
+        }
+    if (cudaStreamSynchronize(st) != cudaSuccess && rc == TN_OK) {
+        tn_set_error("tn_slice_cut: stream synchronisation failed");
+        rc = TN_EDEVICE;
+    }
+    return rc;
 }
 
 int tn_select(tn_plan_h p, double f, uint64_t *slices, int64_t cap, int64_t *n_slices, double *F) {
@@ -2057,7 +2068,9 @@ void *g_cut_dev_ptr[kCutMaxDevices] = {};
 
 // Device address of g_cut_scratch on the current device.  Host code only has a
 // host-side stand-in under that name, so the address is looked up once per device
-// (with that device current) and cached.
+// (with that device current) and cached.  The cache outlives a cudaDeviceReset, after
+// which the module is reloaded at another address: callers that reset a device must
+// not use this entry point afterwards in the same process.
 int cut_scratch_address(void **out) {
     int dev = -1;
     CK(cudaGetDevice(&dev));

@@ -138,9 +138,10 @@ def test_28q_bench_configuration_16384_batches(grid28, prec):
 
 @pytest.mark.parametrize("prec", ["c64", "bf16x2"])
 def test_every_kernel_variant(prec):
-    """autotune = k >= 2 runs variant (step + k - 2) mod count at every step, so nine plans
-    cover every FFMA tile, the row and staged kernels and both tensor-core tile widths
-    at the shapes of a 20-qubit plan with 1024 batches per group."""
+    """autotune = k >= 2 runs variant (step + k - 2) mod count at every step, so ten plans
+    cover every FFMA tile, the row kernel, the staged row kernel, the staged small-product
+    kernel and every tensor-core tile width at the shapes of a 20-qubit plan with 1024
+    batches per group (at most ten candidates per step)."""
     P = pkg()
     circ = cg.sycamore_grid(4, 5, 12, seed=1)
     openq = cg.default_open_qubits(4, 5, 6)
@@ -148,7 +149,7 @@ def test_every_kernel_variant(prec):
     cb = cg.random_closed_bits(1024, 14, seed=9)
     ref = oracle.batch_amplitudes(oracle.simulate(circ), 20, openq, cb)
     precision = {"c64": P.tn.PREC_C64, "bf16x2": P.tn.PREC_BF16X2}[prec]
-    for k in range(2, 11):
+    for k in range(2, 12):
         plan = P.plan(C, openq, n_auto_sliced=6, log2_batches=10, order_trials=16, precision=precision, autotune=k)
         amps = plan.contract(np.arange(64, dtype=np.uint64), cb)
         if prec == "c64":
