@@ -1,20 +1,34 @@
-"""Benchmark: samples/s at fixed fidelity on the 4x7-grid / 14-cycle workload.
+"""Benchmark: samples/s at fixed fidelity (Sec. II.A sampling from Sec. I.C's partial sum).
 
-One step = one pass of the sampling hot path over one group of T = 16384 batches of
-2^6 amplitudes: Philox batch draws, every pairwise contraction of the sliced network
-over the slice set (2^10 slices at fidelity 1) with the batch gathers, the FP64 slice
-sum, p = |a|^2 / F and the warp rejection sampler.  Every step recomputes every tensor,
-the batch-independent ones included (nothing is carried between steps).
-Intermediates exceed L2 (the dominant operands are GiB-sized) and L2 is also flushed
-between timed steps.
+Default workload (grid5x8_m16): the 40-qubit 5x8 ABCD circuit, 16 cycles, 100k samples at
+fidelity f = 1/64 (Alg. 1), batches of 2^6 bitstrings, alpha = 2.  The plan slices legs
+until one slice's tensors fit 2^30 elements; its order search weights the batch steps by
+the job's batch groups.  The sampling job (tn_job_*) splits the retained slices into
+chunks; one chunk is contracted for every batch group of the job (its batch-independent
+intermediates once, its batch part once per group of 4096 batches) and added to the
+job's FP64 amplitude sums; a final pass runs the accept / pick step on every batch.
 
-    python bench.py [--gpus N --steps K --warmup W] [--impl reference]
+One step = one chunk of the job.  The job's chunks are identical in shape and work, so
+the job time is the chunk count times the mean measured chunk time plus the measured
+final pass: `value` = N / that time (samples/s of the whole job, projected from the
+timed chunks; `config.projection` states it).  The working set (tens of GB per chunk)
+exceeds L2 many times over, so no flush is needed between steps.  `e2e` times the same
+job through the public API (job creation with the slice selection and the batch draws,
+chunks, the final pass with host output) and projects it the same way.
 
-Prints one JSON line (rank 0).  Under torchrun each rank runs independent batch
-groups (replicas, weak scaling); the timing is the max over ranks.
+Secondary lines (`secondary`): the 28-qubit 4x7 / 14-cycle workload at fidelity 1, one
+step = one group of 16384 batches of one sampling job (the job's first group runs every
+contraction, later groups reuse the batch-independent intermediates), in split bf16 and
+in complex64 on the same plan recipe.
+
+    python bench.py [--gpus N --steps K --warmup W] [--impl reference] [--workload W]
+
+Prints one JSON line (rank 0).  Under torchrun each rank runs its own job (replicas, weak
+scaling); the timing is the max over ranks.
 """
 import argparse
 import json
+import math
 import os
 import statistics
 import subprocess
@@ -25,22 +39,29 @@ import time
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
+# sampling-job workloads (one step = one slice chunk of the job)
+JOB_WORKLOADS = {
+    # 40 qubits, 16 cycles, 1/64 of the slices, 100k samples (the largest single-GPU case)
+    "grid5x8_m16": dict(rows=5, cols=8, cycles=16, seed=0, n_open=6, log2_batches=12, f=1.0 / 64, N=100000,
+                        alpha=2.0, caps=(30, 29, 28, 27, 26), slice_bytes_max=140e9, budget=150e9, trials=256),
+}
+# batch-group workloads (one step = one batch group of a sampling job over one slice set)
 WORKLOADS = {
-    # the measured workload: 28 qubits, 14 cycles, 2^10 slices, 16384 batches of 64 per step
+    # 28 qubits, 14 cycles, 2^10 slices, 16384 batches of 64 per step
     "grid4x7_m14": dict(rows=4, cols=7, cycles=14, seed=0, n_sliced=10, n_open=6, log2_batches=14),
     # a smaller case of the same kernels (24 qubits), for detailed profiler captures
     "grid4x6_m12": dict(rows=4, cols=6, cycles=12, seed=0, n_sliced=8, n_open=6, log2_batches=8),
 }
-WORKLOAD = WORKLOADS["grid4x7_m14"]
 METRIC = "samples/s at fixed fidelity"
-# DRAM traffic (dram__bytes_read.sum + dram__bytes_write.sum, bytes per launch) of the
-# dominant launch from one-pass ncu captures of this workload (profiles/*_dram_grid4x7_m14_b16384.md),
-# valid for the kernel source it was taken with (sha256 prefix of the named csrc file)
+# DRAM traffic (dram__bytes_read.sum + dram__bytes_write.sum, bytes per launch) of a
+# launch from one-pass ncu captures (profiles/), valid for the kernel source it was taken
+# with (sha256 prefix of the named csrc file): (kernel, shape bits) -> (bytes, file, sha)
 MEASURED_TRAFFIC = {
     ("tc_cgemm<128,3>", (1, 15, 14, 12)): (83.75e9, "tc.cuh", "cbda2ea2f13a3e53"),
     ("cgemm_row", (23, 2, 5, 2)): (16.95e9, "kernels.cuh", "e2dc3ed40cd00353"),
 }
 FFMA_PEAK_NOTE = "152 SMs x 128 FP32 lanes x 2 FLOP x 2070 MHz"
+KERNEL_NAMES = {0: "cgemm_row", 1: "cgemm_small", 4: "cgemm_rowstage", 5: "cgemm_skinny"}
 
 
 def parse():
@@ -49,28 +70,31 @@ def parse():
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--fidelity", type=float, default=1.0)
+    ap.add_argument("--workload", default="grid5x8_m16", choices=sorted(JOB_WORKLOADS) + sorted(WORKLOADS))
+    ap.add_argument("--fidelity", type=float, default=None, help="target fidelity (default: the workload's)")
     ap.add_argument("--trials", type=int, default=256)
     ap.add_argument("--seed", type=int, default=2024)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-secondary", action="store_true", help="skip the 28-qubit secondary lines")
     ap.add_argument("--precision", default="bf16x2", choices=["c64", "bf16x2"])
-    ap.add_argument("--workload", default="grid4x7_m14", choices=sorted(WORKLOADS))
-    ap.add_argument("--log2-batches", type=int, default=None, help="batches per step = 2^this (default: the workload's)")
+    ap.add_argument("--chunk", type=int, default=2, help="job workloads: slices per chunk (a power of two)")
+    ap.add_argument("--log2-batches", type=int, default=None, help="batches per group = 2^this (default: the workload's)")
     ap.add_argument("--autotune", type=int, default=1, help="kernel autotuning (1) or the fixed shape rules (0)")
     ap.add_argument("--anneal", type=int, default=0,
                     help="order search: simulated-annealing moves on the winning tree (tn_plan_opts.anneal_iters)")
     ap.add_argument("--fuse-root", type=int, default=0,
                     help="1: run a row-kernel root step fused with the FP64 slice sum (tn_plan_opts.fuse_root_sum)")
     ap.add_argument("--serve", action="store_true", help="serving run (Poisson request stream) instead of the step bench")
-    ap.add_argument("--grid5x8-sample", action="store_true",
-                    help="bounded sample of the 40-qubit 5x8 / 16-cycle configuration (time per slice, extrapolated)")
     ap.add_argument("--serve-window", type=float, default=60.0, help="seconds of arrivals")
     ap.add_argument("--serve-rate", type=float, default=4.0, help="requests per second")
-    return ap.parse_args()
+    a = ap.parse_args()
+    if a.fidelity is None:
+        a.fidelity = JOB_WORKLOADS[a.workload]["f"] if a.workload in JOB_WORKLOADS else 1.0
+    return a
 
 
 def log2_batches(args):
-    w = WORKLOADS[args.workload]
+    w = JOB_WORKLOADS.get(args.workload) or WORKLOADS[args.workload]
     return w["log2_batches"] if args.log2_batches is None else args.log2_batches
 
 
@@ -86,6 +110,17 @@ def peaks():
         return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
     except Exception:
         return {}
+
+
+def cpu_model():
+    try:
+        for line in open("/proc/cpuinfo"):
+            if line.lower().startswith(("model name", "cpu part", "hardware")):
+                return line.split(":", 1)[1].strip()
+    except Exception:
+        pass
+    import platform
+    return platform.processor() or platform.machine()
 
 
 class Clocks:
@@ -140,7 +175,7 @@ class Clocks:
         return out
 
 
-# ---------------------------------------------------------------- oracle baseline
+# ---------------------------------------------------------------- oracle baselines
 
 def oracle_probs(circ):
     """The oracle's batch-independent part of a sampling job: the FP64 state vector of the
@@ -172,6 +207,52 @@ def cpu_cores():
         return os.cpu_count() or 1
 
 
+SUB_ROWS = 3  # rows of the 40-qubit grid the oracle's bounded sample simulates
+
+
+def oracle_job_sample(circ, openq, T, groups, N, seed, alpha=2.0, threads=None):
+    """One bounded sample of the oracle's work on a job too large for it.  The oracle (FP64
+    state vector) needs 2^n complex128 amplitudes: 17.6 TB at 40 qubits, which no host
+    here holds.  Its work is one pass over the vector per gate (then the sampler on the
+    job's batches), so it is measured on the first SUB_ROWS rows of the same circuit (the
+    gates acting there, the whole circuit's gate mix) and scaled by gates x amplitudes:
+    t_job = (t_sub / (gates_sub 2^n_sub)) gates 2^n + t_sampler per batch x batches.
+    Returns (job samples/s extrapolated, sample description, seconds spent)."""
+    import numpy as np
+    import oracle
+    from paper_2112_15083_gb300 import circuits as cg
+    if threads:
+        os.environ["OMP_NUM_THREADS"] = str(threads)
+    n_sub = SUB_ROWS * circ.cols
+    sub = cg.Circuit(n_qubits=n_sub, gates=[g for g in circ.gates if all(q < n_sub for q in g.qubits)])
+    t0 = time.perf_counter()
+    p = oracle_probs(sub)
+    t_sv = time.perf_counter() - t0
+    # the sampler on one group of T batches of the sub-circuit's 6 lowest qubits open
+    sub_open = list(range(6))
+    t1 = time.perf_counter()
+    oracle_group(p, sub, sub_open, T, seed, 0, alpha)
+    t_smp = time.perf_counter() - t1
+    del p
+    per_gate_amp = t_sv / (len(sub.gates) * 2.0 ** n_sub)
+    t_job = per_gate_amp * len(circ.gates) * 2.0 ** circ.n_qubits + t_smp * groups
+    desc = ("extrapolated: the FP64 state vector of %d qubits (%.1f TB) does not fit the host; the oracle simulated "
+            "the circuit's first %d rows (%d qubits, %d of its %d gates) in %.2f s and sampled %d batches in %.2f s; "
+            "job time = time per gate per amplitude x %d gates x 2^%d + sampler time x %d groups = %.3g s"
+            % (circ.n_qubits, 16 * 2.0 ** circ.n_qubits / 1e12, SUB_ROWS, n_sub, len(sub.gates), len(circ.gates),
+               t_sv, T, t_smp, len(circ.gates), circ.n_qubits, groups, t_job))
+    return N / t_job, desc, time.perf_counter() - t0
+
+
+def job_cpu_baseline(circ, openq, plan, info, w):
+    cores = cpu_cores()
+    v, desc, _ = oracle_job_sample(circ, openq, info["T"], info["groups"], w["N"], 1, w["alpha"], threads=cores)
+    v1, _d1, _ = oracle_job_sample(circ, openq, info["T"], info["groups"], w["N"], 1, w["alpha"], threads=1)
+    os.environ["OMP_NUM_THREADS"] = str(cores)
+    return {"value": v, "unit": "samples/s", "cores": cores, "kind": "oracle", "cpu": cpu_model(), "sample": desc,
+            "value_single_thread": v1}
+
+
 def run_reference(args):
     rank, world, _ = dist_env()
     if rank != 0:
@@ -179,6 +260,34 @@ def run_reference(args):
     from paper_2112_15083_gb300 import circuits as cg
     import oracle
     oracle.lib()
+    cores = cpu_cores()
+    os.environ.setdefault("OMP_NUM_THREADS", str(cores))
+    if args.workload in JOB_WORKLOADS:
+        w = JOB_WORKLOADS[args.workload]
+        circ = cg.sycamore_grid(w["rows"], w["cols"], w["cycles"], seed=w["seed"])
+        openq = cg.default_open_qubits(w["rows"], w["cols"], w["n_open"])
+        T = 1 << log2_batches(args)
+        groups = job_groups_for(w["N"], w["alpha"], T)
+        for _ in range(args.warmup):
+            oracle_job_sample(circ, openq, T, groups, w["N"], args.seed, w["alpha"])
+        vals, secs = [], 0.0
+        for _ in range(args.steps):
+            v, desc, s = oracle_job_sample(circ, openq, T, groups, w["N"], args.seed, w["alpha"])
+            vals.append(v)
+            secs += s
+        val = statistics.median(vals)
+        config = job_config(args, w)
+        line = {
+            "impl": "reference", "metric": METRIC, "value": val, "unit": "samples/s", "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * secs / max(1, args.steps),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": config,
+            "cpu_baseline": {"value": val, "unit": "samples/s", "cores": cores, "kind": "oracle", "cpu": cpu_model(),
+                             "sample": "median of %d bounded samples, each " % args.steps + desc},
+            "e2e": {"value": val, "unit": "samples/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+        }
+        print(json.dumps(line), flush=True)
+        return
     w = WORKLOADS[args.workload]
     circ = cg.sycamore_grid(w["rows"], w["cols"], w["cycles"], seed=w["seed"])
     openq = cg.default_open_qubits(w["rows"], w["cols"], w["n_open"])
@@ -197,18 +306,100 @@ def run_reference(args):
         acc += oracle_group(p, circ, openq, T, args.seed, (args.warmup + k) * T)
     dt = time.perf_counter() - t
     val = acc / dt
-    cores = cpu_cores()
     line = {
         "impl": "reference", "metric": METRIC, "value": val, "unit": "samples/s", "n_gpus": args.gpus,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * dt / max(1, args.steps),
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
         "config": workload_config(args),
-        "cpu_baseline": {"value": val, "unit": "samples/s", "cores": cores, "kind": "oracle",
+        "cpu_baseline": {"value": val, "unit": "samples/s", "cores": cores, "kind": "oracle", "cpu": cpu_model(),
                          "sample": "a job of %d groups: the FP64 state vector of the %d-qubit circuit once, then "
                                    "the sampler on %d batches per group" % (args.steps, circ.n_qubits, T)},
         "e2e": {"value": val, "unit": "samples/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line), flush=True)
+
+
+# ---------------------------------------------------------------- our path
+
+def kernel_name(k):
+    if k >= 9000:
+        return "tc_cgemm<%d,%d>" % (k - 9000, {9128: 3, 9064: 4, 9032: 5}.get(k, 0))
+    if k in KERNEL_NAMES:
+        return KERNEL_NAMES[k]
+    return "cgemm_tile<%d,%d>" % (k // 1000, k % 1000)
+
+
+def roofline_of(trace, steps_traced, pk):
+    """The roofline object of the dominant launch of a traced run (most device time),
+    from CUDA events around every contraction launch: tensor-core steps against the
+    measured bf16 dense peak (algorithmic FLOPs, 8 per complex MAC), HBM-bound short
+    products against the measured copy bandwidth (algorithmic bytes: operands read and
+    result written at complex64), FFMA tiles against the derived FP32 peak."""
+    dom = max(trace, key=lambda s: s["ms"])
+    dom_ms = dom["ms"] / max(1, dom["launches"])
+    alg = dom["flops_per_launch"] / (dom_ms / 1e3) / 1e12
+    shape = "(bat,m,n,k bits = %d,%d,%d,%d)" % (dom["nbat"], dom["nm"], dom["nn"], dom["nk"])
+    k = dom["kernel"]
+    if k >= 9000:
+        # the split path issues 3x the algorithmic products on the tensor pipe
+        peak = pk.get("bf16_tflops", 1900.0)
+        roof = {"bound": "tensor", "achieved": alg, "peak": peak, "unit": "TFLOP/s", "traffic": None,
+                "frac": alg / peak, "tensor_pipe_tflops": 3 * alg, "tensor_pipe_frac": 3 * alg / peak,
+                "peak_source": "measured bf16 dense burst (MEASURED_PEAKS.json)" if "bf16_tflops" in pk
+                else "fallback 1.9 PFLOP/s", "kernel": "%s split bf16 hi+lo %s" % (kernel_name(k), shape)}
+    elif k in KERNEL_NAMES:
+        gbs = dom["bytes_per_launch"] / (dom_ms / 1e3) / 1e9
+        peak = pk.get("hbm_gbs", 6800.0)
+        roof = {"bound": "hbm", "achieved": gbs, "peak": peak, "unit": "GB/s", "traffic": None, "frac": gbs / peak,
+                "peak_source": "measured HBM copy (MEASURED_PEAKS.json)" if "hbm_gbs" in pk else "fallback 6.8 TB/s",
+                "kernel": "%s %s%s" % (kernel_name(k), shape, " after a batch-gather launch" if dom["gathers"] else "")}
+    else:
+        ffma_peak = 152 * 128 * 2 * 2.07e9 / 1e12
+        roof = {"bound": "alu", "achieved": alg, "peak": ffma_peak, "unit": "TFLOP/s", "traffic": None,
+                "frac": alg / ffma_peak, "peak_source": "derived: " + FFMA_PEAK_NOTE + " (FP32 FFMA, complex64 path)",
+                "kernel": "%s %s" % (kernel_name(k), shape)}
+    roof["share_of_step"] = dom["ms"] / max(1e-9, sum(s["ms"] for s in trace))
+    fam = {}
+    for x in trace:
+        name = kernel_name(x["kernel"]).split("<")[0]
+        fam[name] = fam.get(name, 0.0) + x["ms"] / steps_traced
+    roof["kernel_family_ms_per_step"] = {n: round(v, 2) for n, v in sorted(fam.items(), key=lambda kv: -kv[1])}
+    rec = MEASURED_TRAFFIC.get((kernel_name(k), (dom["nbat"], dom["nm"], dom["nn"], dom["nk"])))
+    if rec:
+        import hashlib
+        src = os.path.join(ROOT, "paper_2112_15083_gb300", "csrc", rec[1])
+        if hashlib.sha256(open(src, "rb").read()).hexdigest()[:16] == rec[2]:
+            roof["traffic"] = rec[0]
+            roof["traffic_source"] = "ncu dram__bytes_read.sum + dram__bytes_write.sum, one pass (profiles/)"
+    return roof
+
+
+def top_steps_of(trace, n=6):
+    out = []
+    for s in sorted(trace, key=lambda s: -s["ms"])[:n]:
+        ms1 = s["ms"] / max(1, s["launches"])
+        out.append({"shape_bits": [s["nbat"], s["nm"], s["nn"], s["nk"]], "kernel": kernel_name(s["kernel"]),
+                    "ms": round(ms1, 3), "launches": s["launches"],
+                    "tflops": round(s["flops_per_launch"] / (ms1 / 1e3) / 1e12, 2),
+                    "gbs": round(s["bytes_per_launch"] / (ms1 / 1e3) / 1e9, 1), "gathers": s["gathers"]})
+    return out
+
+
+def split_trace(trace):
+    """(contraction steps with launches, slice-sum entries): the last trace entry is the
+    FP64 slice sum (kernel 2, or 3 when it runs fused with the root step)."""
+    ssum = [s for s in trace if s["kernel"] in (2, 3)]
+    steps = [s for s in trace if s["kernel"] not in (2, 3) and s["launches"] > 0]
+    return steps, ssum
+
+
+def slice_sum_of(ssum):
+    if not ssum or not ssum[0]["launches"]:
+        return None
+    s0 = ssum[0]
+    ms1 = s0["ms"] / s0["launches"]
+    return {"ms": round(ms1, 3), "fp64_gflops": round(s0["flops_per_launch"] / (ms1 / 1e3) / 1e9, 1),
+            "gbs": round(s0["bytes_per_launch"] / (ms1 / 1e3) / 1e9, 1), "fused_root_step": s0["kernel"] == 3}
 
 
 def workload_config(args):
@@ -226,20 +417,16 @@ def workload_config(args):
             "l2": "flushed between timed steps; dominant operands exceed L2"}
 
 
-# ---------------------------------------------------------------- our path
-
-def run_ours(args):
+def run_group(args, with_e2e=True, with_cpu=True):
+    """One sampling job of `steps` batch groups over one slice set (the job's first group
+    runs every contraction, later groups reuse the batch-independent intermediates); the
+    JSON line as a dict (rank 0) or None."""
     import numpy as np
     import torch
-    import __graft_entry__
-    rank, world, local = dist_env()
-    torch.cuda.set_device(local)
-    if world > 1:
-        import torch.distributed as dist
-        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
-    __graft_entry__.build()
     import paper_2112_15083_gb300 as P
     from paper_2112_15083_gb300 import circuits as cg
+    from paper_2112_15083_gb300 import replicas
+    rank, world, local = dist_env()
     w = WORKLOADS[args.workload]
     circ = cg.sycamore_grid(w["rows"], w["cols"], w["cycles"], seed=w["seed"])
     openq = cg.default_open_qubits(w["rows"], w["cols"], w["n_open"])
@@ -257,7 +444,6 @@ def run_ours(args):
     acc2 = [torch.empty(T, dtype=torch.uint8, device=dev) for _ in range(args.steps)]
     bits2 = [torch.empty(T, dtype=torch.int64, device=dev) for _ in range(args.steps)]
     flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
-    from paper_2112_15083_gb300 import replicas
     base_t = replicas.batch_t0(rank, 0, T)
     seed = args.seed
     # warm-up: two full groups (the first tunes the kernels, the second captures the full
@@ -273,11 +459,8 @@ def run_ours(args):
     torch.cuda.synchronize()
     clocks.start()
     # timed region: one sampling job of `steps` batch groups over one slice set, each group
-    # as deployed (one CUDA-graph replay of the contraction plus the draw and sampler
-    # launches), L2 flushed in between.  The job's first group runs every contraction; its
-    # later groups reuse the batch-independent intermediates (the stem) that the first
-    # left on the device (tn_sample_step reuse_stem), as tn_sample does for the groups of
-    # one call.  Warm-up leaves nothing the first timed group uses.
+    # one CUDA-graph replay of the contraction plus the draw and sampler launches, L2
+    # flushed in between; warm-up leaves nothing the first timed group uses
     for k in range(args.steps):
         flush.zero_()
         ev0[k].record()
@@ -286,8 +469,7 @@ def run_ours(args):
     torch.cuda.synchronize()
     if world > 1:
         torch.distributed.barrier()
-    step_ms = [ev0[k].elapsed_time(ev1[k]) for k in range(args.steps)]
-    tot_ms = sum(step_ms)
+    tot_ms = sum(ev0[k].elapsed_time(ev1[k]) for k in range(args.steps))
     # the same number of groups, each on its own (the stem recomputed in every group)
     for k in range(args.steps):
         flush.zero_()
@@ -299,8 +481,7 @@ def run_ours(args):
         torch.distributed.barrier()
     clk = clocks.stop()
     solo_ms = sum(ev0[k].elapsed_time(ev1[k]) for k in range(args.steps))
-    # traced region (the job again, CUDA events around every contraction launch): per-launch
-    # device times for the roofline of the dominant kernel, and the job's launch counts
+    # traced region (the job again, CUDA events around every contraction launch)
     plan.trace(True)
     acc_t = torch.empty(T, dtype=torch.uint8, device=dev)
     bits_t = torch.empty(T, dtype=torch.int64, device=dev)
@@ -315,83 +496,16 @@ def run_ours(args):
     accepted2 = int(sum(int(a.sum().item()) for a in acc2))
     solo_ms_max, accepted2_all = replicas.reduce_run(solo_ms, accepted2, device=dev)
     value_solo = accepted2_all / (solo_ms_max / 1e3)
-    # the last trace entry is the FP64 slice sum (kernel 2, or 3 when it runs fused with the
-    # root step, whose own entry then has no launches); the rest are contraction steps
-    ssum = [s for s in trace if s["kernel"] in (2, 3)]
-    trace = [s for s in trace if s["kernel"] not in (2, 3)]
-    # contraction FLOPs per group: a whole group's, and the job's average (the stem once)
-    flops_group = sum(s["flops_per_launch"] for s in trace)
-    trace = [s for s in trace if s["launches"] > 0]
-    flops_step = sum(s["flops_per_launch"] * s["launches"] for s in trace) / args.steps
-    slice_sum = None
-    if ssum and ssum[0]["launches"]:
-        s0 = ssum[0]
-        ms1 = s0["ms"] / s0["launches"]
-        slice_sum = {"ms": round(ms1, 3), "fp64_gflops": round(s0["flops_per_launch"] / (ms1 / 1e3) / 1e9, 1),
-                     "gbs": round(s0["bytes_per_launch"] / (ms1 / 1e3) / 1e9, 1),
-                     "fused_root_step": s0["kernel"] == 3}
-
-    # dominant kernel of the job (most device time) from the live per-launch events
-    dom = max(trace, key=lambda s: s["ms"])
-    dom_ms = dom["ms"] / max(1, dom["launches"])
-    pk = peaks()
-    alg = dom["flops_per_launch"] / (dom_ms / 1e3) / 1e12
-    shape = "(bat,m,n,k bits = %d,%d,%d,%d)" % (dom["nbat"], dom["nm"], dom["nn"], dom["nk"])
-    if dom["kernel"] in (9128, 9064, 9032):
-        # tensor-core step: algorithmic complex FLOPs (8 per complex MAC) against the
-        # measured dense bf16 peak; the split path issues 3x that on the tensor pipe
-        peak = pk.get("bf16_tflops", 1900.0)
-        roofline = {"bound": "tensor", "achieved": alg, "peak": peak, "unit": "TFLOP/s", "traffic": None,
-                    "frac": alg / peak, "tensor_pipe_tflops": 3 * alg, "tensor_pipe_frac": 3 * alg / peak,
-                    "peak_source": "measured bf16 dense burst (MEASURED_PEAKS.json)" if "bf16_tflops" in pk
-                    else "fallback 1.9 PFLOP/s",
-                    "kernel": "tc_cgemm<%d,%d> split bf16 hi+lo %s" % (
-                        dom["kernel"] - 9000, {9128: 3, 9064: 4, 9032: 5}[dom["kernel"]], shape)}
-    elif dom["kernel"] in (0, 1, 4):
-        # short products (row kernel, staged small kernel): algorithmic bytes (operands
-        # read + result written, complex64; gathered operands at their batch size)
-        # against the measured copy bandwidth
-        gbs = dom["bytes_per_launch"] / (dom_ms / 1e3) / 1e9
-        peak = pk.get("hbm_gbs", 6800.0)
-        roofline = {"bound": "hbm", "achieved": gbs, "peak": peak, "unit": "GB/s", "traffic": None, "frac": gbs / peak,
-                    "peak_source": "measured HBM copy (MEASURED_PEAKS.json)" if "hbm_gbs" in pk else "fallback 6.8 TB/s",
-                    "kernel": "%s %s%s" % ({0: "cgemm_row", 1: "cgemm_small", 4: "cgemm_rowstage"}[dom["kernel"]], shape,
-                                           " after a batch-gather launch" if dom["gathers"] else "")}
-    else:
-        ffma_peak = 152 * 128 * 2 * 2.07e9 / 1e12
-        roofline = {"bound": "alu", "achieved": alg, "peak": ffma_peak, "unit": "TFLOP/s", "traffic": None,
-                    "frac": alg / ffma_peak, "peak_source": "derived: " + FFMA_PEAK_NOTE + " (FP32 FFMA, complex64 path)",
-                    "kernel": "cgemm_tile<%d,%d> %s" % (dom["kernel"] // 1000, dom["kernel"] % 1000, shape)}
-    roofline["share_of_step"] = dom["ms"] / max(1e-9, sum(s["ms"] for s in trace))
-    # device time per kernel family, averaged over the job's groups
-    fam = {}
-    for x in trace:
-        k = x["kernel"]
-        name = ("tc_cgemm" if k >= 9000 else {0: "cgemm_row", 1: "cgemm_small", 4: "cgemm_rowstage"}.get(k, "cgemm_tile"))
-        fam[name] = fam.get(name, 0.0) + x["ms"] / args.steps
-    roofline["kernel_family_ms_per_step"] = {k: round(v, 2) for k, v in sorted(fam.items(), key=lambda kv: -kv[1])}
-    key = {9128: "tc_cgemm<128,3>", 0: "cgemm_row"}.get(dom["kernel"])
-    rec = MEASURED_TRAFFIC.get((key, (dom["nbat"], dom["nm"], dom["nn"], dom["nk"]))) if key else None
-    if rec:
-        import hashlib
-        src = os.path.join(ROOT, "paper_2112_15083_gb300", "csrc", rec[1])
-        if hashlib.sha256(open(src, "rb").read()).hexdigest()[:16] == rec[2]:
-            roofline["traffic"] = rec[0]
-            roofline["traffic_source"] = "ncu dram__bytes_read.sum + dram__bytes_write.sum, one pass, full size (profiles/)"
+    flops_group = sum(s["flops_per_launch"] for s in trace if s["kernel"] not in (2, 3))
+    steps_tr, ssum = split_trace(trace)
+    flops_step = sum(s["flops_per_launch"] * s["launches"] for s in steps_tr) / args.steps
+    roofline = roofline_of(steps_tr, args.steps, peaks())
     roofline["measured"] = "CUDA events around each contraction launch over %d traced steps" % args.steps
-    top_steps = []
-    for s in sorted(trace, key=lambda s: -s["ms"])[:6]:
-        ms1 = s["ms"] / max(1, s["launches"])
-        top_steps.append({"shape_bits": [s["nbat"], s["nm"], s["nn"], s["nk"]], "kernel": s["kernel"],
-                          "ms": round(ms1, 3), "launches_per_job": s["launches"],
-                          "tflops": round(s["flops_per_launch"] / (ms1 / 1e3) / 1e12, 2),
-                          "gbs": round(s["bytes_per_launch"] / (ms1 / 1e3) / 1e9, 1)})
 
-    # end to end through the public API with host buffers: the same job as one tn_sample
-    # call (selection of the slices included), about one group's expected samples
-    # (T (1 - eps) / alpha) per step
     e2e = None
-    if rank == 0:
+    if rank == 0 and with_e2e:
+        # the same job as one tn_sample call (selection included) with host output, about
+        # one group's expected samples (T (1 - eps) / alpha) per step
         n_job = int(0.47 * T) * args.steps
         torch.cuda.synchronize()
         t = time.perf_counter()
@@ -400,44 +514,246 @@ def run_ours(args):
         groups = (st["steps"] + T - 1) // T
         e2e = {"value": len(b) / dt, "unit": "samples/s", "h2d_bytes_per_step": 0,
                "d2h_bytes_per_step": int((groups * T * (1 + 8 + 8) + n_job * 8) / args.steps),
-               "api": "tn_sample(host bitstrings): one call for the job's %d samples" % n_job,
-               "groups": groups}
+               "api": "tn_sample(host bitstrings): one call for the job's %d samples" % n_job, "groups": groups}
+
+    cpu = None
+    if rank == 0 and world == 1 and with_cpu and not args.no_cpu_baseline:
+        cpu = group_cpu_baseline(circ, openq, T, seed, args.steps)
+
+    if rank != 0:
+        return None
+    return {
+        "metric": METRIC, "value": value, "unit": "samples/s", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": tot_ms_max / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None,
+        "dtype": ("bf16x2 split hi+lo on tcgen05, fp32 accumulation (small steps c64 FFMA); fp64 slice sum/sampler"
+                  if args.precision == "bf16x2" else "c64 (fp32 FFMA), fp64 slice sum/sampler"),
+        "data": "synthetic", "config": workload_config(args),
+        "fidelity": F, "contraction_tflops": flops_step * args.steps / (tot_ms / 1e3) / 1e12,
+        "flops_per_step": flops_step, "flops_per_group_with_stem": flops_group,
+        "stem": "the job's first group runs every contraction; its later groups reuse the batch-independent "
+                "intermediates (tn_sample_step reuse_stem)",
+        "value_stem_each_step": value_solo, "ms_per_step_stem_each_step": solo_ms_max / args.steps,
+        "plan": info, "clocks": clk, "roofline": roofline,
+        "cpu_baseline": cpu, "e2e": e2e, "top_steps": top_steps_of(steps_tr), "slice_sum": slice_sum_of(ssum),
+        # the job's contraction launches, batch gathers and slice sums, plus a batch draw and
+        # a sampler launch per step
+        "gpu_launches": (sum(s["launches"] * (1 + s["gathers"]) for s in steps_tr)
+                         + sum(s["launches"] for s in ssum) + 2 * args.steps),
+    }
+
+
+def group_cpu_baseline(circ, openq, T, seed, groups):
+    """The oracle on the same job (its state vector once, then the sampler on `groups`
+    groups of T batches), on all host cores, and the state vector single-threaded."""
+    cores = cpu_cores()
+    os.environ["OMP_NUM_THREADS"] = str(cores)
+    t = time.perf_counter()
+    p = oracle_probs(circ)
+    a = sum(oracle_group(p, circ, openq, T, seed, g * T) for g in range(groups))
+    del p
+    dt = time.perf_counter() - t
+    return {"value": a / dt, "unit": "samples/s", "cores": cores, "kind": "oracle", "cpu": cpu_model(),
+            "sample": "a job of %d groups: the FP64 state vector of the %d-qubit circuit once, then the sampler on %d "
+                      "batches per group (%d accepted in %.1f s)" % (groups, circ.n_qubits, T, a, dt)}
+
+
+def job_groups_for(N, alpha, T):
+    """The job's batch groups (as tn_job_create draws them)."""
+    need = 1.1 * alpha * N + 8.0 * math.sqrt(alpha * N) + 64.0
+    return max(1, math.ceil(need / T))
+
+
+def plan_job_workload(args, P, C, openq, w, precision):
+    """The largest tensor cap whose one-slice working set fits, with the order search
+    weighting the batch steps by the job's groups."""
+    import numpy as np
+    T = 1 << log2_batches(args)
+    groups = job_groups_for(w["N"], w["alpha"], T)
+    plan = None
+    for cap in w["caps"]:
+        plan = P.plan(C, openq, log2_batches=log2_batches(args), order_trials=args.trials, order_seed=0,
+                      max_log2_tensor=cap, hbm_budget_bytes=w["budget"], precision=precision, autotune=args.autotune,
+                      max_norm_flops=3e16, job_groups=groups, anneal_iters=args.anneal)
+        if plan.estimate(np.zeros(1, np.uint64))[0] <= w["slice_bytes_max"]:
+            break
+    return plan, cap, groups
+
+
+def job_config(args, w):
+    """The workload of a job line (identical in both arms); plan-dependent figures go to
+    the line's `job` object."""
+    q = w["rows"] * w["cols"]
+    T = 1 << log2_batches(args)
+    return {"workload": "%s: %d-qubit %dx%d Sycamore-style ABCD circuit, %d cycles, fSim(pi/2,pi/6); %d samples at "
+                        "fidelity %g (Alg. 1 slice selection); batches of 64 bitstrings, %d per group" % (
+                            args.workload, q, w["rows"], w["cols"], w["cycles"], w["N"], args.fidelity, T),
+            "qubits": q, "cycles": w["cycles"], "samples": w["N"], "fidelity_target": args.fidelity,
+            "alpha": w["alpha"], "batch_size": 64, "batches_per_group": T, "order_trials": args.trials,
+            "precision": args.precision, "chunk_slices": args.chunk, "anneal_iters": int(args.anneal),
+            "step": "one slice chunk of the job contracted for all of its batch groups (batch-independent "
+                    "intermediates once) and added to its FP64 amplitude sums",
+            "projection": "value = samples / (chunks x mean timed chunk + the final accept/pick pass); the job's "
+                          "chunks are identical in shape and work",
+            "l2": "not flushed: every chunk's working set (tens of GB) exceeds L2"}
+
+
+def run_job(args):
+    import numpy as np
+    import torch
+    import paper_2112_15083_gb300 as P
+    from paper_2112_15083_gb300 import circuits as cg
+    from paper_2112_15083_gb300 import replicas
+    rank, world, local = dist_env()
+    w = JOB_WORKLOADS[args.workload]
+    N, alpha = w["N"], w["alpha"]
+    circ = cg.sycamore_grid(w["rows"], w["cols"], w["cycles"], seed=w["seed"])
+    openq = cg.default_open_qubits(w["rows"], w["cols"], w["n_open"])
+    C = P.circuit_load(circ.serialize())
+    prec = {"c64": P.tn.PREC_C64, "bf16x2": P.tn.PREC_BF16X2}[args.precision]
+    t = time.perf_counter()
+    plan, cap, _ = plan_job_workload(args, P, C, openq, w, prec)
+    plan_s = time.perf_counter() - t
+    plan_info = plan.info()
+    seed = args.seed + rank  # replicas: independent Philox keys
+    t = time.perf_counter()
+    job = plan.job(args.fidelity, N, seed, alpha=alpha, max_chunk_slices=args.chunk)
+    create_s = time.perf_counter() - t
+    info = job.info()
+    need = args.warmup + args.steps + 1
+    if info["n_chunks"] < need:
+        raise SystemExit("the job has %d chunks; warm-up + steps + a traced chunk need %d" % (info["n_chunks"], need))
+    # warm-up: the first chunks of the job (kernel autotuning, graph capture)
+    for c in range(args.warmup):
+        job.run(c, 1)
+    torch.cuda.synchronize()
+    clocks = Clocks(local)
+    ev0 = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    ev1 = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    if world > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+    clocks.start()
+    # timed region: the next `steps` chunks of the job, each contracted for every batch
+    # group and added to the job's amplitude sums (CUDA events on the plan's stream)
+    for k in range(args.steps):
+        ev0[k].record()
+        job.run(args.warmup + k, 1)
+        ev1[k].record()
+    torch.cuda.synchronize()
+    if world > 1:
+        torch.distributed.barrier()
+    clk = clocks.stop()
+    chunk_ms = [ev0[k].elapsed_time(ev1[k]) for k in range(args.steps)]
+    tot_ms = sum(chunk_ms)
+    # the job's final pass (accept / pick over every batch, host output)
+    torch.cuda.synchronize()
+    t = time.perf_counter()
+    _bits, st = job.finish(partial=True)
+    finish_s = time.perf_counter() - t
+    # one more chunk traced (CUDA events around every launch): per-launch device times
+    plan.trace(True)
+    job.run(args.warmup + args.steps, 1)
+    trace = plan.trace_read()
+    plan.trace(False)
+    steps_tr, ssum = split_trace(trace)
+    job_s = info["n_chunks"] * (tot_ms / args.steps) / 1e3 + finish_s
+    job_s_max, n_all = replicas.reduce_run(job_s * 1e3, N, device=torch.device("cuda", local))
+    value = n_all / (job_s_max / 1e3)
+    roofline = roofline_of(steps_tr, 1, peaks())
+    roofline["measured"] = "CUDA events around each launch of one traced chunk (%d groups)" % info["groups"]
+    del job
+
+    e2e = None
+    if rank == 0:
+        # the same job through the public API with host output: creation (slice selection,
+        # batch draws), chunks, the final pass; projected to all chunks as `value`
+        ke = max(2, args.steps // 4)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        job2 = plan.job(args.fidelity, N, seed + 7919, alpha=alpha, max_chunk_slices=args.chunk)
+        t1 = time.perf_counter()
+        job2.run(0, ke)
+        t2 = time.perf_counter()
+        job2.finish(partial=True)
+        t3 = time.perf_counter()
+        inf2 = job2.info()
+        del job2
+        e2e_s = (t1 - t0) + inf2["n_chunks"] * (t2 - t1) / ke + (t3 - t2)
+        nb = inf2["groups"] * inf2["T"]
+        e2e = {"value": N / e2e_s, "unit": "samples/s", "h2d_bytes_per_step": 0,
+               "d2h_bytes_per_step": int((nb * (1 + 8 + 8) + N * 8) / inf2["n_chunks"]),
+               "api": "tn_job_create + tn_job_run + tn_job_finish (host bitstrings), the calls tn_sample makes; "
+                      "%d chunks timed, projected to the job's %d" % (ke, inf2["n_chunks"]),
+               "create_s": round(t1 - t0, 3), "chunk_s": round((t2 - t1) / ke, 4), "finish_s": round(t3 - t2, 4)}
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        os.environ.setdefault("OMP_NUM_THREADS", str(cpu_cores()))
-        t = time.perf_counter()
-        p = oracle_probs(circ)
-        a = sum(oracle_group(p, circ, openq, T, seed, g * T) for g in range(3))
-        del p
-        dt = time.perf_counter() - t
-        cpu = {"value": a / dt, "unit": "samples/s", "cores": int(os.environ["OMP_NUM_THREADS"]), "kind": "oracle",
-               "sample": "a job of 3 groups: the FP64 state vector of the %d-qubit circuit once, then the sampler "
-                         "on %d batches per group (%d accepted in %.1f s)" % (circ.n_qubits, T, a, dt)}
+        cpu = job_cpu_baseline(circ, openq, plan, info, w)
 
-    if rank == 0:
-        line = {
-            "metric": METRIC, "value": value, "unit": "samples/s", "n_gpus": world, "steps": args.steps,
-            "warmup": args.warmup, "ms_per_step": tot_ms_max / args.steps, "higher_is_better": True,
-            "scaling": "weak", "vs_baseline": None,
-            "dtype": ("bf16x2 split hi+lo on tcgen05, fp32 accumulation (small steps c64 FFMA); fp64 slice sum/sampler"
-                      if args.precision == "bf16x2" else "c64 (fp32 FFMA), fp64 slice sum/sampler"),
-            "data": "synthetic", "config": workload_config(args),
-            "fidelity": F, "contraction_tflops": flops_step * args.steps / (tot_ms / 1e3) / 1e12,
-            "flops_per_step": flops_step, "flops_per_group_with_stem": flops_group,
-            "stem": "the job's first group runs every contraction; its later groups reuse the batch-independent "
-                    "intermediates (tn_sample_step reuse_stem)",
-            "value_stem_each_step": value_solo, "ms_per_step_stem_each_step": solo_ms_max / args.steps,
-            "plan": info, "clocks": clk, "roofline": roofline,
-            "cpu_baseline": cpu, "e2e": e2e, "top_steps": top_steps, "slice_sum": slice_sum,
-            # the job's contraction launches, batch gathers and slice sums, plus a batch draw
-            # and a sampler launch per step
-            "gpu_launches": (sum(s["launches"] * (1 + s["gathers"]) for s in trace)
-                             + sum(s["launches"] for s in ssum) + 2 * args.steps),
-        }
+    secondary = None
+    if rank == 0 and world == 1 and not args.no_secondary:
+        secondary = secondary_lines(args)
+
+    if rank != 0:
+        return None
+    per_chunk_launches = (sum(s["launches"] * (1 + s["gathers"]) for s in steps_tr) + sum(s["launches"] for s in ssum)
+                          + info["groups"])
+    return {
+        "metric": METRIC, "value": value, "unit": "samples/s", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": tot_ms / args.steps, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None,
+        "dtype": ("bf16x2 split hi+lo on tcgen05, fp32 accumulation (small steps c64 FFMA); fp64 slice and chunk "
+                  "sums, fp64 sampler" if args.precision == "bf16x2" else "c64 (fp32 FFMA); fp64 sums and sampler"),
+        "data": "synthetic", "config": job_config(args, w),
+        "job": {"sliced_legs": plan_info["n_sliced"], "max_log2_tensor_cap": cap, "retained_slices": info["n_slices"],
+                "chunk_slices": info["chunk_slices"], "chunks": info["n_chunks"], "groups": info["groups"],
+                "batches": info["groups"] * info["T"]},
+        "fidelity": info["F"], "job_seconds": job_s, "job_hours": job_s / 3600.0,
+        "chunk_ms": [round(x, 2) for x in chunk_ms], "finish_s": finish_s,
+        "contraction_tflops": info["flops_chunk"] / (tot_ms / args.steps / 1e3) / 1e12,
+        "flops_per_chunk": info["flops_chunk"], "plan_seconds": plan_s, "job_create_seconds": create_s,
+        "eps_hat_partial": st["eps_hat"], "plan": plan_info, "clocks": clk, "roofline": roofline,
+        "cpu_baseline": cpu, "e2e": e2e, "top_steps": top_steps_of(steps_tr, 8), "slice_sum": slice_sum_of(ssum),
+        "secondary": secondary,
+        # per chunk: every contraction launch, its gathers and slice sums, one amplitude
+        # accumulation per group (counted from the traced chunk)
+        "gpu_launches": per_chunk_launches * args.steps,
+    }
+
+
+def secondary_lines(args):
+    """The 28-qubit workload at fidelity 1 in split bf16 and complex64 (same plan recipe)."""
+    out = {}
+    for prec in ("bf16x2", "c64"):
+        a = argparse.Namespace(**vars(args))
+        a.workload, a.precision, a.fidelity, a.steps, a.warmup = "grid4x7_m14", prec, 1.0, 5, 3
+        a.log2_batches, a.fuse_root, a.anneal = None, 0, 0
+        line = run_group(a, with_e2e=False, with_cpu=False)
+        out["grid4x7_m14_" + prec] = {
+            "value": line["value"], "ms_per_step": line["ms_per_step"], "steps": a.steps, "fidelity": line["fidelity"],
+            "value_stem_each_step": line["value_stem_each_step"],
+            "roofline": {k: line["roofline"][k] for k in ("kernel", "bound", "achieved", "unit", "frac")},
+            "top_steps": line["top_steps"][:3]}
+    out["split_over_c64"] = out["grid4x7_m14_bf16x2"]["value"] / out["grid4x7_m14_c64"]["value"]
+    return out
+
+
+def run_ours(args):
+    import torch
+    import __graft_entry__
+    rank, world, local = dist_env()
+    torch.cuda.set_device(local)
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    __graft_entry__.build()
+    line = run_job(args) if args.workload in JOB_WORKLOADS else run_group(args)
+    if line is not None:
         print(json.dumps(line), flush=True)
     if world > 1:
         torch.distributed.destroy_process_group()
+
 
 
 # ---------------------------------------------------------------- serving
@@ -531,107 +847,11 @@ def run_serve(args):
     print(json.dumps(line), flush=True)
 
 
-def run_grid5x8_sample(args):
-    """Bounded sample of the 40-qubit configuration (5x8 grid, 16 cycles, 1/64 of the
-    slices retained, 100k samples): the plan slices legs until one slice's tensors fit
-    2^30 elements, Alg. 1 selects the retained slices, and the first retained slices are
-    contracted for one group of 4096 batches, alone and two at a time (shared
-    intermediates).  The full job's time is extrapolated from the measured time per
-    slice and group; nothing of it is run."""
-    import math
-    import numpy as np
-    import torch
-    import __graft_entry__
-    torch.cuda.set_device(0)
-    __graft_entry__.build()
-    import paper_2112_15083_gb300 as P
-    from paper_2112_15083_gb300 import circuits as cg
-    rows, cols, cycles, lb, f, N, alpha = 5, 8, 16, 12, 1.0 / 64, 100000, 2.0
-    circ = cg.sycamore_grid(rows, cols, cycles, seed=0)
-    openq = cg.default_open_qubits(rows, cols, 6)
-    C = P.circuit_load(circ.serialize())
-    # the job's batch groups: the order search weights the batch steps by them (the
-    # batch-independent ones run once per slice)
-    job_groups = math.ceil(1.1 * alpha * N / (1 << lb))
-    t = time.perf_counter()
-    # the largest tensor cap whose one-slice working set fits the budget
-    for cap in (30, 29, 28, 27, 26):
-        plan = P.plan(C, openq, log2_batches=lb, order_trials=256, order_seed=0, max_log2_tensor=cap,
-                      hbm_budget_bytes=150e9, precision=P.tn.PREC_BF16X2, autotune=0, max_norm_flops=3e16,
-                      job_groups=job_groups)
-        if plan.estimate(np.zeros(1, np.uint64))[0] <= 140e9:
-            break
-        del plan
-    plan_s = time.perf_counter() - t
-    info = plan.info()
-    line = {"metric": "40-qubit bounded sample: seconds per retained slice per batch group (shared part amortised)",
-            "unit": "s",
-            "data": "synthetic", "n_gpus": 1,
-            "config": {"workload": "grid5x8_m16: 40-qubit 5x8 Sycamore-style ABCD circuit, 16 cycles, seed 0; "
-                                   "slices until one slice's working set fits 140 GB; f = 1/64; %d batches of 64 "
-                                   "per group; bf16x2" % (1 << lb)},
-            "plan": {"seconds": round(plan_s, 1), "sliced_legs": info["n_sliced"], "max_log2_tensor_cap": cap,
-                     "job_groups": job_groups,
-                     "log2_max_tensor": info["log2_max_tensor"], "flops_all_slices": info["flops_all_slices"]}}
-    t = time.perf_counter()
-    try:
-        slices, F = plan.select(f)
-        line["selection"] = {"seconds": round(time.perf_counter() - t, 1), "retained_slices": int(len(slices)),
-                             "F": F}
-    except P.TnError as e:
-        line["selection"] = {"error": str(e)}
-        print(json.dumps(line), flush=True)
-        return
-    T = 1 << lb
-    cb = np.random.default_rng(1).integers(0, 1 << 34, size=2 * T, dtype=np.int64).astype(np.uint64)
-    samples = []
-    for chunk in (1, 2):
-        sl = slices[:chunk]
-        nbytes, fl_first, fl_next = plan.estimate(sl)
-        row = {"slices": chunk, "device_bytes": nbytes, "flops_first_group": fl_first, "flops_later_group": fl_next}
-        for groups in (1, 2):
-            plan.contract(sl, cb[: groups * T])  # first execution (leaves, call plan, graphs)
-            torch.cuda.synchronize()
-            t = time.perf_counter()
-            plan.contract(sl, cb[: groups * T])
-            torch.cuda.synchronize()
-            row["seconds_%d_group%s" % (groups, "s" if groups > 1 else "")] = round(time.perf_counter() - t, 4)
-        # one group = batch-independent part + batch part; each later group adds the batch part
-        row["batch_part_s"] = round(row["seconds_2_groups"] - row["seconds_1_group"], 4)
-        row["shared_part_s"] = round(row["seconds_1_group"] - row["batch_part_s"], 4)
-        row["tflops_first_group"] = round(fl_first / row["seconds_1_group"] / 1e12, 1)
-        samples.append(row)
-    line["samples"] = samples
-    # per-step device times of one slice over two groups (the second reuses the shared part)
-    plan.trace(True)
-    plan.contract(slices[:1], cb[: 2 * T])
-    tr = plan.trace_read()
-    plan.trace(False)
-    tops = sorted(tr, key=lambda x: -x["ms"])[:10]
-    line["top_steps"] = [{"shape_bits": [x["nbat"], x["nm"], x["nn"], x["nk"]], "kernel": x["kernel"],
-                          "launches": x["launches"], "ms": round(x["ms"], 3),
-                          "tflops": round(x["flops_per_launch"] * x["launches"] / max(1e-9, x["ms"] / 1e3) / 1e12, 1),
-                          "gbs": round(x["bytes_per_launch"] * x["launches"] / max(1e-9, x["ms"] / 1e3) / 1e9, 1),
-                          "gathers": x["gathers"]} for x in tops]
-    groups = math.ceil(1.1 * alpha * N / T)
-    best = min(samples, key=lambda r: (r["shared_part_s"] + groups * r["batch_part_s"]) / r["slices"])
-    per_slice = (best["shared_part_s"] + groups * best["batch_part_s"]) / best["slices"]
-    hours = per_slice * len(slices) / 3600.0
-    line["value"] = round(per_slice / groups, 4)
-    line["extrapolated"] = {"groups": groups, "retained_slices": int(len(slices)),
-                            "seconds_per_slice_all_groups": round(per_slice, 3), "hours": round(hours, 1),
-                            "note": "retained slices x (shared part + groups x batch part) per slice, from the "
-                                    "measured chunk of %d slice(s); the job itself is not run" % best["slices"]}
-    print(json.dumps(line), flush=True)
-
-
 if __name__ == "__main__":
     a = parse()
     if a.impl == "reference":
         run_reference(a)
     elif a.serve:
         run_serve(a)
-    elif a.grid5x8_sample:
-        run_grid5x8_sample(a)
     else:
         run_ours(a)

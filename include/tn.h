@@ -289,7 +289,9 @@ typedef struct {
  * t = 0, 1, ... draw j_t uniformly, contract the batch j_t over the slices, set
  * p_{i,j} = |a_{i,j}|^2 / F, accept with probability min(1, p_j N_B / alpha) and pick i
  * with probability p_{i,j}/p_j.  Batches are processed 2^log2_batches at a time until N
- * are accepted (at most ceil(8 alpha N) + 4096 batches).  Random numbers: Philox4x32-10
+ * are accepted (at most ceil(8 alpha N) + 4096 batches).  When the selected slice set does
+ * not fit the plan's HBM budget in one execution, the call runs a sampling job instead
+ * (tn_job_create with automatic chunks, every chunk, tn_job_finish).  Random numbers: Philox4x32-10
  * with key = seed and counter = (t, stream): stream 0 gives j (low |B| bits of words
  * 0-1) and u (words 2-3), stream 1 gives v; a 64-bit word w maps to (w >> 11) 2^-53.
  * Accept iff u*alpha < p_j*N_B.  Requires n_open = 6.
@@ -298,6 +300,66 @@ typedef struct {
  */
 int tn_sample(tn_plan_h p, double f_target, int64_t N, uint64_t seed, double alpha,
               uint64_t *bitstrings, int32_t flags, tn_sample_stats *stats);
+
+/*
+ * Sampling job over a slice set larger than one execution's memory (Sec. I.C step 1 with
+ * Sec. II.A).  The retained slices X x {0,1}^{|I|-k} of tn_select are split into chunks
+ * of chunk_slices consecutive slices (the same low free legs vary inside every chunk);
+ * the job's batches t = 0 .. groups * T - 1 (T = 2^log2_batches) are drawn once (Philox,
+ * as in tn_sample).  tn_job_run contracts chunks for every batch group: per chunk the
+ * batch-independent intermediates are computed once and reused by all groups, and each
+ * group's sum over the chunk's slices is added in FP64 to that group's amplitudes, chunk
+ * after chunk in chunk order.  tn_job_finish then runs the accept / pick step of
+ * tn_sample on all batches (p = |a|^2 / F) and returns the first N accepted strings in t
+ * order.  groups = ceil((1.1 alpha N + 8 sqrt(alpha N) + 64) / T) batches are drawn, so
+ * that N accepted strings are all but certain; TN_EINVAL reports a shortfall.
+ * The job owns device buffers of groups * T * (64 * 16 + 8) bytes (from the plan's
+ * allocator) until tn_job_destroy.  Requires n_open = 6.
+ */
+typedef struct tn_job_s *tn_job_h;
+
+typedef struct {
+    int64_t n_slices;      /* retained slices */
+    double F;              /* their fidelity (Alg. 1) */
+    int64_t chunk_slices;  /* slices per chunk */
+    int64_t n_chunks;
+    int64_t groups;        /* batch groups of T batches */
+    int64_t T;             /* batches per group */
+    int64_t chunks_done;   /* chunks contracted so far */
+    double flops_done;     /* algorithmic FLOPs of the chunks contracted so far */
+    double flops_chunk;    /* algorithmic FLOPs of one chunk over all groups (stem once) */
+} tn_job_info;
+
+/*
+ * Create a job for N samples at fidelity f_target.  max_chunk_slices > 0 caps the chunk
+ * (rounded down to a power of two); 0 picks the largest power of two whose working set
+ * (tn_plan_estimate) plus the job's buffers fits the plan's HBM budget.
+ * Errors: TN_EINVAL (arguments, n_open != 6), TN_ENOMEM (not even one slice fits).
+ */
+int tn_job_create(tn_plan_h p, double f_target, int64_t N, uint64_t seed, double alpha,
+                  int64_t max_chunk_slices, tn_job_h *out, tn_job_info *info);
+
+/* Contract chunks first .. first + count - 1 for every group and add them to the job's
+ * amplitudes; synchronises.  Each chunk may run once (TN_EINVAL otherwise). */
+int tn_job_run(tn_job_h j, int64_t first, int64_t count);
+
+int tn_job_get_info(tn_job_h j, tn_job_info *info);
+
+/* The accumulated amplitudes of group g (T * 64 complex128, batch-major), unnormalised,
+ * into a host array; synchronises. */
+int tn_job_amplitudes(tn_job_h j, int64_t g, double *amps);
+
+/*
+ * Accept / pick over every batch of the job and the first N accepted strings in t order
+ * (host array; stats as tn_sample).  Unless flags & TN_JOB_PARTIAL, every chunk must have
+ * run (TN_EINVAL otherwise); with it, the sums over the chunks run so far are sampled
+ * (not the target distribution: for timing only) and fewer than N accepted strings is not
+ * an error (stats->accepted says how many were written).
+ */
+#define TN_JOB_PARTIAL 2
+int tn_job_finish(tn_job_h j, uint64_t *bitstrings, int32_t flags, tn_sample_stats *stats);
+
+void tn_job_destroy(tn_job_h j);
 
 /*
  * One sampling step over one batch group (Sec. II.A for t = t0 .. t0 + T - 1, T =
@@ -311,6 +373,17 @@ int tn_sample(tn_plan_h p, double f_target, int64_t N, uint64_t seed, double alp
 int tn_sample_step(tn_plan_h p, const uint64_t *slices, int64_t n_slices, double F, uint64_t seed,
                    uint64_t t0, double alpha, int32_t reuse_stem, uint8_t *accept, uint64_t *bits,
                    int32_t flags);
+
+/*
+ * Test hook for failure detection (the paper has no counterpart).  With cycles > 0, every
+ * tensor-core launch of the plan's later executions first makes its MMA warp wait on a
+ * shared-memory barrier that nothing arrives on, giving up after about `cycles` SM clock
+ * cycles.  The launch then takes its bounded-wait exit: the CTA records the error word,
+ * waits (bounded) for the tile copies it already issued, frees its tensor memory and
+ * returns, and the call that synchronises reports TN_ETIMEOUT with the outputs undefined.
+ * cycles = 0 restores normal operation; the plan stays usable.  cycles <= 4e9.
+ */
+int tn_plan_test_stall(tn_plan_h p, int64_t cycles);
 
 /* Tracing: when on, every execution records CUDA events around each contraction step
  * and around the FP64 slice sum on the plan's stream.  tn_trace_read synchronises and

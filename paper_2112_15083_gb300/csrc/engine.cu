@@ -11,8 +11,10 @@
 #include <cmath>
 #include <cstring>
 #include <map>
+#include <memory>
 #include <mutex>
 #include <numeric>
+#include <type_traits>
 #include <unordered_map>
 
 #include <cudaTypedefs.h>
@@ -143,6 +145,8 @@ struct CNet {
     int autotune = 1;          // 1: time the applicable variants of unseen step shapes;
                                // 0: fixed shape rules; k >= 2: variant (step + k - 2) mod count
     bool fuse_root = false;    // run a row-kernel root step fused with the slice sum
+    long long tc_stall = 0;    // tests only: tensor-core launches first wait this many cycles
+                               // on a barrier nothing arrives on (see tn_plan_test_stall)
     DBuf err;                  // device error word of the bounded waits
     int *d_err = nullptr;
     // CUDA graphs of one execution (index: stem reuse off / on), valid for the current
@@ -610,7 +614,8 @@ int prepare_call(DevMem &mem, CNet &cn, const std::vector<uint64_t> &slices, dou
 
 // Kernel variants of a step (ids as in tn_step_trace.kernel): 0 row kernel, 1 staged
 // small products, TM*1000+TN FFMA tile, 9128 / 9064 tensor-core tile of 128 / 64 columns.
-constexpr int kVarRow = 0, kVarSmall = 1, kVarRowStage = 4, kVarTc128 = 9128, kVarTc64 = 9064, kVarTc32 = 9032;
+constexpr int kVarRow = 0, kVarSmall = 1, kVarRowStage = 4, kVarSkinny = 5, kVarTc128 = 9128, kVarTc64 = 9064,
+              kVarTc32 = 9032;
 
 // Whether the staged row kernel can run step si: the row kernel's shapes with complex64
 // rows of 16 to 64 elements.
@@ -618,6 +623,13 @@ bool rowstage_fits(const CNet &cn, const Step &s) {
     return cn.elem == 8 && std::min(s.nm, s.nn) <= 5 && s.nk >= 4 && s.nk <= 6;
 }
 constexpr int kTiles[7][2] = {{128, 64}, {64, 64}, {128, 32}, {64, 32}, {32, 32}, {128, 16}, {16, 16}};
+
+// Whether the long-K kernel runs step si: at most 8 rows and 8 columns, K >= 1024, complex64
+// operands.  It is then the step's only kernel (its lane split of K rounds differently).
+bool skinny_fits(const CNet &cn, const Step &s) {
+    return cn.elem == 8 && s.nm <= 3 && s.nn <= 3 && s.nk >= 10 && cn.fmt[s.a] == tnk::OUT_C64 &&
+           cn.fmt[s.b] == tnk::OUT_C64 && (cn.use_tc.empty() || !cn.use_tc[&s - cn.steps.data()]);
+}
 
 bool small_fits(const Step &s, size_t esz) {
     return s.nm <= 6 && s.nn <= 6 && s.nk <= 6 && s.nbat >= 4 &&
@@ -628,6 +640,7 @@ bool small_fits(const Step &s, size_t esz) {
 std::vector<int> step_variants(const CNet &cn, size_t si) {
     const Step &s = cn.steps[si];
     std::vector<int> v;
+    if (skinny_fits(cn, s)) return {kVarSkinny};
     if (!cn.use_tc.empty() && cn.use_tc[si]) {
         if (s.nn <= 5) return {kVarTc32, kVarTc64};
         if (s.nn == 6) return {kVarTc128, kVarTc64, kVarTc32};
@@ -644,6 +657,7 @@ std::vector<int> step_variants(const CNet &cn, size_t si) {
 // The fixed shape rules used without autotuning.
 int default_variant(const CNet &cn, size_t si) {
     const Step &s = cn.steps[si];
+    if (skinny_fits(cn, s)) return kVarSkinny;
     if (!cn.use_tc.empty() && cn.use_tc[si]) return s.nn <= 5 ? kVarTc32 : kVarTc128;
     if (std::min(s.nm, s.nn) == 6 && std::max(s.nm, s.nn) == 6 && small_fits(s, (size_t)cn.elem)) return kVarSmall;
     if (std::min(s.nm, s.nn) <= 5 && s.nk <= 6) return kVarRow;
@@ -676,6 +690,27 @@ bool row_fuses(const CNet &cn, size_t si) {
     return true;
 }
 
+// The long-K kernel reads a gathered operand in place when it is a single complex version
+// whose every row (K elements) is contiguous in its source.
+bool skinny_fuses(const CNet &cn, size_t si) {
+    const Step &s = cn.steps[si];
+    if (!(s.gat[0] || s.gat[1]) || cn.cp.gd_off.size() <= si + 1) return false;
+    for (int o = 0; o < 2; o++) {
+        if (!s.gat[o]) continue;
+        const tnk::GatherDesc &g = cn.cp.gd[cn.cp.gd_off[si] + (o == 1 && s.gat[0] ? 1 : 0)];
+        if (g.nver != 1 || g.nplanes != 1 || g.esize != cn.elem || g.lb < 1) return false;
+        if (g.pos_beta[g.lb - 1] < s.nk) return false;
+    }
+    return true;
+}
+
+// Whether variant var of step si reads its gathered operands in place (no gather launch).
+bool reads_in_place(const CNet &cn, size_t si, int var) {
+    if (var == kVarRow || var == kVarRowStage) return row_fuses(cn, si);
+    if (var == kVarSkinny) return skinny_fuses(cn, si);
+    return false;
+}
+
 template <int BN, int ST>
 int launch_tc(CNet &cn, const Step &s, size_t si, const tnk::GemmParams &p, cudaStream_t st) {
     const CallPlan &cp = cn.cp;
@@ -689,6 +724,7 @@ int launch_tc(CNet &cn, const Step &s, size_t si, const tnk::GemmParams &p, cuda
     tp.in_fp16 = cn.fmt[s.a] == tnk::OUT_SPLIT_FP16;
     tp.out_scale = p.out_scale;
     tp.err = cn.d_err;
+    tp.stall_cycles = cn.tc_stall;
     tp.c_plane = p.c_vstride;
     for (int i = 0; i < s.nbat; i++) tp.pos_bat[i] = s.pos_bat[i];
     for (int i = 0; i < s.nm; i++) tp.pos_m[i] = s.pos_m[i];
@@ -827,6 +863,40 @@ int launch_variant(CNet &cn, const Step &s, cudaStream_t st, int var) {
                 case 4: RC(go(tnk::cgemm_rowstage<16>)); break;
                 default: RC(go(tnk::cgemm_rowstage<32>)); break;
             }
+        }
+    } else if (var == kVarSkinny) {
+        if (!skinny_fits(cn, s)) { tn_set_error("long-K kernel: unsupported step shape"); return TN_EINVAL; }
+        if constexpr (sizeof(T) == sizeof(float2)) {
+            const size_t si2 = &s - cn.steps.data();
+            if (cn.cur_closed && skinny_fuses(cn, si2)) {
+                const auto *gd = static_cast<const tnk::GatherDesc *>(cn.gdescs.p) + cn.cp.gd_off[si2];
+                p.gA = s.gat[0] ? gd : nullptr;
+                p.gB = s.gat[1] ? gd + (s.gat[0] ? 1 : 0) : nullptr;
+                p.closed_bits = cn.cur_closed;
+            }
+            // W warps per batch, MW rows of A each (W MW = M)
+            const long long batches = p.nver << s.nbat;
+            const unsigned blocks = (unsigned)std::min<long long>(batches, 8LL * num_sms());
+            auto go = [&](auto kern, int warps) { kern<<<blocks, 32 * warps, 0, st>>>(p); };
+            auto by_n = [&](auto m_tag) {
+                constexpr int M = decltype(m_tag)::value;
+                constexpr int W = M >= 2 ? M / 2 : 1, MW = M / W;
+                switch (s.nn) {
+                    case 0: go(tnk::cgemm_skinny<W, MW, 1>, W); break;
+                    case 1: go(tnk::cgemm_skinny<W, MW, 2>, W); break;
+                    case 2: go(tnk::cgemm_skinny<W, MW, 4>, W); break;
+                    default: go(tnk::cgemm_skinny<W, MW, 8>, W); break;
+                }
+            };
+            switch (s.nm) {
+                case 0: by_n(std::integral_constant<int, 1>{}); break;
+                case 1: by_n(std::integral_constant<int, 2>{}); break;
+                case 2: by_n(std::integral_constant<int, 4>{}); break;
+                default: by_n(std::integral_constant<int, 8>{}); break;
+            }
+        } else {
+            tn_set_error("long-K kernel on a complex128 network");
+            return TN_EINVAL;
         }
     } else if (var == kVarRow) {
         row_roles(cn, s, p);
@@ -1003,7 +1073,7 @@ int execute(CNet &cn, const uint64_t *d_closed, bool skip_beta_free, double2 *ou
         }
         cn.cur_closed = d_closed;
         const int var = si < cn.variant.size() && cn.variant[si] >= 0 ? cn.variant[si] : default_variant(cn, si);
-        const bool in_place = (var == kVarRow || var == kVarRowStage) && d_closed && row_fuses(cn, si);
+        const bool in_place = d_closed && reads_in_place(cn, si, var);
         if (!in_place) RC(launch_gathers(cn, si, d_closed, st));
         if (cn.elem == 8) RC(launch_step<float2>(cn, s, st));
         else RC(launch_step<double2>(cn, s, st));
@@ -1242,6 +1312,71 @@ int build_cnet(const Merged &mg, CNet &cn, const tn_plan_opts &o, const int32_t 
     cn.compiled = true;
     assign_formats(cn);
     return setup_leaves(mem, cn);
+}
+
+}  // namespace
+
+// ---------------------------------------------------------------- sampling jobs
+
+namespace {
+
+// Device bytes of one execution on slice set sl (arena, leaves, per-group buffers, slack)
+// and its algorithmic FLOPs for the first and each later batch group; host only.
+int estimate_call(tn_plan_s *p, const std::vector<uint64_t> &sl, int64_t *bytes, double *flops_first,
+                  double *flops_next) {
+    const uint64_t E = explicit_legs(sl, (int)p->I.size());
+    Tree t = p->amp.tree;
+    std::vector<Step> steps;
+    RC(tn_compile(p->amp.net, t, E, steps, p->amp.prec != TN_PREC_C64));
+    CallLayout lay;
+    layout_call(t, steps, E, 8, sl, lay);
+    const long long T = 1LL << p->log2T;
+    if (bytes) *bytes = (int64_t)(lay.arena_bytes + 2 * p->amp.leaf_bytes + T * (64 * 16 + 64)) + (64ll << 20);
+    if (flops_first) *flops_first = lay.flops;
+    if (flops_next) *flops_next = lay.flops_beta;
+    return TN_OK;
+}
+
+// Batches a job draws for N samples at acceptance about 1/alpha: 10% above the mean
+// need, plus 8 standard deviations and 64, rounded up to whole groups of T.
+int64_t job_groups_for(int64_t N, double alpha, long long T) {
+    const double need = 1.1 * alpha * (double)N + 8.0 * std::sqrt(alpha * (double)N) + 64.0;
+    return std::max<int64_t>(1, (int64_t)std::ceil(need / (double)T));
+}
+
+}  // namespace
+
+struct tn_job_s {
+    tn_plan_s *p = nullptr;
+    std::vector<uint64_t> slices;
+    double F = 1.0, alpha = 2.0;
+    int64_t N = 0, chunk = 1, n_chunks = 0, groups = 0;
+    uint64_t seed = 0;
+    std::vector<char> done;
+    int64_t chunks_done = 0;
+    double flops_done = 0, flops_chunk = 0;
+    DBuf d_jall, d_acc;              // batch patterns and summed amplitudes of every batch
+    DBuf d_accept, d_bits, d_eps, d_pick;
+};
+
+namespace {
+
+void job_fill_info(const tn_job_s *j, tn_job_info *info) {
+    if (!info) return;
+    info->n_slices = (int64_t)j->slices.size();
+    info->F = j->F;
+    info->chunk_slices = j->chunk;
+    info->n_chunks = j->n_chunks;
+    info->groups = j->groups;
+    info->T = 1LL << j->p->log2T;
+    info->chunks_done = j->chunks_done;
+    info->flops_done = j->flops_done;
+    info->flops_chunk = j->flops_chunk;
+}
+
+void job_release(tn_job_s *j) {
+    DevMem &m = j->p->mem;
+    for (DBuf *b : {&j->d_jall, &j->d_acc, &j->d_accept, &j->d_bits, &j->d_eps, &j->d_pick}) release(m, *b);
 }
 
 }  // namespace
@@ -1883,7 +2018,7 @@ int tn_trace_read(tn_plan_h p, tn_step_trace *out, int32_t cap, int32_t *n_out) 
         t.kernel = cn.tr_kernel[si];
         // a gather launch precedes the step unless the row kernels read the operands in place
         const bool has = cn.cp.valid && cn.cp.gd_off[si + 1] > cn.cp.gd_off[si];
-        const bool in_place = (t.kernel == kVarRow || t.kernel == kVarRowStage) && row_fuses(cn, (size_t)si);
+        const bool in_place = reads_in_place(cn, (size_t)si, t.kernel);
         t.gathers = has && !in_place ? 1 : 0;
     }
     return TN_OK;
@@ -1961,6 +2096,26 @@ int tn_sample(tn_plan_h p, double f_target, int64_t N, uint64_t seed, double alp
     st_local.n_slices = nsl;
     cudaStream_t st = p->mem.stream;
     if (!(p->amp.cp.valid && p->amp.cp.slices == sl)) {
+        // a slice set beyond one execution's memory runs as a chunked sampling job
+        int64_t need = 0;
+        RC(estimate_call(p, sl, &need, nullptr, nullptr));
+        if ((double)need > p->budget) {
+            tn_job_h job = nullptr;
+            RC(tn_job_create(p, f_target, N, seed, alpha, 0, &job, nullptr));
+            std::vector<uint64_t> res((size_t)N);
+            int rc = tn_job_run(job, 0, job->n_chunks);
+            if (rc == TN_OK) rc = tn_job_finish(job, res.data(), 0, &st_local);
+            tn_job_destroy(job);
+            RC(rc);
+            if (flags & TN_DEVICE_BUFFERS) {
+                CK(cudaMemcpyAsync(bitstrings, res.data(), (size_t)N * sizeof(uint64_t), cudaMemcpyHostToDevice, st));
+                CK(cudaStreamSynchronize(st));
+            } else {
+                std::copy(res.begin(), res.end(), bitstrings);
+            }
+            if (stats) *stats = st_local;
+            return TN_OK;
+        }
         RC(ensure_variant(p->mem, p->amp, explicit_legs(sl, (int)p->I.size())));
         RC(prepare_call(p->mem, p->amp, sl, p->budget));
     }
@@ -2037,6 +2192,201 @@ int tn_sample(tn_plan_h p, double f_target, int64_t N, uint64_t seed, double alp
         return TN_EINVAL;
     }
     return TN_OK;
+}
+
+int tn_plan_test_stall(tn_plan_h p, int64_t cycles) {
+    if (!p || cycles < 0 || cycles > 4000000000LL) { tn_set_error("tn_plan_test_stall: bad arguments"); return TN_EINVAL; }
+    p->amp.tc_stall = cycles;
+    drop_graphs(p->amp);  // the captured launches hold the previous setting
+    return TN_OK;
+}
+
+int tn_job_create(tn_plan_h p, double f_target, int64_t N, uint64_t seed, double alpha, int64_t max_chunk_slices,
+                  tn_job_h *out, tn_job_info *info) {
+    if (!p || !out || N < 1 || !(alpha > 1.0) || !(f_target > 0.0) || max_chunk_slices < 0) {
+        tn_set_error("tn_job_create: bad arguments (N >= 1, alpha > 1, f_target > 0)");
+        return TN_EINVAL;
+    }
+    if (p->open.size() != 6) { tn_set_error("tn_job_create: needs 6 open qubits (batches of 64)"); return TN_EUNSUPPORTED; }
+    *out = nullptr;
+    std::unique_ptr<tn_job_s> j(new tn_job_s());
+    j->p = p;
+    j->N = N;
+    j->seed = seed;
+    j->alpha = alpha;
+    int64_t nsl = 0;
+    RC(tn_select(p, f_target, nullptr, 0, &nsl, &j->F));
+    j->slices.resize((size_t)nsl);
+    RC(tn_select(p, f_target, j->slices.data(), nsl, &nsl, &j->F));
+    const long long T = 1LL << p->log2T;
+    j->groups = job_groups_for(N, alpha, T);
+    const double job_bytes = (double)j->groups * (double)T * (64.0 * 16.0 + 8.0 + 1.0 + 8.0 + 8.0 + 4.0);
+    // chunks: aligned runs of a power of two of consecutive slices of the selection
+    // (the lowest free legs vary inside a chunk, so every chunk compiles alike)
+    int64_t c = 1;
+    while (c * 2 <= nsl && nsl % (c * 2) == 0 && (max_chunk_slices == 0 || c * 2 <= max_chunk_slices)) {
+        if (max_chunk_slices == 0) {
+            int64_t b = 0;
+            std::vector<uint64_t> sl(j->slices.begin(), j->slices.begin() + c * 2);
+            RC(estimate_call(p, sl, &b, nullptr, nullptr));
+            if ((double)b + job_bytes > 0.95 * p->budget) break;
+        }
+        c *= 2;
+    }
+    {
+        int64_t b = 0;
+        std::vector<uint64_t> sl(j->slices.begin(), j->slices.begin() + c);
+        RC(estimate_call(p, sl, &b, nullptr, nullptr));
+        if ((double)b + job_bytes > p->budget && max_chunk_slices == 0) {
+            tn_set_error("tn_job_create: one slice and the job's buffers exceed the HBM budget");
+            return TN_ENOMEM;
+        }
+        double f1 = 0, f2 = 0;
+        RC(estimate_call(p, sl, nullptr, &f1, &f2));
+        j->flops_chunk = f1 + (double)(j->groups - 1) * f2;
+    }
+    j->chunk = c;
+    j->n_chunks = nsl / c;
+    j->done.assign((size_t)j->n_chunks, 0);
+    DevMem &m = p->mem;
+    const long long nb = j->groups * T;
+    cudaStream_t st = m.stream;
+    int rc = TN_OK;
+    auto fail = [&](int r) { job_release(j.get()); return r; };
+    if ((rc = ensure(m, j->d_jall, nb * sizeof(uint64_t))) || (rc = ensure(m, j->d_acc, nb * 64 * sizeof(double2))) ||
+        (rc = ensure(m, j->d_accept, nb)) || (rc = ensure(m, j->d_bits, nb * sizeof(uint64_t))) ||
+        (rc = ensure(m, j->d_eps, nb * sizeof(double))) || (rc = ensure(m, j->d_pick, nb * sizeof(int32_t))))
+        return fail(rc);
+    if (cudaMemsetAsync(j->d_acc.p, 0, nb * 64 * sizeof(double2), st) != cudaSuccess) {
+        tn_set_error("tn_job_create: clearing the amplitude sums failed");
+        return fail(TN_EDEVICE);
+    }
+    tnk::draw_batches<<<(unsigned)((nb + 255) / 256), 256, 0, st>>>(seed, 0, nb, (int)p->closed.size(),
+                                                                    static_cast<uint64_t *>(j->d_jall.p));
+    if (cudaGetLastError() != cudaSuccess || cudaStreamSynchronize(st) != cudaSuccess) {
+        tn_set_error("tn_job_create: batch draws failed");
+        return fail(TN_EDEVICE);
+    }
+    job_fill_info(j.get(), info);
+    *out = j.release();
+    return TN_OK;
+}
+
+int tn_job_run(tn_job_h j, int64_t first, int64_t count) {
+    if (!j || first < 0 || count < 0 || first + count > j->n_chunks) { tn_set_error("tn_job_run: bad chunk range"); return TN_EINVAL; }
+    for (int64_t c = first; c < first + count; c++)
+        if (j->done[(size_t)c]) { tn_set_error("tn_job_run: chunk " + std::to_string(c) + " already ran"); return TN_EINVAL; }
+    tn_plan_s *p = j->p;
+    cudaStream_t st = p->mem.stream;
+    const long long T = 1LL << p->log2T;
+    RC(ensure(p->mem, p->d_j, T * sizeof(uint64_t)));
+    RC(ensure(p->mem, p->d_amps, T * 64 * sizeof(double2)));
+    const uint64_t *jall = static_cast<const uint64_t *>(j->d_jall.p);
+    double2 *acc = static_cast<double2 *>(j->d_acc.p);
+    const unsigned agrid = (unsigned)std::min<long long>((T * 64 + 255) / 256, 8LL * num_sms());
+    for (int64_t c = first; c < first + count; c++) {
+        std::vector<uint64_t> sl(j->slices.begin() + c * j->chunk, j->slices.begin() + (c + 1) * j->chunk);
+        RC(ensure_variant(p->mem, p->amp, explicit_legs(sl, (int)p->I.size())));
+        RC(prepare_call(p->mem, p->amp, sl, p->budget));
+        for (int64_t g = 0; g < j->groups; g++) {
+            // the group's patterns go to the buffer the captured graphs read
+            CK(cudaMemcpyAsync(p->d_j.p, jall + g * T, T * sizeof(uint64_t), cudaMemcpyDeviceToDevice, st));
+            RC(execute_graphed(p->mem, p->amp, static_cast<const uint64_t *>(p->d_j.p), g > 0,
+                               static_cast<double2 *>(p->d_amps.p), st, p->budget));
+            tnk::accumulate_amps<<<agrid, 256, 0, st>>>(acc + g * T * 64, static_cast<const double2 *>(p->d_amps.p),
+                                                        T * 64);
+            CK(cudaGetLastError());
+        }
+        j->flops_done += p->amp.cp.flops_all + (double)(j->groups - 1) * p->amp.cp.flops_beta;
+        j->done[(size_t)c] = 1;
+        j->chunks_done++;
+    }
+    CK(cudaStreamSynchronize(st));
+    return check_err(p->amp, st);
+}
+
+int tn_job_get_info(tn_job_h j, tn_job_info *info) {
+    if (!j || !info) { tn_set_error("tn_job_get_info: bad arguments"); return TN_EINVAL; }
+    job_fill_info(j, info);
+    return TN_OK;
+}
+
+int tn_job_amplitudes(tn_job_h j, int64_t g, double *amps) {
+    if (!j || !amps || g < 0 || g >= j->groups) { tn_set_error("tn_job_amplitudes: bad arguments"); return TN_EINVAL; }
+    const long long T = 1LL << j->p->log2T;
+    cudaStream_t st = j->p->mem.stream;
+    CK(cudaMemcpyAsync(amps, static_cast<const double2 *>(j->d_acc.p) + g * T * 64, T * 64 * sizeof(double2),
+                       cudaMemcpyDeviceToHost, st));
+    CK(cudaStreamSynchronize(st));
+    return TN_OK;
+}
+
+int tn_job_finish(tn_job_h j, uint64_t *bitstrings, int32_t flags, tn_sample_stats *stats) {
+    if (!j || !bitstrings) { tn_set_error("tn_job_finish: bad arguments"); return TN_EINVAL; }
+    if (j->chunks_done < j->n_chunks && !(flags & TN_JOB_PARTIAL)) {
+        tn_set_error("tn_job_finish: " + std::to_string(j->n_chunks - j->chunks_done) + " chunks have not run");
+        return TN_EINVAL;
+    }
+    tn_plan_s *p = j->p;
+    cudaStream_t st = p->mem.stream;
+    const long long T = 1LL << p->log2T, nb = j->groups * T;
+    const int b_bits = (int)p->closed.size();
+    tnk::SampleParams sp;
+    std::memset(&sp, 0, sizeof(sp));
+    sp.amps = static_cast<const double2 *>(j->d_acc.p);
+    sp.invF_num = j->F;
+    sp.T = nb;
+    sp.b_bits = b_bits;
+    sp.alpha = j->alpha;
+    sp.seed = j->seed;
+    sp.t0 = 0;
+    sp.accept = static_cast<uint8_t *>(j->d_accept.p);
+    sp.pick = static_cast<int32_t *>(j->d_pick.p);
+    sp.eps = static_cast<double *>(j->d_eps.p);
+    sp.j = static_cast<const uint64_t *>(j->d_jall.p);
+    sp.bits = static_cast<uint64_t *>(j->d_bits.p);
+    sp.n_open = 6;
+    sp.n_closed = b_bits;
+    for (int r = 0; r < 6; r++) sp.open_q[r] = (int8_t)p->open[r];
+    for (int c = 0; c < b_bits; c++) sp.closed_q[c] = (int8_t)p->closed[c];
+    tnk::sampler<<<(unsigned)((nb * 32 + 255) / 256), 256, 0, st>>>(sp);
+    CK(cudaGetLastError());
+    std::vector<uint8_t> h_acc((size_t)nb);
+    std::vector<uint64_t> h_bits((size_t)nb);
+    std::vector<double> h_eps((size_t)nb);
+    CK(cudaMemcpyAsync(h_acc.data(), j->d_accept.p, nb, cudaMemcpyDeviceToHost, st));
+    CK(cudaMemcpyAsync(h_bits.data(), j->d_bits.p, nb * sizeof(uint64_t), cudaMemcpyDeviceToHost, st));
+    CK(cudaMemcpyAsync(h_eps.data(), j->d_eps.p, nb * sizeof(double), cudaMemcpyDeviceToHost, st));
+    CK(cudaStreamSynchronize(st));
+    tn_sample_stats sst;
+    std::memset(&sst, 0, sizeof(sst));
+    int64_t got = 0;
+    double eps_sum = 0;
+    for (long long t = 0; t < nb; t++) {
+        eps_sum += h_eps[(size_t)t];
+        if (h_acc[(size_t)t]) {
+            sst.accepted++;
+            if (got < j->N) bitstrings[got++] = h_bits[(size_t)t];
+        }
+    }
+    sst.F = j->F;
+    sst.steps = nb;
+    sst.eps_hat = eps_sum / (double)nb;
+    sst.n_slices = (int64_t)j->slices.size();
+    sst.flops = j->flops_done;
+    if (stats) *stats = sst;
+    if (got < j->N && !(flags & TN_JOB_PARTIAL)) {
+        tn_set_error("tn_job_finish: " + std::to_string(got) + " of " + std::to_string(j->N) +
+                     " samples accepted in the job's batches");
+        return TN_EINVAL;
+    }
+    return TN_OK;
+}
+
+void tn_job_destroy(tn_job_h j) {
+    if (!j) return;
+    job_release(j);
+    delete j;
 }
 
 }  // extern "C"

@@ -321,6 +321,102 @@ __global__ void __launch_bounds__(32 * kRowWarps) cgemm_rowstage(GemmParams p) {
     }
 }
 
+// Batched products with at most 8 rows and 8 columns and a long K (K >= 1024, complex64
+// operands).  A block of W warps takes one (version, batch) at a time; warp w owns rows
+// MW w .. MW w + MW - 1 of A and every column.  Per 64-element K block (kSkinnyU blocks
+// per stage), lane l reads
+// elements 2 l and 2 l + 1 of its A rows (16-byte loads, 512 contiguous bytes per row and
+// warp, evict-first) and of the B rows its warp stages, and the block shares the staged B
+// block through double-buffered shared memory (one barrier per block), so each operand
+// element leaves DRAM once.  Each lane accumulates in ascending k and the warp adds its 32
+// lane sums by a fixed xor butterfly.  Gathered operands are read in place, one decode per
+// row and warp.  The lane split of K rounds differently from the kernels that accumulate
+// each output over k in one thread, so it is the only kernel the engine runs for these
+// shapes.
+constexpr int kSkinnyU = 2;  // 64-element K blocks per stage (loads in flight per lane)
+template <int W, int MW, int N>
+__global__ void __launch_bounds__(32 * W) cgemm_skinny(GemmParams p) {
+    __shared__ float4 sB[2][kSkinnyU][N][32];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const long long batches = p.nver << p.lbat;
+    const int K = 1 << p.lk;
+    for (long long bv = blockIdx.x; bv < batches; bv += gridDim.x) {
+        const long long bat = bv & ((1LL << p.lbat) - 1), v = bv >> p.lbat;
+        const float2 *a[MW], *b[(N + W - 1) / W];
+#pragma unroll
+        for (int i = 0; i < MW; i++) {
+            const long long e = ((bat << p.lm) | (long long)(warp * MW + i)) << p.lk;
+            a[i] = p.gA ? reinterpret_cast<const float2 *>(p.gA->src) +
+                              gather_src_warp(*p.gA, e, p.gA->pos_beta[p.gA->lb - 1], p.closed_bits)
+                        : static_cast<const float2 *>(p.ptrA[v]) + e;
+        }
+        // B rows staged by this warp: n = warp, warp + W, ...
+#pragma unroll
+        for (int r = 0; r < (N + W - 1) / W; r++) {
+            const int n = warp + r * W;
+            const long long e = (bat << (p.ln + p.lk)) | ((long long)(n < N ? n : 0) << p.lk);
+            b[r] = p.gB ? reinterpret_cast<const float2 *>(p.gB->src) +
+                              gather_src_warp(*p.gB, e, p.gB->pos_beta[p.gB->lb - 1], p.closed_bits)
+                        : static_cast<const float2 *>(p.ptrB[v]) + e;
+        }
+        float2 acc[MW][N];
+#pragma unroll
+        for (int i = 0; i < MW; i++)
+#pragma unroll
+            for (int n = 0; n < N; n++) acc[i][n] = make_float2(0.f, 0.f);
+        int buf = 0;
+        for (int k0 = 2 * lane; k0 < K; k0 += 64 * kSkinnyU, buf ^= 1) {
+            float4 x[kSkinnyU][MW], y[kSkinnyU][(N + W - 1) / W];
+#pragma unroll
+            for (int u = 0; u < kSkinnyU; u++) {
+#pragma unroll
+                for (int i = 0; i < MW; i++) x[u][i] = __ldcs(reinterpret_cast<const float4 *>(a[i] + k0 + 64 * u));
+#pragma unroll
+                for (int r = 0; r < (N + W - 1) / W; r++)
+                    if (warp + r * W < N) y[u][r] = __ldcs(reinterpret_cast<const float4 *>(b[r] + k0 + 64 * u));
+            }
+#pragma unroll
+            for (int u = 0; u < kSkinnyU; u++)
+#pragma unroll
+                for (int r = 0; r < (N + W - 1) / W; r++)
+                    if (warp + r * W < N) sB[buf][u][warp + r * W][lane] = y[u][r];
+            // with two buffers one barrier per stage suffices: a warp writes a buffer again
+            // only after every warp has passed the barrier that follows its last reads of it
+            __syncthreads();
+#pragma unroll
+            for (int u = 0; u < kSkinnyU; u++)
+#pragma unroll
+                for (int n = 0; n < N; n++) {
+                    const float4 yb = sB[buf][u][n][lane];
+#pragma unroll
+                    for (int i = 0; i < MW; i++) {
+                        acc[i][n] = cfma(make_float2(x[u][i].x, x[u][i].y), make_float2(yb.x, yb.y), acc[i][n]);
+                        acc[i][n] = cfma(make_float2(x[u][i].z, x[u][i].w), make_float2(yb.z, yb.w), acc[i][n]);
+                    }
+                }
+        }
+#pragma unroll
+        for (int off = 16; off > 0; off >>= 1)
+#pragma unroll
+            for (int i = 0; i < MW; i++)
+#pragma unroll
+                for (int n = 0; n < N; n++) {
+                    acc[i][n].x += __shfl_xor_sync(0xffffffffu, acc[i][n].x, off);
+                    acc[i][n].y += __shfl_xor_sync(0xffffffffu, acc[i][n].y, off);
+                }
+        // every lane holds the totals: lane i N + n stores output (row MW warp + i, column n)
+        const long long cb = scatter_bits(bat, p.pos_bat, p.lbat);
+#pragma unroll
+        for (int i = 0; i < MW; i++)
+#pragma unroll
+            for (int n = 0; n < N; n++)
+                if (lane == i * N + n)
+                    store_c(p, v, cb + scatter_bits(warp * MW + i, p.pos_m, p.lm) + scatter_bits(n, p.pos_n, p.ln),
+                            acc[i][n]);
+        __syncthreads();  // the staging buffers are reused by the block's next batch
+    }
+}
+
 // Batched small products (M, N <= 64, K <= 64): a block stages the operands of 2^lg
 // consecutive batches in shared memory and walks that chunk's outputs in the order of
 // their positions in C (local bit i = chunk bit kind[i] / idx[i]), so consecutive threads
@@ -679,6 +775,18 @@ __global__ void __launch_bounds__(256) root_slice_sum(GemmParams p, int nfree, i
         }
     }
     out[e] = make_double2(re, im);
+}
+
+// ---------------------------------------------------------------- sampling job
+
+// acc[e] += x[e] in FP64 for e < n: a sampling job adds each slice chunk's sum over its
+// slices (Sec. I.C step 1) to the running total of the same batches, chunk after chunk,
+// so every amplitude is summed in one fixed order.
+__global__ void accumulate_amps(double2 *acc, const double2 *x, long long n) {
+    for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < n; e += (long long)gridDim.x * blockDim.x) {
+        const double2 a = acc[e], b = x[e];
+        acc[e] = make_double2(__dadd_rn(a.x, b.x), __dadd_rn(a.y, b.y));
+    }
 }
 
 // ---------------------------------------------------------------- verification XEB

@@ -41,6 +41,8 @@ struct TcParams {
     float out_scale;         // multiply results by this before storing
     int *err;                // set to 1 if a bounded wait gives up
     int group_m;             // m tiles per raster group (>= 1): see tc_tile
+    long long stall_cycles;  // > 0 (tests only): the MMA warp first waits this long on a
+                             // barrier nothing arrives on, so the bounded-wait path runs
     int8_t pos_bat[kMaxBits], pos_m[kMaxBits], pos_n[kMaxBits];
 };
 
@@ -198,7 +200,8 @@ __global__ void __launch_bounds__(kTcThreads, 1)
     uint64_t *empty = full + STAGES;
     uint64_t *acc_full = empty + STAGES;  // [2]: MMA -> epilogue
     uint64_t *acc_empty = acc_full + 2;   // [2]: epilogue -> MMA
-    uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(acc_empty + 2);
+    uint64_t *never = acc_empty + 2;      // test stall: initialised, never arrived on
+    uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(never + 1);
     volatile int *abort_flag = reinterpret_cast<volatile int *>(tmem_slot + 1);
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -228,6 +231,7 @@ __global__ void __launch_bounds__(kTcThreads, 1)
             mbar_init(smem_u32(&acc_full[b]), 1);
             mbar_init(smem_u32(&acc_empty[b]), 4);  // one arrive per epilogue warp
         }
+        mbar_init(smem_u32(never), 1);
         *abort_flag = 0;
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
@@ -286,6 +290,8 @@ __global__ void __launch_bounds__(kTcThreads, 1)
             int it = 0, last_b = -1;
             uint32_t last_par = 0;
             bool ok = true;
+            // test hook: a wait that runs out before any MMA is issued
+            if (p.stall_cycles > 0) ok = mbar_wait(smem_u32(never), 0u, abort_flag, p.stall_cycles);
             for (long long t = blockIdx.x; t < ntiles && ok; t += gridDim.x, it++) {
                 const int b = it & 1;
                 if (it >= 2 &&

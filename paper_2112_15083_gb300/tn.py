@@ -26,6 +26,7 @@ EXPORTED = [
     "tn_plan_host", "tn_sliced_vertex_select", "tn_sample_step", "tn_trace_enable", "tn_trace_read",
     "tn_slice_cut_noalloc", "tn_plan_estimate", "tn_plan_sync", "tn_server_opts_default", "tn_server_create",
     "tn_server_submit", "tn_server_query", "tn_server_wait", "tn_server_get_stats", "tn_server_destroy",
+    "tn_plan_test_stall", "tn_job_create", "tn_job_run", "tn_job_get_info", "tn_job_amplitudes", "tn_job_finish", "tn_job_destroy",
 ]
 
 REQ_STATUS = {0: "queued", 1: "planning", 2: "planned", 3: "active", 4: "done", 5: "failed", 6: "rejected"}
@@ -111,6 +112,14 @@ class StepTrace(ctypes.Structure):
     ]
 
 
+class JobInfo(ctypes.Structure):
+    _fields_ = [
+        ("n_slices", ctypes.c_int64), ("F", ctypes.c_double), ("chunk_slices", ctypes.c_int64),
+        ("n_chunks", ctypes.c_int64), ("groups", ctypes.c_int64), ("T", ctypes.c_int64),
+        ("chunks_done", ctypes.c_int64), ("flops_done", ctypes.c_double), ("flops_chunk", ctypes.c_double),
+    ]
+
+
 class SampleStats(ctypes.Structure):
     _fields_ = [
         ("F", ctypes.c_double), ("eps_hat", ctypes.c_double), ("steps", ctypes.c_int64),
@@ -167,13 +176,22 @@ def lib():
         L.tn_server_destroy.argtypes = [vp]
         L.tn_server_destroy.restype = None
         L.tn_slice_cut_noalloc.argtypes = [vp, i32, dbl, vp, vp, ctypes.POINTER(i32), ctypes.POINTER(dbl)]
+        L.tn_plan_test_stall.argtypes = [vp, i64]
+        L.tn_job_create.argtypes = [vp, dbl, i64, u64, dbl, i64, ctypes.POINTER(vp), ctypes.POINTER(JobInfo)]
+        L.tn_job_run.argtypes = [vp, i64, i64]
+        L.tn_job_get_info.argtypes = [vp, ctypes.POINTER(JobInfo)]
+        L.tn_job_amplitudes.argtypes = [vp, i64, vp]
+        L.tn_job_finish.argtypes = [vp, vp, i32, ctypes.POINTER(SampleStats)]
+        L.tn_job_destroy.argtypes = [vp]
+        L.tn_job_destroy.restype = None
         L.tn_strerror.argtypes = [ctypes.c_int]
         L.tn_strerror.restype = ctypes.c_char_p
         L.tn_last_error.argtypes = []
         L.tn_last_error.restype = ctypes.c_char_p
         for name in EXPORTED:
             if name not in ("tn_plan_opts_default", "tn_circuit_destroy", "tn_plan_destroy",
-                            "tn_strerror", "tn_last_error", "tn_server_opts_default", "tn_server_destroy"):
+                            "tn_strerror", "tn_last_error", "tn_server_opts_default", "tn_server_destroy",
+                            "tn_job_destroy"):
                 getattr(L, name).restype = ctypes.c_int
         _lib = L
     return _lib
@@ -420,12 +438,65 @@ class Plan:
         _check(lib().tn_trace_read(self.h, arr, n.value, ctypes.byref(n)), "tn_trace_read")
         return [{k: getattr(arr[i], k) for k, _ in StepTrace._fields_} for i in range(n.value)]
 
+    def test_stall(self, cycles: int):
+        """Tests only: make the tensor-core launches' first wait run out (tn_plan_test_stall)."""
+        _check(lib().tn_plan_test_stall(self.h, int(cycles)), "tn_plan_test_stall")
+
+    def job(self, f_target: float, N: int, seed: int, alpha: float = 2.0, max_chunk_slices: int = 0) -> "Job":
+        return Job(self, f_target, N, seed, alpha, max_chunk_slices)
+
     def sample(self, f_target: float, N: int, seed: int, alpha: float = 2.0):
         out = np.zeros(max(1, N), dtype=np.uint64)
         st = SampleStats()
         rc = lib().tn_sample(self.h, f_target, N, seed, alpha, _np_ptr(out), 0, ctypes.byref(st))
         _check(rc, "tn_sample")
         return out[:N], {k: getattr(st, k) for k, _ in SampleStats._fields_}
+
+
+JOB_PARTIAL = 2
+
+
+class Job:
+    """A chunked sampling job (tn_job_*): the retained slices in chunks, every chunk
+    contracted for all of the job's batch groups and summed in FP64, then one accept /
+    pick pass over all batches."""
+
+    def __init__(self, plan: "Plan", f_target: float, N: int, seed: int, alpha: float = 2.0,
+                 max_chunk_slices: int = 0):
+        self.h = ctypes.c_void_p()
+        self._plan = plan
+        self.N = int(N)
+        inf = JobInfo()
+        _check(lib().tn_job_create(plan.h, f_target, int(N), int(seed), alpha, int(max_chunk_slices),
+                                   ctypes.byref(self.h), ctypes.byref(inf)), "tn_job_create")
+
+    def __del__(self):
+        if getattr(self, "h", None) and self.h.value and _lib is not None:
+            _lib.tn_job_destroy(self.h)
+            self.h = None
+
+    def info(self) -> dict:
+        inf = JobInfo()
+        _check(lib().tn_job_get_info(self.h, ctypes.byref(inf)), "tn_job_get_info")
+        return {k: getattr(inf, k) for k, _ in JobInfo._fields_}
+
+    def run(self, first: int = 0, count: int | None = None):
+        if count is None:
+            count = self.info()["n_chunks"] - first
+        _check(lib().tn_job_run(self.h, int(first), int(count)), "tn_job_run")
+
+    def amplitudes(self, g: int) -> np.ndarray:
+        T = self.info()["T"]
+        out = np.zeros((T, 64), dtype=np.complex128)
+        _check(lib().tn_job_amplitudes(self.h, int(g), _np_ptr(out)), "tn_job_amplitudes")
+        return out
+
+    def finish(self, partial: bool = False):
+        out = np.zeros(self.N, dtype=np.uint64)
+        st = SampleStats()
+        _check(lib().tn_job_finish(self.h, _np_ptr(out), JOB_PARTIAL if partial else 0, ctypes.byref(st)),
+               "tn_job_finish")
+        return out, {k: getattr(st, k) for k, _ in SampleStats._fields_}
 
 
 def plan_host(circuit: Circuit, open_qubits, sliced=None, order=None, log2_batches=8, order_seed=0,

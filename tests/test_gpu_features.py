@@ -211,3 +211,56 @@ def test_fused_root_sum_same_samples():
     res = [pl.sample(0.25, 3000, seed=9) for pl in (a, b)]
     assert np.array_equal(res[0][0], res[1][0])
     assert res[0][1]["eps_hat"] == res[1][1]["eps_hat"]
+
+
+# ------------------------------------------------------------------ long-K products
+
+@pytest.mark.parametrize("n_open,lb,prec", [(4, 4, "c64"), (2, 4, "c64"), (2, 8, "bf16x2"), (2, 0, "c64")])
+def test_long_k_kernel_against_state_vector(n_open, lb, prec):
+    """Plans of a 4x5 / 12-cycle circuit whose root joins two halves over K = 2^10 .. 2^12
+    with at most 8 x 8 outputs per batch: that step runs the long-K kernel (lane split of
+    K, butterfly), checked with every amplitude against the state vector."""
+    P = pkg()
+    circ = cg.sycamore_grid(4, 5, 12, seed=1)
+    openq = list(range(n_open))
+    C = P.circuit_load(circ.serialize())
+    precision = {"c64": P.tn.PREC_C64, "bf16x2": P.tn.PREC_BF16X2}[prec]
+    plan = P.plan(C, openq, log2_batches=lb, order_trials=16, precision=precision)
+    nb = (1 << lb) + 3  # a ragged second group
+    cb = cg.random_closed_bits(nb, 20 - n_open, seed=4)
+    plan.trace(True)
+    amps = plan.contract(np.arange(1, dtype=np.uint64), cb)
+    tr = plan.trace_read()
+    plan.trace(False)
+    assert any(s["kernel"] == 5 and s["launches"] > 0 for s in tr), "the long-K kernel did not run"
+    ref = oracle.batch_amplitudes(oracle.simulate(circ), 20, openq, cb)
+    if prec == "c64":
+        close_c64(amps, ref)
+    else:
+        assert np.linalg.norm(amps - ref) / np.linalg.norm(ref) <= 1e-3
+
+
+# ------------------------------------------------------------------ failure detection
+
+def test_bounded_wait_times_out_and_the_plan_recovers():
+    """A tensor-core wait that nothing satisfies (tn_plan_test_stall) must end in the
+    kernel's bounded-wait exit and TN_ETIMEOUT from the synchronising call, leave the
+    context usable, and a following normal call must match the oracle again."""
+    P = pkg()
+    circ = cg.sycamore_grid(4, 5, 10, seed=1)
+    openq = cg.default_open_qubits(4, 5, 6)
+    C = P.circuit_load(circ.serialize())
+    plan = P.plan(C, openq, n_auto_sliced=6, log2_batches=10, order_trials=16, precision=P.tn.PREC_BF16X2,
+                  autotune=0)
+    cb = cg.random_closed_bits(1024, 14, seed=2)
+    slices = np.arange(64, dtype=np.uint64)
+    ref = oracle.batch_amplitudes(oracle.simulate(circ), 20, openq, cb)
+    first = plan.contract(slices, cb)
+    assert np.linalg.norm(first - ref) / np.linalg.norm(ref) <= 1e-3
+    plan.test_stall(2_000_000)  # about 1 ms at 2 GHz
+    with pytest.raises(P.TnError) as e:
+        plan.contract(slices, cb)
+    assert e.value.code == P.tn.TN_ETIMEOUT
+    plan.test_stall(0)
+    again = plan.contract(slices, cb)
+    assert np.array_equal(again, first)
