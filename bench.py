@@ -321,8 +321,11 @@ def run_reference(args):
 
 # ---------------------------------------------------------------- our path
 
+TC_VARIANTS = (9128, 9064, 9032)
+
+
 def kernel_name(k):
-    if k >= 9000:
+    if k in TC_VARIANTS:
         return "tc_cgemm<%d,%d>" % (k - 9000, {9128: 3, 9064: 4, 9032: 5}.get(k, 0))
     if k in KERNEL_NAMES:
         return KERNEL_NAMES[k]
@@ -340,7 +343,7 @@ def roofline_of(trace, steps_traced, pk):
     alg = dom["flops_per_launch"] / (dom_ms / 1e3) / 1e12
     shape = "(bat,m,n,k bits = %d,%d,%d,%d)" % (dom["nbat"], dom["nm"], dom["nn"], dom["nk"])
     k = dom["kernel"]
-    if k >= 9000:
+    if k in TC_VARIANTS:
         # the split path issues 3x the algorithmic products on the tensor pipe
         peak = pk.get("bf16_tflops", 1900.0)
         roof = {"bound": "tensor", "achieved": alg, "peak": peak, "unit": "TFLOP/s", "traffic": None,
@@ -657,6 +660,12 @@ def run_job(args):
     trace = plan.trace_read()
     plan.trace(False)
     steps_tr, ssum = split_trace(trace)
+    # launch gaps: the graph-replayed chunk against the sum of its launches' device times
+    # (the traced chunk runs the same launches one by one, CUDA events around each); the
+    # difference also holds the per-group pattern copies and FP64 accumulations
+    launches_ms = sum(s["ms"] for s in steps_tr) + sum(s["ms"] for s in ssum)
+    gaps = {"chunk_ms_replayed": round(tot_ms / args.steps, 2), "launch_device_ms_sum": round(launches_ms, 2),
+            "outside_traced_launches_ms": round(tot_ms / args.steps - launches_ms, 2)}
     job_s = info["n_chunks"] * (tot_ms / args.steps) / 1e3 + finish_s
     job_s_max, n_all = replicas.reduce_run(job_s * 1e3, N, device=torch.device("cuda", local))
     value = n_all / (job_s_max / 1e3)
@@ -715,7 +724,7 @@ def run_job(args):
         "flops_per_chunk": info["flops_chunk"], "plan_seconds": plan_s, "job_create_seconds": create_s,
         "eps_hat_partial": st["eps_hat"], "plan": plan_info, "clocks": clk, "roofline": roofline,
         "cpu_baseline": cpu, "e2e": e2e, "top_steps": top_steps_of(steps_tr, 8), "slice_sum": slice_sum_of(ssum),
-        "secondary": secondary,
+        "secondary": secondary, "launch_gaps": gaps,
         # per chunk: every contraction launch, its gathers and slice sums, one amplitude
         # accumulation per group (counted from the traced chunk)
         "gpu_launches": per_chunk_launches * args.steps,

@@ -304,7 +304,9 @@ int tn_sample(tn_plan_h p, double f_target, int64_t N, uint64_t seed, double alp
 /*
  * Sampling job over a slice set larger than one execution's memory (Sec. I.C step 1 with
  * Sec. II.A).  The retained slices X x {0,1}^{|I|-k} of tn_select are split into chunks
- * of chunk_slices consecutive slices (the same low free legs vary inside every chunk);
+ * of chunk_slices slices that differ only in the same free legs (those that add the least
+ * work when they vary inside a chunk: the steps that do not depend on them run once per
+ * chunk);
  * the job's batches t = 0 .. groups * T - 1 (T = 2^log2_batches) are drawn once (Philox,
  * as in tn_sample).  tn_job_run contracts chunks for every batch group: per chunk the
  * batch-independent intermediates are computed once and reused by all groups, and each

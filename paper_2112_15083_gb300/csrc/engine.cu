@@ -624,11 +624,13 @@ bool rowstage_fits(const CNet &cn, const Step &s) {
 }
 constexpr int kTiles[7][2] = {{128, 64}, {64, 64}, {128, 32}, {64, 32}, {32, 32}, {128, 16}, {16, 16}};
 
-// Whether the long-K kernel runs step si: at most 8 rows and 8 columns, K >= 1024, complex64
-// operands.  It is then the step's only kernel (its lane split of K rounds differently).
+// Whether the long-K kernel runs step si: at most 8 outputs on the short side and 32 on
+// the long side, K >= 1024, complex64 operands.  It is then the step's only kernel (its
+// lane split of K rounds differently from the others).
 bool skinny_fits(const CNet &cn, const Step &s) {
-    return cn.elem == 8 && s.nm <= 3 && s.nn <= 3 && s.nk >= 10 && cn.fmt[s.a] == tnk::OUT_C64 &&
-           cn.fmt[s.b] == tnk::OUT_C64 && (cn.use_tc.empty() || !cn.use_tc[&s - cn.steps.data()]);
+    return cn.elem == 8 && std::min(s.nm, s.nn) <= 3 && std::max(s.nm, s.nn) <= 5 && s.nk >= 10 &&
+           cn.fmt[s.a] == tnk::OUT_C64 && cn.fmt[s.b] == tnk::OUT_C64 &&
+           (cn.use_tc.empty() || !cn.use_tc[&s - cn.steps.data()]);
 }
 
 bool small_fits(const Step &s, size_t esz) {
@@ -874,25 +876,34 @@ int launch_variant(CNet &cn, const Step &s, cudaStream_t st, int var) {
                 p.gB = s.gat[1] ? gd + (s.gat[0] ? 1 : 0) : nullptr;
                 p.closed_bits = cn.cur_closed;
             }
+            // the longer side are the kernel's rows (C = A B^T is symmetric in the roles)
+            if (p.ln > p.lm) {
+                std::swap(p.ptrA, p.ptrB);
+                std::swap(p.gA, p.gB);
+                std::swap(p.lm, p.ln);
+                for (int i = 0; i < tnk::kMaxBits; i++) std::swap(p.pos_m[i], p.pos_n[i]);
+            }
             // W warps per batch, MW rows of A each (W MW = M)
-            const long long batches = p.nver << s.nbat;
+            const long long batches = p.nver << p.lbat;
             const unsigned blocks = (unsigned)std::min<long long>(batches, 8LL * num_sms());
             auto go = [&](auto kern, int warps) { kern<<<blocks, 32 * warps, 0, st>>>(p); };
             auto by_n = [&](auto m_tag) {
                 constexpr int M = decltype(m_tag)::value;
-                constexpr int W = M >= 2 ? M / 2 : 1, MW = M / W;
-                switch (s.nn) {
+                constexpr int W = M >= 16 ? 8 : (M >= 2 ? M / 2 : 1), MW = M / W;
+                switch (p.ln) {
                     case 0: go(tnk::cgemm_skinny<W, MW, 1>, W); break;
                     case 1: go(tnk::cgemm_skinny<W, MW, 2>, W); break;
                     case 2: go(tnk::cgemm_skinny<W, MW, 4>, W); break;
                     default: go(tnk::cgemm_skinny<W, MW, 8>, W); break;
                 }
             };
-            switch (s.nm) {
+            switch (p.lm) {
                 case 0: by_n(std::integral_constant<int, 1>{}); break;
                 case 1: by_n(std::integral_constant<int, 2>{}); break;
                 case 2: by_n(std::integral_constant<int, 4>{}); break;
-                default: by_n(std::integral_constant<int, 8>{}); break;
+                case 3: by_n(std::integral_constant<int, 8>{}); break;
+                case 4: by_n(std::integral_constant<int, 16>{}); break;
+                default: by_n(std::integral_constant<int, 32>{}); break;
             }
         } else {
             tn_set_error("long-K kernel on a complex128 network");
@@ -1360,6 +1371,73 @@ struct tn_job_s {
 };
 
 namespace {
+
+// Reorder a selection X x {0,1}^free (tn_select's order: partial assignments, then the
+// free legs' values) so that the free legs that add the least work when they vary inside
+// a chunk vary fastest.  Varying leg e inside a chunk doubles every tensor below which e
+// is sliced (it becomes a layout bit), while the steps that do not depend on e run once for
+// the whole chunk; batch steps count once per batch group.  Legs are taken greedily by the
+// job's FLOPs per slice, up to 12 of them.
+int order_chunk_legs(tn_plan_s *p, double f, double groups, std::vector<uint64_t> &slices) {
+    const int nI = (int)p->I.size();
+    if (nI == 0 || nI > 40) return TN_OK;
+    uint64_t smask = 0;
+    if (f < 1.0)
+        for (int e : p->norm_S) smask |= 1ull << e;
+    std::vector<int> freeb;
+    for (int e = 0; e < nI; e++)
+        if (!((smask >> e) & 1)) freeb.push_back(e);
+    const size_t per = size_t(1) << freeb.size();
+    if (freeb.empty() || slices.size() % per) return TN_OK;
+    // per-slice FLOPs and slice dependences of every step (all sliced legs explicit)
+    Tree t = p->amp.tree;
+    std::vector<Step> steps;
+    const uint64_t all = nI >= 64 ? ~0ull : ((1ull << nI) - 1);
+    RC(tn_compile(p->amp.net, t, all, steps, p->amp.prec != TN_PREC_C64));
+    std::vector<double> w(steps.size());
+    std::vector<uint64_t> dep(steps.size());
+    for (size_t i = 0; i < steps.size(); i++) {
+        w[i] = steps[i].flops_per_version * (t.nodes[steps[i].c].beta ? groups : 1.0);
+        dep[i] = t.nodes[steps[i].c].dep;
+    }
+    auto per_slice = [&](uint64_t V) {
+        double c = 0;
+        for (size_t i = 0; i < steps.size(); i++) c += w[i] * std::ldexp(1.0, __builtin_popcountll(dep[i] & V));
+        return c / std::ldexp(1.0, __builtin_popcountll(V));
+    };
+    std::vector<int> V;
+    uint64_t vm = 0;
+    while (V.size() < std::min<size_t>(12, freeb.size())) {
+        int best = -1;
+        double bc = 0;
+        for (int e : freeb) {
+            if ((vm >> e) & 1) continue;
+            const double c = per_slice(vm | (1ull << e));
+            if (best < 0 || c < bc) { best = e; bc = c; }
+        }
+        V.push_back(best);
+        vm |= 1ull << best;
+    }
+    std::vector<int> rest;
+    for (int e : freeb)
+        if (!((vm >> e) & 1)) rest.push_back(e);
+    std::vector<uint64_t> out;
+    out.reserve(slices.size());
+    for (size_t i = 0; i < slices.size(); i += per) {
+        const uint64_t base = slices[i];  // the block's member with every free leg at 0
+        for (uint64_t r2 = 0; r2 < (1ull << rest.size()); r2++) {
+            uint64_t s2 = base;
+            for (size_t u = 0; u < rest.size(); u++) s2 |= ((r2 >> u) & 1ull) << rest[u];
+            for (uint64_t r1 = 0; r1 < (1ull << V.size()); r1++) {
+                uint64_t s1 = s2;
+                for (size_t u = 0; u < V.size(); u++) s1 |= ((r1 >> u) & 1ull) << V[u];
+                out.push_back(s1);
+            }
+        }
+    }
+    slices.swap(out);
+    return TN_OK;
+}
 
 void job_fill_info(const tn_job_s *j, tn_job_info *info) {
     if (!info) return;
@@ -2220,6 +2298,7 @@ int tn_job_create(tn_plan_h p, double f_target, int64_t N, uint64_t seed, double
     RC(tn_select(p, f_target, j->slices.data(), nsl, &nsl, &j->F));
     const long long T = 1LL << p->log2T;
     j->groups = job_groups_for(N, alpha, T);
+    RC(order_chunk_legs(p, f_target, (double)j->groups, j->slices));
     const double job_bytes = (double)j->groups * (double)T * (64.0 * 16.0 + 8.0 + 1.0 + 8.0 + 8.0 + 4.0);
     // chunks: aligned runs of a power of two of consecutive slices of the selection
     // (the lowest free legs vary inside a chunk, so every chunk compiles alike)

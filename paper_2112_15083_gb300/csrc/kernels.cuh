@@ -321,7 +321,7 @@ __global__ void __launch_bounds__(32 * kRowWarps) cgemm_rowstage(GemmParams p) {
     }
 }
 
-// Batched products with at most 8 rows and 8 columns and a long K (K >= 1024, complex64
+// Batched products with at most 32 rows and 8 columns and a long K (K >= 1024, complex64
 // operands).  A block of W warps takes one (version, batch) at a time; warp w owns rows
 // MW w .. MW w + MW - 1 of A and every column.  Per 64-element K block (kSkinnyU blocks
 // per stage), lane l reads

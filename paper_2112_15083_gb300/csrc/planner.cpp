@@ -560,9 +560,9 @@ StepEst step_estimate(const Network &net, const Node &a, const Node &b, const No
                   : lo >= 4 ? flop_rate / 4
                   : hi >= 5 ? flop_rate / 6
                             : flop_rate / 16;
-    // at most 8 x 8 outputs over K >= 1024: the long-K kernel streams the operands, so the
+    // at most 8 x 32 outputs over K >= 1024: the long-K kernel streams the operands, so the
     // bytes bound it
-    if (hi <= 3 && nk >= 10) rate = flop_rate;
+    if (lo <= 3 && hi <= 5 && nk >= 10) rate = flop_rate;
     if (net.tc_flop_rate > 0 && tn_tc_shape(hi, lo, nk)) {
         rate = net.tc_flop_rate * (lo >= 6 ? 1.0 : 0.5);
         // a batch of products of one or two output tiles each pays the tile's pipeline
