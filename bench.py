@@ -77,7 +77,7 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-secondary", action="store_true", help="skip the 28-qubit secondary lines")
     ap.add_argument("--precision", default="bf16x2", choices=["c64", "bf16x2"])
-    ap.add_argument("--chunk", type=int, default=2, help="job workloads: slices per chunk (a power of two)")
+    ap.add_argument("--chunk", type=int, default=8, help="job workloads: at most this many slices per chunk (a power of two)")
     ap.add_argument("--log2-batches", type=int, default=None, help="batches per group = 2^this (default: the workload's)")
     ap.add_argument("--autotune", type=int, default=1, help="kernel autotuning (1) or the fixed shape rules (0)")
     ap.add_argument("--anneal", type=int, default=0,

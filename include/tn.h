@@ -333,9 +333,9 @@ typedef struct {
 } tn_job_info;
 
 /*
- * Create a job for N samples at fidelity f_target.  max_chunk_slices > 0 caps the chunk
- * (rounded down to a power of two); 0 picks the largest power of two whose working set
- * (tn_plan_estimate) plus the job's buffers fits the plan's HBM budget.
+ * Create a job for N samples at fidelity f_target.  The chunk is the largest power of two
+ * of slices whose working set (tn_plan_estimate) plus the job's buffers fits 95% of the
+ * plan's HBM budget; max_chunk_slices > 0 caps it further.
  * Errors: TN_EINVAL (arguments, n_open != 6), TN_ENOMEM (not even one slice fits).
  */
 int tn_job_create(tn_plan_h p, double f_target, int64_t N, uint64_t seed, double alpha,
@@ -403,11 +403,15 @@ typedef struct {
     int32_t kernel; /* 0: row kernel, 1: staged small products, 2: FP64 slice sum,
                        3: the root step fused with the FP64 slice sum (the root step's
                        own entry then counts no launches), 4: row kernel with rows
-                       staged through shared memory, 9128 / 9064 / 9032:
+                       staged through shared memory, 5: long-K kernel (at most 8 x 32
+                       outputs per batch, K >= 1024), 9128 / 9064 / 9032:
                        tensor-core kernel with 128- / 64- / 32-column tiles,
                        TM*1000+TN: FFMA tile kernel */
-    int32_t gathers; /* batch-gather launches that precede each launch of the step (0 or
-                        1; 0 when the row kernel reads gathered operands in place) */
+    int32_t gathers;  /* batch-gather launches that precede each launch of the step (0 or
+                         1; 0 when the kernel reads its gathered operands in place) */
+    int32_t in_place; /* 1: the step has gathered operands and its kernel reads them in
+                         place (row and long-K kernels through the gather's tables,
+                         tensor-core kernels through a tensor map over the stored form) */
 } tn_step_trace;
 int tn_trace_enable(tn_plan_h p, int32_t on);
 int tn_trace_read(tn_plan_h p, tn_step_trace *out, int32_t cap, int32_t *n_out);

@@ -40,7 +40,11 @@ def build(force: bool = False, verbose: bool = False) -> str:
             return LIB
     os.makedirs(OUT, exist_ok=True)
     nvcc = _nvcc()
-    common = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "-I", INCLUDE, "-I", CSRC]
+    # -ffp-contract=off: host code rounds every product and sum separately on x86_64 and
+    # aarch64 alike, so the order search (a cost model in floating point) picks the same
+    # plans on both
+    common = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "-Xcompiler", "-ffp-contract=off",
+              "-I", INCLUDE, "-I", CSRC]
     objs = []
 
     def compile_one(src):

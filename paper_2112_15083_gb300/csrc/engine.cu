@@ -118,6 +118,8 @@ struct CallPlan {
     std::vector<CUtensorMap> maps;
     std::vector<size_t> vidx_off;              // per step: offset into the version index table
     std::vector<int> fold;                     // per step: 0, 1 (versions into M), 2 (into N)
+    std::vector<std::array<char, 2>> tc_inplace;  // per step and operand: tensor-core map over the
+                                                  // stored form of a gathered operand (no copy)
     std::vector<int> vidx;                     // host copy; device copy in CNet::vidx_dev
     std::vector<std::array<size_t, 2>> goff;   // per step: arena offsets of gathered operands
     std::vector<tnk::GatherDesc> gd;           // batch gathers (device copy in CNet::gdescs)
@@ -496,6 +498,7 @@ int prepare_call(DevMem &mem, CNet &cn, const std::vector<uint64_t> &slices, dou
     // the node's arena versions) and a table giving each C version's operand versions
     cp.map_off.assign(cn.steps.size(), 0);
     cp.vidx_off.assign(cn.steps.size(), 0);
+    cp.tc_inplace.assign(cn.steps.size(), {0, 0});
     cp.maps.clear();
     cp.vidx.clear();
     auto version_count = [&](int x) -> long long {
@@ -513,17 +516,25 @@ int prepare_call(DevMem &mem, CNet &cn, const std::vector<uint64_t> &slices, dou
         cp.vidx_off[i] = cp.vidx.size();
         const bool f16 = cn.fmt[s.a] == tnk::OUT_SPLIT_FP16;
         CUtensorMap ma, mb;
-        const void *ra = s.gat[0] ? static_cast<const char *>(cn.arena.p) + cp.goff[i][0] : region(s.a);
-        const void *rb = s.gat[1] ? static_cast<const char *>(cn.arena.p) + cp.goff[i][1] : region(s.b);
+        // a gathered operand of an unfolded step is read in place: its map spans the stored
+        // form, whose batch planes are the non-beta batch bits and the closed legs on top
+        const int nnb = s.nbat - cn.net.n_beta;
+        const bool ipa = s.gat[0] && cp.fold[i] == 0 && nnb >= 0, ipb = s.gat[1] && cp.fold[i] == 0 && nnb >= 0;
+        cp.tc_inplace[i] = {(char)ipa, (char)ipb};
+        const void *ra = ipa ? region(s.a) : s.gat[0] ? static_cast<const char *>(cn.arena.p) + cp.goff[i][0]
+                                                      : region(s.a);
+        const void *rb = ipb ? region(s.b) : s.gat[1] ? static_cast<const char *>(cn.arena.p) + cp.goff[i][1]
+                                                      : region(s.b);
+        const int lba = ipa ? nnb + s.g_nq[0] : s.nbat, lbb = ipb ? nnb + s.g_nq[1] : s.nbat;
         // B for 128-, 64- and 32-column tiles (a folded B wider than a tile keeps the
         // 128-column map; those variants are not offered for it)
         CUtensorMap mb64, mb32;
-        RC(encode_operand(&ma, ra, s.nk, s.nm, s.nbat, version_count(s.a), f16, cp.fold[i] == 1));
-        RC(encode_operand(&mb, rb, s.nk, s.nn, s.nbat, version_count(s.b), f16, cp.fold[i] == 2));
+        RC(encode_operand(&ma, ra, s.nk, s.nm, lba, version_count(s.a), f16, cp.fold[i] == 1));
+        RC(encode_operand(&mb, rb, s.nk, s.nn, lbb, version_count(s.b), f16, cp.fold[i] == 2));
         if (cp.fold[i] == 2 && s.nn > 6) mb64 = mb;
-        else RC(encode_operand(&mb64, rb, s.nk, s.nn, s.nbat, version_count(s.b), f16, cp.fold[i] == 2, 64));
+        else RC(encode_operand(&mb64, rb, s.nk, s.nn, lbb, version_count(s.b), f16, cp.fold[i] == 2, 64));
         if (cp.fold[i] == 2 && s.nn > 5) mb32 = mb;
-        else RC(encode_operand(&mb32, rb, s.nk, s.nn, s.nbat, version_count(s.b), f16, cp.fold[i] == 2, 32));
+        else RC(encode_operand(&mb32, rb, s.nk, s.nn, lbb, version_count(s.b), f16, cp.fold[i] == 2, 32));
         cp.maps.push_back(ma);
         cp.maps.push_back(mb);
         cp.maps.push_back(mb64);
@@ -710,6 +721,11 @@ bool skinny_fuses(const CNet &cn, size_t si) {
 bool reads_in_place(const CNet &cn, size_t si, int var) {
     if (var == kVarRow || var == kVarRowStage) return row_fuses(cn, si);
     if (var == kVarSkinny) return skinny_fuses(cn, si);
+    if (var == kVarTc128 || var == kVarTc64 || var == kVarTc32) {
+        const Step &s = cn.steps[si];
+        if (!(s.gat[0] || s.gat[1]) || cn.cp.tc_inplace.size() <= si) return false;
+        return (!s.gat[0] || cn.cp.tc_inplace[si][0]) && (!s.gat[1] || cn.cp.tc_inplace[si][1]);
+    }
     return false;
 }
 
@@ -727,6 +743,23 @@ int launch_tc(CNet &cn, const Step &s, size_t si, const tnk::GemmParams &p, cuda
     tp.out_scale = p.out_scale;
     tp.err = cn.d_err;
     tp.stall_cycles = cn.tc_stall;
+    for (int o = 0; o < 2; o++) {
+        if (cp.tc_inplace.size() <= si || !cp.tc_inplace[si][o]) continue;
+        if (!cn.cur_closed) { tn_set_error("tensor-core step: batch patterns missing"); return TN_EINVAL; }
+        tnk::TcGather &g = o ? tp.gb : tp.ga;
+        const int base = s.nk + (o ? s.nn : s.nm);  // read-layout position of batch bit 0
+        g.closed = cn.cur_closed;
+        g.nnb = s.nbat - cn.net.n_beta;
+        g.nq = s.g_nq[o];
+        if (s.nbat > 24 || g.nq > 32) { tn_set_error("tensor-core gather too wide"); return TN_EUNSUPPORTED; }
+        for (int t = 0; t < cn.net.n_beta; t++) {
+            const int i = s.g_pos_beta[o][t] - base;
+            if (i < 0 || i >= s.nbat) { tn_set_error("tensor-core gather: beta bit outside the batch dims"); return TN_EINVAL; }
+            g.beta_mask |= 1u << i;
+            g.beta_t[i] = (int8_t)t;
+        }
+        for (int t = 0; t < g.nq; t++) g.q[t] = (int8_t)s.g_q[o][t];
+    }
     tp.c_plane = p.c_vstride;
     for (int i = 0; i < s.nbat; i++) tp.pos_bat[i] = s.pos_bat[i];
     for (int i = 0; i < s.nm; i++) tp.pos_m[i] = s.pos_m[i];
@@ -2098,6 +2131,7 @@ int tn_trace_read(tn_plan_h p, tn_step_trace *out, int32_t cap, int32_t *n_out) 
         const bool has = cn.cp.valid && cn.cp.gd_off[si + 1] > cn.cp.gd_off[si];
         const bool in_place = reads_in_place(cn, (size_t)si, t.kernel);
         t.gathers = has && !in_place ? 1 : 0;
+        t.in_place = has && in_place ? 1 : 0;
     }
     return TN_OK;
 }
@@ -2304,19 +2338,17 @@ int tn_job_create(tn_plan_h p, double f_target, int64_t N, uint64_t seed, double
     // (the lowest free legs vary inside a chunk, so every chunk compiles alike)
     int64_t c = 1;
     while (c * 2 <= nsl && nsl % (c * 2) == 0 && (max_chunk_slices == 0 || c * 2 <= max_chunk_slices)) {
-        if (max_chunk_slices == 0) {
-            int64_t b = 0;
-            std::vector<uint64_t> sl(j->slices.begin(), j->slices.begin() + c * 2);
-            RC(estimate_call(p, sl, &b, nullptr, nullptr));
-            if ((double)b + job_bytes > 0.95 * p->budget) break;
-        }
+        int64_t b = 0;
+        std::vector<uint64_t> sl(j->slices.begin(), j->slices.begin() + c * 2);
+        RC(estimate_call(p, sl, &b, nullptr, nullptr));
+        if ((double)b + job_bytes > 0.95 * p->budget) break;
         c *= 2;
     }
     {
         int64_t b = 0;
         std::vector<uint64_t> sl(j->slices.begin(), j->slices.begin() + c);
         RC(estimate_call(p, sl, &b, nullptr, nullptr));
-        if ((double)b + job_bytes > p->budget && max_chunk_slices == 0) {
+        if ((double)b + job_bytes > p->budget) {
             tn_set_error("tn_job_create: one slice and the job's buffers exceed the HBM budget");
             return TN_ENOMEM;
         }

@@ -29,6 +29,33 @@ namespace tnk {
 constexpr int kTcBM = 128;
 constexpr int kTcBK = 32;      // K elements per ring slot (64 bytes per row: 64B swizzle)
 
+// An operand read in place from its stored form instead of a per-batch gathered copy.
+// The stored form is the read layout [K][rows][non-beta batch bits] with the operand's
+// closed legs on top; a tile of batch `bat` reads plane coordinate (non-beta bits of bat)
+// | (the batch pattern's bits q[0..nq) packed) << nnb, the pattern being the group's
+// closed_bits[beta index of bat].
+struct TcGather {
+    const uint64_t *closed;  // null: the operand is read as laid out (no gather)
+    uint32_t beta_mask;      // bits of bat that are beta (batch-index) bits
+    int8_t beta_t[24];       // for such bit i: which bit of the batch index it is
+    int nnb;                 // non-beta bits of bat
+    int nq;
+    int8_t q[32];            // closed positions of the pattern bits, lowest first
+};
+
+__device__ __forceinline__ int tc_gather_plane(const TcGather &g, int lbat, int bat) {
+    int beta = 0, nonb = 0, j = 0;
+    for (int i = 0; i < lbat; i++) {
+        const int bit = (bat >> i) & 1;
+        if ((g.beta_mask >> i) & 1) beta |= bit << g.beta_t[i];
+        else nonb |= bit << j++;
+    }
+    const uint64_t pat = g.closed[beta];
+    int sel = 0;
+    for (int t = 0; t < g.nq; t++) sel |= (int)((pat >> g.q[t]) & 1ull) << t;
+    return nonb | (sel << g.nnb);
+}
+
 struct TcParams {
     void *C;                 // output base (version 0); version v at C + 8 * v * c_plane bytes
     long long c_plane;       // elements per version (= split plane stride)
@@ -43,6 +70,7 @@ struct TcParams {
     int group_m;             // m tiles per raster group (>= 1): see tc_tile
     long long stall_cycles;  // > 0 (tests only): the MMA warp first waits this long on a
                              // barrier nothing arrives on, so the bounded-wait path runs
+    TcGather ga, gb;         // operands read in place through their batch gather
     int8_t pos_bat[kMaxBits], pos_m[kMaxBits], pos_n[kMaxBits];
 };
 
@@ -258,6 +286,11 @@ __global__ void __launch_bounds__(kTcThreads, 1)
                 const int ia = p.fold == 1 ? p.vidx[0] + tm_i * vm : p.vidx[p.fold == 2 ? 0 : v];
                 const int ib = p.fold == 2 ? p.vidx[p.nver] + tn_i * vn : p.vidx[p.nver + (p.fold == 1 ? 0 : v)];
                 const int rowA = p.fold == 1 ? 0 : tm_i * kTcBM, rowB = p.fold == 2 ? 0 : tn_i * BN;
+                // plane coordinates: plane pl of batch bat, or of its stored pattern block
+                const int pza = p.ga.closed ? tc_gather_plane(p.ga, p.lbat, bat) : bat;
+                const int pzb = p.gb.closed ? tc_gather_plane(p.gb, p.lbat, bat) : bat;
+                const int sza = p.ga.closed ? 1 << (p.ga.nnb + p.ga.nq) : BAT;
+                const int szb = p.gb.closed ? 1 << (p.gb.nnb + p.gb.nq) : BAT;
                 for (int kb = 0; kb < nkb; kb++, slot++) {
                     const int s = (int)(slot % STAGES);
                     if (slot >= STAGES &&
@@ -269,9 +302,9 @@ __global__ void __launch_bounds__(kTcThreads, 1)
                     mbar_expect_tx(fb, L::kStage);
                     unsigned char *st = smem + s * L::kStage;
                     for (int pl = 0; pl < 4; pl++) {
-                        tma_load_4d(smem_u32(st + pl * L::kAPlane), &tmA, kb * kTcBK, rowA, pl * BAT + bat, ia, fb);
+                        tma_load_4d(smem_u32(st + pl * L::kAPlane), &tmA, kb * kTcBK, rowA, pl * sza + pza, ia, fb);
                         tma_load_4d(smem_u32(st + 4 * L::kAPlane + pl * L::kBPlane), &tmB, kb * kTcBK, rowB,
-                                    pl * BAT + bat, ib, fb);
+                                    pl * szb + pzb, ib, fb);
                     }
                     issued = slot + 1;
                 }

@@ -109,6 +109,7 @@ class StepTrace(ctypes.Structure):
         ("flops_per_launch", ctypes.c_double), ("bytes_per_launch", ctypes.c_double),
         ("nbat", ctypes.c_int32), ("nm", ctypes.c_int32), ("nn", ctypes.c_int32), ("nk", ctypes.c_int32),
         ("nver", ctypes.c_int64), ("kernel", ctypes.c_int32), ("gathers", ctypes.c_int32),
+        ("in_place", ctypes.c_int32),
     ]
 
 

@@ -217,7 +217,7 @@ def test_job_bench_line_carries_the_contract(monkeypatch):
     # warm-up chunks 0-2, timed chunks 3-6, traced chunk 7
     assert job.ran == list(range(8))
     assert line["ms_per_step"] == pytest.approx(2.0)
-    chunks = 4096 // 2
+    chunks = 4096 // args.chunk
     assert line["job_seconds"] == pytest.approx(chunks * 2e-3 + line["finish_s"])
     assert line["value"] == pytest.approx(100000 / line["job_seconds"])
     # per traced chunk: 1 stem launch, 55 x (2 + 1 gather) batch launches, 55 slice sums,
