@@ -210,7 +210,7 @@ def cpu_cores():
 SUB_ROWS = 3  # rows of the 40-qubit grid the oracle's bounded sample simulates
 
 
-def oracle_job_sample(circ, openq, T, groups, N, seed, alpha=2.0, threads=None):
+def oracle_job_sample(circ, openq, T, groups, N, seed, alpha=2.0):
     """One bounded sample of the oracle's work on a job too large for it.  The oracle (FP64
     state vector) needs 2^n complex128 amplitudes: 17.6 TB at 40 qubits, which no host
     here holds.  Its work is one pass over the vector per gate (then the sampler on the
@@ -218,11 +218,8 @@ def oracle_job_sample(circ, openq, T, groups, N, seed, alpha=2.0, threads=None):
     gates acting there, the whole circuit's gate mix) and scaled by gates x amplitudes:
     t_job = (t_sub / (gates_sub 2^n_sub)) gates 2^n + t_sampler per batch x batches.
     Returns (job samples/s extrapolated, sample description, seconds spent)."""
-    import numpy as np
-    import oracle
+    import oracle  # noqa: F401
     from paper_2112_15083_gb300 import circuits as cg
-    if threads:
-        os.environ["OMP_NUM_THREADS"] = str(threads)
     n_sub = SUB_ROWS * circ.cols
     sub = cg.Circuit(n_qubits=n_sub, gates=[g for g in circ.gates if all(q < n_sub for q in g.qubits)])
     t0 = time.perf_counter()
@@ -244,11 +241,22 @@ def oracle_job_sample(circ, openq, T, groups, N, seed, alpha=2.0, threads=None):
     return N / t_job, desc, time.perf_counter() - t0
 
 
-def job_cpu_baseline(circ, openq, plan, info, w):
+def oracle_job_sample_child(workload, T, groups, threads):
+    """oracle_job_sample in a child process with `threads` OpenMP threads (the thread count
+    is read once per process); returns its samples/s."""
+    code = ("import json, sys; sys.path.insert(0, %r); import bench; from paper_2112_15083_gb300 import circuits as cg; "
+            "w = bench.JOB_WORKLOADS[%r]; c = cg.sycamore_grid(w['rows'], w['cols'], w['cycles'], seed=w['seed']); "
+            "v, d, s = bench.oracle_job_sample(c, cg.default_open_qubits(w['rows'], w['cols'], w['n_open']), %d, %d, "
+            "w['N'], 1, w['alpha']); print(json.dumps(v))" % (ROOT, workload, T, groups))
+    env = dict(os.environ, OMP_NUM_THREADS=str(threads))
+    r = subprocess.run([sys.executable, "-c", code], capture_output=True, text=True, env=env, timeout=600)
+    return float(r.stdout.strip().splitlines()[-1]) if r.returncode == 0 else None
+
+
+def job_cpu_baseline(circ, openq, plan, info, w, workload):
     cores = cpu_cores()
-    v, desc, _ = oracle_job_sample(circ, openq, info["T"], info["groups"], w["N"], 1, w["alpha"], threads=cores)
-    v1, _d1, _ = oracle_job_sample(circ, openq, info["T"], info["groups"], w["N"], 1, w["alpha"], threads=1)
-    os.environ["OMP_NUM_THREADS"] = str(cores)
+    v, desc, _ = oracle_job_sample(circ, openq, info["T"], info["groups"], w["N"], 1, w["alpha"])
+    v1 = oracle_job_sample_child(workload, info["T"], info["groups"], 1)
     return {"value": v, "unit": "samples/s", "cores": cores, "kind": "oracle", "cpu": cpu_model(), "sample": desc,
             "value_single_thread": v1}
 
@@ -698,7 +706,7 @@ def run_job(args):
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        cpu = job_cpu_baseline(circ, openq, plan, info, w)
+        cpu = job_cpu_baseline(circ, openq, plan, info, w, args.workload)
 
     secondary = None
     if rank == 0 and world == 1 and not args.no_secondary:

@@ -9,10 +9,11 @@
 // (Cr, Ci); the subtracted products use the descriptor's negate-A bit.
 //
 // One CTA computes a 128 x BN tile: warp 0 / lane 0 streams the 8 operand plane tiles
-// of each 32-wide K slice with 3-D TMA (64-byte swizzle) into a 3-stage ring, warp 1 /
-// lane 0 issues the MMAs and releases ring slots with tcgen05.commit, and all four
-// warps read the accumulators back with tcgen05.ld (warp w owns TMEM lanes 32w..32w+31,
-// i.e. tile rows) and store in the consumer's format through the bit-scatter epilogue.
+// of each 32-wide K slice with 4-D TMA (64-byte swizzle) into a ring of stages, warp 1 /
+// lane 0 issues the MMAs and releases ring slots with tcgen05.commit, and eight epilogue
+// warps read the accumulators back with tcgen05.ld (warp w owns TMEM lanes
+// 32 (w % 4) .. 32 (w % 4) + 31, i.e. tile rows, and half of the columns) and store in the
+// consumer's format through the bit-scatter epilogue.
 // Every mbarrier wait is bounded: on timeout the CTA sets *err, stops, waits (bounded)
 // for work it already issued, frees its TMEM and returns.
 #pragma once
@@ -202,6 +203,28 @@ __device__ __forceinline__ void tmem_ld16(uint32_t taddr, float *v) {
     for (int i = 0; i < 16; i++) v[i] = __uint_as_float(r[i]);
 }
 
+// Both accumulators' 16 columns (Cr, Ci) with one wait for the two loads.
+__device__ __forceinline__ void tmem_ld16x2(uint32_t ta, uint32_t tb, float *va, float *vb) {
+    uint32_t r[32];
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x16.b32 "
+        "{%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%32];\n\t"
+        "tcgen05.ld.sync.aligned.32x32b.x16.b32 "
+        "{%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%33];\n\t"
+        "tcgen05.wait::ld.sync.aligned;"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+          "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]),
+          "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]),
+          "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+        : "r"(ta), "r"(tb)
+        : "memory");
+#pragma unroll
+    for (int i = 0; i < 16; i++) {
+        va[i] = __uint_as_float(r[i]);
+        vb[i] = __uint_as_float(r[16 + i]);
+    }
+}
+
 template <int BN, int STAGES>
 struct TcSmem {
     static constexpr int kAPlane = kTcBM * kTcBK * 2;  // bytes per A plane tile
@@ -210,7 +233,8 @@ struct TcSmem {
     static constexpr int kBytes = STAGES * kStage + 1024 /*barriers*/ + 1024 /*alignment*/;
 };
 
-constexpr int kTcThreads = 192;  // warp 0: TMA, warp 1: MMA, warps 2-5: epilogue
+constexpr int kTcEpiWarps = 8;   // two per TMEM lane quarter, each owning half the tile's columns
+constexpr int kTcThreads = 64 + 32 * kTcEpiWarps;  // warp 0: TMA, warp 1: MMA, warps 2-9: epilogue
 
 // Persistent kernel: CTA c processes tiles c, c + gridDim.x, ...  Tile order: N tiles
 // fastest, then M tiles, then batch, then explicit version (CTAs running together share
@@ -257,7 +281,7 @@ __global__ void __launch_bounds__(kTcThreads, 1)
         }
         for (int b = 0; b < 2; b++) {
             mbar_init(smem_u32(&acc_full[b]), 1);
-            mbar_init(smem_u32(&acc_empty[b]), 4);  // one arrive per epilogue warp
+            mbar_init(smem_u32(&acc_empty[b]), kTcEpiWarps);  // one arrive per epilogue warp
         }
         mbar_init(smem_u32(never), 1);
         *abort_flag = 0;
@@ -362,8 +386,10 @@ __global__ void __launch_bounds__(kTcThreads, 1)
             if (*abort_flag && last_b >= 0) mbar_drain(smem_u32(&acc_full[last_b]), last_par, kLimit);
         }
     } else {
-        // epilogue warps 2..5: TMEM lane quarter = warp % 4 = tile rows 32*(warp%4)..
+        // epilogue warps 2..9: TMEM lane quarter = warp % 4 = tile rows 32*(warp%4)..; warps
+        // 2-5 store columns [0, BN/2) of the tile, warps 6-9 columns [BN/2, BN)
         const int quarter = warp & 3;
+        const int c_begin = ((warp - 2) >> 2) * (BN / 2), c_end = c_begin + BN / 2;
         const int row = 32 * quarter + lane;
         const long long M = 1LL << p.lm, N = 1LL << p.ln;
         // scatter(n0 + c0 + j) = scatter(n0 + c0) + scatter(j) for j < 16 (disjoint bits)
@@ -389,11 +415,10 @@ __global__ void __launch_bounds__(kTcThreads, 1)
             const bool row_ok = m < M && vrow < p.nver;
             const long long cbase = scatter_bits(bat, p.pos_bat, p.lbat) + (row_ok ? scatter_bits(m, p.pos_m, p.lm) : 0);
             const uint32_t lane_addr = tmem + ((uint32_t)(32 * quarter) << 16) + (uint32_t)(b * 2 * BN);
-            for (int c0 = 0; c0 < BN; c0 += 16) {
+            for (int c0 = c_begin; c0 < c_end; c0 += 16) {
                 float re[16], im[16];
                 __syncwarp();
-                tmem_ld16(lane_addr + c0, re);
-                tmem_ld16(lane_addr + BN + c0, im);
+                tmem_ld16x2(lane_addr + c0, lane_addr + BN + c0, re, im);
                 if (!row_ok) continue;
                 if (p.fold == 2) {
                     // columns: version (c0 + j) / N of this tile, n = (c0 + j) % N

@@ -306,25 +306,27 @@ def test_bounded_wait_times_out_and_the_plan_recovers():
 
 # ------------------------------------------------------------------ gathered operands read in place
 
-@pytest.mark.parametrize("q_lb", [(8, 10), (10, 12)])
-def test_tensor_core_steps_read_gathered_operands_in_place(q_lb):
-    """Batch steps on the tensor cores read an operand with closed legs (the batch's
-    selection of a batch-independent tensor) straight from its stored form through a
-    tensor map, one plane coordinate per batch; every amplitude against the oracle."""
+@pytest.mark.parametrize("seed,n_sliced", [(0, 0), (1, 4)])
+def test_tensor_core_steps_read_gathered_operands_in_place(seed, n_sliced):
+    """4x6 grid, 14 cycles, 1024 batches (+5 in a ragged second group): a batch step on the
+    tensor cores, (10,8,5,7), reads an operand with closed legs (the batch's selection of
+    a batch-independent tensor) straight from its stored form through a tensor map, one
+    plane coordinate per batch; every amplitude against the oracle's state vector."""
     P = pkg()
-    circ = cg.sycamore_grid(4, 5, q_lb[0] + 2, seed=3)
-    openq = cg.default_open_qubits(4, 5, 6)
+    circ = cg.sycamore_grid(4, 6, 14, seed=seed)
+    openq = cg.default_open_qubits(4, 6, 6)
     C = P.circuit_load(circ.serialize())
-    plan = P.plan(C, openq, n_auto_sliced=4, log2_batches=q_lb[1], order_trials=16, precision=P.tn.PREC_BF16X2)
-    cb = cg.random_closed_bits((1 << q_lb[1]) + 5, 14, seed=7)
-    slices = np.arange(16, dtype=np.uint64)
+    plan = P.plan(C, openq, n_auto_sliced=n_sliced, log2_batches=10, order_trials=16,
+                  precision=P.tn.PREC_BF16X2)
+    cb = cg.random_closed_bits(1024 + 5, 18, seed=7)
+    slices = np.arange(1 << n_sliced, dtype=np.uint64)
     plan.contract(slices, cb)
     plan.trace(True)
     amps = plan.contract(slices, cb)
     tr = plan.trace_read()
     plan.trace(False)
     tc_in_place = [s for s in tr if s["kernel"] in (9128, 9064, 9032) and s["in_place"] and s["launches"]]
-    print("tensor-core steps reading gathered operands in place:",
-          [(s["nbat"], s["nm"], s["nn"], s["nk"]) for s in tc_in_place])
-    ref = oracle.batch_amplitudes(oracle.simulate(circ), 20, openq, cb)
+    assert tc_in_place, "no tensor-core step read a gathered operand in place"
+    assert all(s["gathers"] == 0 for s in tc_in_place)
+    ref = oracle.batch_amplitudes(oracle.simulate(circ), 24, openq, cb)
     assert np.linalg.norm(amps - ref) / np.linalg.norm(ref) <= 1e-3
