@@ -562,7 +562,9 @@ StepEst step_estimate(const Network &net, const Node &a, const Node &b, const No
                             : flop_rate / 16;
     // at most 8 x 32 outputs over K >= 1024: the long-K kernel streams the operands, so the
     // bytes bound it
-    if (lo <= 3 && hi <= 5 && nk >= 10) rate = flop_rate;
+    if (lo <= 3 && hi <= 5 && nk >= 10) {
+        rate = flop_rate;
+    }
     if (net.tc_flop_rate > 0 && tn_tc_shape(hi, lo, nk)) {
         rate = net.tc_flop_rate * (lo >= 6 ? 1.0 : 0.5);
         // a batch of products of one or two output tiles each pays the tile's pipeline
@@ -1586,6 +1588,24 @@ int tn_plan_build_host(const Merged &mg, const tn_plan_opts &o, const int32_t *o
         net.q_max = t0.q_max >= -1 ? t0.q_max : net.q_max;
         tree = t0;
         tn_recompute_deps(net, tree);
+        // re-optimise its subtrees for the per-slice cost under the size cap: the search
+        // priced the unsliced network, where the sliced legs were not yet sliced (kept
+        // only when cheaper with every tensor within the cap)
+        {
+            net.per_slice = true;
+            net.cap_bits = o.max_log2_tensor;
+            Tree r;
+            if (reconfigured(net, tree, r)) {
+                r.q_max = tree.q_max;
+                int widest = 0;
+                for (const Node &nd : r.nodes) widest = std::max(widest, nd.idx.count());
+                if (widest <= o.max_log2_tensor && tn_tree_cost(net, r).time < tn_tree_cost(net, tree).time)
+                    tree = r;
+            }
+            net.per_slice = false;
+            net.cap_bits = 0;
+            tn_recompute_deps(net, tree);
+        }
         // optionally anneal it for the per-slice cost under the size cap (kept only when
         // cheaper with every tensor within the cap)
         if (net.anneal_iters > 0) {
