@@ -635,11 +635,11 @@ bool rowstage_fits(const CNet &cn, const Step &s) {
 }
 constexpr int kTiles[7][2] = {{128, 64}, {64, 64}, {128, 32}, {64, 32}, {32, 32}, {128, 16}, {16, 16}};
 
-// Whether the long-K kernel runs step si: at most 8 outputs on the short side and 32 on
+// Whether the long-K kernel runs step si: at most 8 outputs on the short side and 64 on
 // the long side, K >= 1024, complex64 operands.  It is then the step's only kernel (its
 // lane split of K rounds differently from the others).
 bool skinny_fits(const CNet &cn, const Step &s) {
-    return cn.elem == 8 && std::min(s.nm, s.nn) <= 3 && std::max(s.nm, s.nn) <= 5 && s.nk >= 10 &&
+    return cn.elem == 8 && std::min(s.nm, s.nn) <= 3 && std::max(s.nm, s.nn) <= 6 && s.nk >= 10 &&
            cn.fmt[s.a] == tnk::OUT_C64 && cn.fmt[s.b] == tnk::OUT_C64 &&
            (cn.use_tc.empty() || !cn.use_tc[&s - cn.steps.data()]);
 }
@@ -916,9 +916,9 @@ int launch_variant(CNet &cn, const Step &s, cudaStream_t st, int var) {
                 std::swap(p.lm, p.ln);
                 for (int i = 0; i < tnk::kMaxBits; i++) std::swap(p.pos_m[i], p.pos_n[i]);
             }
-            // W warps per batch, MW rows of A each (W MW = M)
-            const long long batches = p.nver << p.lbat;
-            const unsigned blocks = (unsigned)std::min<long long>(batches, 8LL * num_sms());
+            // blocks of W warps with MW rows of A each (W MW = min(M, 32) rows per block)
+            const long long units = (p.nver << p.lbat) * std::max(1, (1 << p.lm) / 32);
+            const unsigned blocks = (unsigned)std::min<long long>(units, 8LL * num_sms());
             auto go = [&](auto kern, int warps) { kern<<<blocks, 32 * warps, 0, st>>>(p); };
             auto by_n = [&](auto m_tag) {
                 constexpr int M = decltype(m_tag)::value;
@@ -936,7 +936,7 @@ int launch_variant(CNet &cn, const Step &s, cudaStream_t st, int var) {
                 case 2: by_n(std::integral_constant<int, 4>{}); break;
                 case 3: by_n(std::integral_constant<int, 8>{}); break;
                 case 4: by_n(std::integral_constant<int, 16>{}); break;
-                default: by_n(std::integral_constant<int, 32>{}); break;
+                default: by_n(std::integral_constant<int, 32>{}); break;  // 64 rows: two row blocks
             }
         } else {
             tn_set_error("long-K kernel on a complex128 network");

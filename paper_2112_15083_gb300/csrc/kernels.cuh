@@ -321,9 +321,10 @@ __global__ void __launch_bounds__(32 * kRowWarps) cgemm_rowstage(GemmParams p) {
     }
 }
 
-// Batched products with at most 32 rows and 8 columns and a long K (K >= 1024, complex64
-// operands).  A block of W warps takes one (version, batch) at a time; warp w owns rows
-// MW w .. MW w + MW - 1 of A and every column.  Per 64-element K block (kSkinnyU blocks
+// Batched products with at most 64 rows and 8 columns and a long K (K >= 1024, complex64
+// operands).  A block of W warps takes W MW rows of one (version, batch) at a time (a
+// batch with more rows is split into row blocks); each warp owns MW rows of A and every
+// column.  Per 64-element K block (kSkinnyU blocks
 // per stage), lane l reads
 // elements 2 l and 2 l + 1 of its A rows (16-byte loads, 512 contiguous bytes per row and
 // warp, evict-first) and of the B rows its warp stages, and the block shares the staged B
@@ -338,14 +339,19 @@ template <int W, int MW, int N>
 __global__ void __launch_bounds__(32 * W) cgemm_skinny(GemmParams p) {
     __shared__ float4 sB[2][kSkinnyU][N][32];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    const long long batches = p.nver << p.lbat;
+    // a block covers W MW rows of one batch: row blocks of the batch, then batches
+    const int row_blocks = (1 << p.lm) / (W * MW);
+    const long long units = (p.nver << p.lbat) * row_blocks;
     const int K = 1 << p.lk;
-    for (long long bv = blockIdx.x; bv < batches; bv += gridDim.x) {
+    for (long long u = blockIdx.x; u < units; u += gridDim.x) {
+        const int rb = (int)(u % row_blocks);
+        const long long bv = u / row_blocks;
         const long long bat = bv & ((1LL << p.lbat) - 1), v = bv >> p.lbat;
+        const int row0 = rb * W * MW + warp * MW;  // this warp's first row of A
         const float2 *a[MW], *b[(N + W - 1) / W];
 #pragma unroll
         for (int i = 0; i < MW; i++) {
-            const long long e = ((bat << p.lm) | (long long)(warp * MW + i)) << p.lk;
+            const long long e = ((bat << p.lm) | (long long)(row0 + i)) << p.lk;
             a[i] = p.gA ? reinterpret_cast<const float2 *>(p.gA->src) +
                               gather_src_warp(*p.gA, e, p.gA->pos_beta[p.gA->lb - 1], p.closed_bits)
                         : static_cast<const float2 *>(p.ptrA[v]) + e;
@@ -411,7 +417,7 @@ __global__ void __launch_bounds__(32 * W) cgemm_skinny(GemmParams p) {
 #pragma unroll
             for (int n = 0; n < N; n++)
                 if (lane == i * N + n)
-                    store_c(p, v, cb + scatter_bits(warp * MW + i, p.pos_m, p.lm) + scatter_bits(n, p.pos_n, p.ln),
+                    store_c(p, v, cb + scatter_bits(row0 + i, p.pos_m, p.lm) + scatter_bits(n, p.pos_n, p.ln),
                             acc[i][n]);
         __syncthreads();  // the staging buffers are reused by the block's next batch
     }

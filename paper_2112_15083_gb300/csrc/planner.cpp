@@ -562,7 +562,7 @@ StepEst step_estimate(const Network &net, const Node &a, const Node &b, const No
                             : flop_rate / 16;
     // at most 8 x 32 outputs over K >= 1024: the long-K kernel streams the operands, so the
     // bytes bound it
-    if (lo <= 3 && hi <= 5 && nk >= 10) {
+    if (lo <= 3 && hi <= 6 && nk >= 10) {
         rate = flop_rate;
     }
     if (net.tc_flop_rate > 0 && tn_tc_shape(hi, lo, nk)) {
