@@ -329,10 +329,18 @@ def run_reference(args):
 
 # ---------------------------------------------------------------- our path
 
-TC_VARIANTS = (9128, 9064, 9032)
+TC_VARIANTS = (9128, 9064, 9032, 19128, 19064)
+STACKED_VARIANTS = (19128, 19064)  # one stack-list launch before each launch
+
+
+def launches_per(s):
+    """Kernel launches per launch of a traced step: its gather and stack-list launches."""
+    return 1 + s["gathers"] + (1 if s["kernel"] in STACKED_VARIANTS else 0)
 
 
 def kernel_name(k):
+    if k in STACKED_VARIANTS:
+        return "tc_cgemm<%d,%d> stacked" % (k - 19000, {19128: 3, 19064: 4}[k])
     if k in TC_VARIANTS:
         return "tc_cgemm<%d,%d>" % (k - 9000, {9128: 3, 9064: 4, 9032: 5}.get(k, 0))
     if k in KERNEL_NAMES:
@@ -549,7 +557,7 @@ def run_group(args, with_e2e=True, with_cpu=True):
         "cpu_baseline": cpu, "e2e": e2e, "top_steps": top_steps_of(steps_tr), "slice_sum": slice_sum_of(ssum),
         # the job's contraction launches, batch gathers and slice sums, plus a batch draw and
         # a sampler launch per step
-        "gpu_launches": (sum(s["launches"] * (1 + s["gathers"]) for s in steps_tr)
+        "gpu_launches": (sum(s["launches"] * launches_per(s) for s in steps_tr)
                          + sum(s["launches"] for s in ssum) + 2 * args.steps),
     }
 
@@ -714,7 +722,7 @@ def run_job(args):
 
     if rank != 0:
         return None
-    per_chunk_launches = (sum(s["launches"] * (1 + s["gathers"]) for s in steps_tr) + sum(s["launches"] for s in ssum)
+    per_chunk_launches = (sum(s["launches"] * launches_per(s) for s in steps_tr) + sum(s["launches"] for s in ssum)
                           + info["groups"])
     return {
         "metric": METRIC, "value": value, "unit": "samples/s", "n_gpus": world, "steps": args.steps,

@@ -406,6 +406,10 @@ typedef struct {
                        staged through shared memory, 5: long-K kernel (at most 8 x 32
                        outputs per batch, K >= 1024), 9128 / 9064 / 9032:
                        tensor-core kernel with 128- / 64- / 32-column tiles,
+                       19128 / 19064: stacked tensor-core tiles of 128 / 64 columns (the
+                       batches of a group that read the same stored block of an in-place
+                       operand, 2 to 4 side by side; each launch is preceded by one
+                       launch that builds the group's stack list),
                        TM*1000+TN: FFMA tile kernel */
     int32_t gathers;  /* batch-gather launches that precede each launch of the step (0 or
                          1; 0 when the kernel reads its gathered operands in place) */

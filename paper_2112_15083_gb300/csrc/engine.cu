@@ -160,6 +160,7 @@ struct CNet {
     std::vector<int> leaf_codebits;
     std::vector<std::vector<int>> leaf_sl;  // sliced legs (e) in leg order
     DBuf arena, tables, vidx_dev, gdescs, gtabs;
+    DBuf stacks;  // stacked tensor-core tiles: the group's stack list (tnk::tc_stack_build)
     CallPlan cp;
     std::vector<int> parent;
     size_t leaf_bytes = 0;
@@ -263,6 +264,10 @@ int get_encoder() {
 // 4-D map of a split operand: [versions][4 * BAT planes][rows][K] of 2-byte elements
 // (a version is 8 bytes per element: four planes), tiles of 32 (K) x 128 rows, 64-byte
 // swizzle; out-of-range rows/columns read as zero.
+// Stacked tensor-core tiles sort a group's batch indices in shared memory (8 bytes each):
+// up to 2^14 batches per group.
+constexpr int kStackMaxBeta = 14;
+
 int encode_operand(CUtensorMap *m, const void *base, int lk, int lrows, int lbat, long long nver, bool fp16,
                    bool fold = false, int box_rows = 128) {
     RC(get_encoder());
@@ -303,6 +308,8 @@ int setup_leaves(DevMem &mem, CNet &cn) {
                                 tnk::TcSmem<64, 4>::kBytes));
         CK(cudaFuncSetAttribute(tnk::tc_cgemm<32, 5>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                 tnk::TcSmem<32, 5>::kBytes));
+        CK(cudaFuncSetAttribute(tnk::tc_stack_build, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                8 << kStackMaxBeta));
         smem_set = true;
     }
     for (auto &b : cn.leaf_src) release(mem, b);
@@ -390,6 +397,7 @@ void free_cnet(DevMem &mem, CNet &cn) {
     release(mem, cn.arena);
     release(mem, cn.tables);
     release(mem, cn.vidx_dev);
+    release(mem, cn.stacks);
     release(mem, cn.err);
     release(mem, cn.absmax);
     cn.d_err = nullptr;
@@ -607,6 +615,12 @@ int prepare_call(DevMem &mem, CNet &cn, const std::vector<uint64_t> &slices, dou
         CK(cudaMemcpyAsync(cn.gdescs.p, cp.gd.data(), cp.gd.size() * sizeof(tnk::GatherDesc), cudaMemcpyHostToDevice,
                            mem.stream));
     }
+    // the stack list of stacked tensor-core tiles (any step with an in-place A may use them)
+    for (size_t i = 0; i < cn.steps.size(); i++) {
+        if (!cp.tc_inplace[i][0] || cn.net.n_beta > kStackMaxBeta) continue;
+        RC(ensure(mem, cn.stacks, (1 + ((size_t)(tnk::kTcMaxStack + 1) << cn.net.n_beta)) * sizeof(int)));
+        break;
+    }
     if (!cp.vidx.empty()) {
         RC(ensure(mem, cn.vidx_dev, cp.vidx.size() * sizeof(int)));
         CK(cudaMemcpyAsync(cn.vidx_dev.p, cp.vidx.data(), cp.vidx.size() * sizeof(int), cudaMemcpyHostToDevice,
@@ -624,9 +638,32 @@ int prepare_call(DevMem &mem, CNet &cn, const std::vector<uint64_t> &slices, dou
 }
 
 // Kernel variants of a step (ids as in tn_step_trace.kernel): 0 row kernel, 1 staged
-// small products, TM*1000+TN FFMA tile, 9128 / 9064 tensor-core tile of 128 / 64 columns.
+// small products, 4 staged row kernel, 5 long-K kernel, TM*1000+TN FFMA tile, 9128 / 9064 /
+// 9032 tensor-core tile of 128 / 64 / 32 columns, 19128 / 19064 stacked tensor-core tile of
+// 128 / 64 columns (batches sharing a stored block of A side by side).
 constexpr int kVarRow = 0, kVarSmall = 1, kVarRowStage = 4, kVarSkinny = 5, kVarTc128 = 9128, kVarTc64 = 9064,
-              kVarTc32 = 9032;
+              kVarTc32 = 9032, kVarTcS128 = 19128, kVarTcS64 = 19064;
+
+bool is_tc_variant(int v) {
+    return v == kVarTc128 || v == kVarTc64 || v == kVarTc32 || v == kVarTcS128 || v == kVarTcS64;
+}
+
+// Whether step si can run stacked tensor-core tiles of BN columns: A read in place from its
+// stored form, N of 32 or 64 (two to four batches per tile), at most 2^14 batches per
+// group, and a B read in place (if any) with its batch-index bits where A has them.
+bool stack_fits(const CNet &cn, size_t si, int BN) {
+    const Step &s = cn.steps[si];
+    const CallPlan &cp = cn.cp;
+    if (cn.use_tc.empty() || !cn.use_tc[si] || cp.tc_inplace.size() <= si || !cp.tc_inplace[si][0]) return false;
+    if (!cn.stacks.p || cp.fold.size() <= si || cp.fold[si] != 0) return false;
+    if ((s.nn != 5 && s.nn != 6) || (BN >> s.nn) < 2 || (BN >> s.nn) > tnk::kTcMaxStack) return false;
+    const int nb = cn.net.n_beta;
+    if (nb < 1 || nb > kStackMaxBeta || s.nbat < nb || s.nbat > 24) return false;
+    if (cp.tc_inplace[si][1])
+        for (int t = 0; t < nb; t++)
+            if (s.g_pos_beta[1][t] - (s.nk + s.nn) != s.g_pos_beta[0][t] - (s.nk + s.nm)) return false;
+    return true;
+}
 
 // Whether the staged row kernel can run step si: the row kernel's shapes with complex64
 // rows of 16 to 64 elements.
@@ -655,9 +692,12 @@ std::vector<int> step_variants(const CNet &cn, size_t si) {
     std::vector<int> v;
     if (skinny_fits(cn, s)) return {kVarSkinny};
     if (!cn.use_tc.empty() && cn.use_tc[si]) {
-        if (s.nn <= 5) return {kVarTc32, kVarTc64};
-        if (s.nn == 6) return {kVarTc128, kVarTc64, kVarTc32};
-        return {kVarTc128, kVarTc64};
+        if (s.nn <= 5) v = {kVarTc32, kVarTc64};
+        else if (s.nn == 6) v = {kVarTc128, kVarTc64, kVarTc32};
+        else v = {kVarTc128, kVarTc64};
+        if (stack_fits(cn, si, 128)) v.push_back(kVarTcS128);
+        if (stack_fits(cn, si, 64)) v.push_back(kVarTcS64);
+        return v;
     }
     if (std::min(s.nm, s.nn) <= 5 && s.nk <= 6) v.push_back(kVarRow);
     if (rowstage_fits(cn, s)) v.push_back(kVarRowStage);
@@ -721,7 +761,7 @@ bool skinny_fuses(const CNet &cn, size_t si) {
 bool reads_in_place(const CNet &cn, size_t si, int var) {
     if (var == kVarRow || var == kVarRowStage) return row_fuses(cn, si);
     if (var == kVarSkinny) return skinny_fuses(cn, si);
-    if (var == kVarTc128 || var == kVarTc64 || var == kVarTc32) {
+    if (is_tc_variant(var)) {
         const Step &s = cn.steps[si];
         if (!(s.gat[0] || s.gat[1]) || cn.cp.tc_inplace.size() <= si) return false;
         return (!s.gat[0] || cn.cp.tc_inplace[si][0]) && (!s.gat[1] || cn.cp.tc_inplace[si][1]);
@@ -730,7 +770,7 @@ bool reads_in_place(const CNet &cn, size_t si, int var) {
 }
 
 template <int BN, int ST>
-int launch_tc(CNet &cn, const Step &s, size_t si, const tnk::GemmParams &p, cudaStream_t st) {
+int launch_tc(CNet &cn, const Step &s, size_t si, const tnk::GemmParams &p, cudaStream_t st, bool stacked = false) {
     const CallPlan &cp = cn.cp;
     tnk::TcParams tp;
     std::memset(&tp, 0, sizeof(tp));
@@ -759,6 +799,18 @@ int launch_tc(CNet &cn, const Step &s, size_t si, const tnk::GemmParams &p, cuda
             g.beta_t[i] = (int8_t)t;
         }
         for (int t = 0; t < g.nq; t++) g.q[t] = (int8_t)s.g_q[o][t];
+    }
+    // stacked tiles: this group's stack list first (same stream), then tiles of S batches
+    if (stacked) {
+        if (!stack_fits(cn, si, BN) || !cn.cur_closed) {
+            tn_set_error("stacked tensor-core tile: step not eligible");
+            return TN_EINVAL;
+        }
+        tp.stack = static_cast<const int *>(cn.stacks.p);
+        tp.stack_S = BN >> s.nn;
+        tnk::tc_stack_build<<<1, 1024, (size_t)8 << cn.net.n_beta, st>>>(tp.ga, cn.net.n_beta, tp.stack_S,
+                                                                          static_cast<int *>(cn.stacks.p));
+        CK(cudaGetLastError());
     }
     tp.c_plane = p.c_vstride;
     for (int i = 0; i < s.nbat; i++) tp.pos_bat[i] = s.pos_bat[i];
@@ -790,8 +842,9 @@ int launch_tc(CNet &cn, const Step &s, size_t si, const tnk::GemmParams &p, cuda
         tp.group_m = (int)std::max<long long>(1, std::min<long long>({g, 64, tiles_m}));
     }
     const CUtensorMap *m = &cp.maps[cp.map_off[si]];
-    tnk::tc_cgemm<BN, ST><<<(unsigned)blocks, tnk::kTcThreads, Lay::kBytes, st>>>(m[0], m[BN == 128 ? 1 : BN == 64 ? 2 : 3],
-                                                                                 tp);
+    // B map: box of BN rows, or of one stacked batch's N rows
+    const int ib = stacked ? (s.nn == 6 ? 2 : 3) : (BN == 128 ? 1 : BN == 64 ? 2 : 3);
+    tnk::tc_cgemm<BN, ST><<<(unsigned)blocks, tnk::kTcThreads, Lay::kBytes, st>>>(m[0], m[ib], tp);
     CK(cudaGetLastError());
     return TN_OK;
 }
@@ -847,10 +900,12 @@ int launch_variant(CNet &cn, const Step &s, cudaStream_t st, int var) {
     RC(step_params(cn, s, p));
     const size_t si = &s - cn.steps.data();
     if (cn.trace) cn.tr_kernel[si] = var;
-    if (var == kVarTc128 || var == kVarTc64 || var == kVarTc32) {
+    if (is_tc_variant(var)) {
         if constexpr (sizeof(T) == sizeof(float2)) {
             if (var == kVarTc128) return launch_tc<128, 3>(cn, s, si, p, st);
             if (var == kVarTc64) return launch_tc<64, 4>(cn, s, si, p, st);
+            if (var == kVarTcS128) return launch_tc<128, 3>(cn, s, si, p, st, true);
+            if (var == kVarTcS64) return launch_tc<64, 4>(cn, s, si, p, st, true);
             return launch_tc<32, 5>(cn, s, si, p, st);
         }
         tn_set_error("tensor-core variant on a complex128 network");
@@ -1149,8 +1204,10 @@ std::map<std::vector<long long>, int> g_tune;
 
 std::vector<long long> tune_key(const CNet &cn, size_t si) {
     const Step &s = cn.steps[si];
+    const bool ipa = cn.cp.tc_inplace.size() > si && cn.cp.tc_inplace[si][0];
+    const bool ipb = cn.cp.tc_inplace.size() > si && cn.cp.tc_inplace[si][1];
     return {cn.elem, cn.use_tc.empty() ? 0 : cn.use_tc[si], cn.cp.fold.empty() ? 0 : cn.cp.fold[si], cn.fmt[s.a],
-            cn.fmt[s.c], s.nbat, s.nm, s.nn, s.nk, cn.cp.nver[s.c]};
+            cn.fmt[s.c], s.nbat, s.nm, s.nn, s.nk, cn.cp.nver[s.c], ipa + 2 * ipb + 4 * stack_fits(cn, si, 128)};
 }
 
 // Fill in every step's variant that is known (single candidate, autotuning off, or a

@@ -44,6 +44,13 @@ struct TcGather {
     int8_t q[32];            // closed positions of the pattern bits, lowest first
 };
 
+// The stored block a batch pattern selects: its bits at the closed positions q[].
+__device__ __forceinline__ int tc_gather_sel(const TcGather &g, uint64_t pat) {
+    int sel = 0;
+    for (int t = 0; t < g.nq; t++) sel |= (int)((pat >> g.q[t]) & 1ull) << t;
+    return sel;
+}
+
 __device__ __forceinline__ int tc_gather_plane(const TcGather &g, int lbat, int bat) {
     int beta = 0, nonb = 0, j = 0;
     for (int i = 0; i < lbat; i++) {
@@ -51,10 +58,98 @@ __device__ __forceinline__ int tc_gather_plane(const TcGather &g, int lbat, int 
         if ((g.beta_mask >> i) & 1) beta |= bit << g.beta_t[i];
         else nonb |= bit << j++;
     }
-    const uint64_t pat = g.closed[beta];
-    int sel = 0;
-    for (int t = 0; t < g.nq; t++) sel |= (int)((pat >> g.q[t]) & 1ull) << t;
-    return nonb | (sel << g.nnb);
+    return nonb | (tc_gather_sel(g, g.closed[beta]) << g.nnb);
+}
+
+// The batch index whose beta bits are `beta` and whose other bits are `nonb` (lowest first).
+__device__ __forceinline__ int tc_compose_bat(const TcGather &g, int lbat, int nonb, int beta) {
+    int bat = 0, j = 0;
+    for (int i = 0; i < lbat; i++) {
+        const int bit = ((g.beta_mask >> i) & 1) ? (beta >> g.beta_t[i]) & 1 : (nonb >> j++) & 1;
+        bat |= bit << i;
+    }
+    return bat;
+}
+
+// Stacked tiles.  The batches of a group whose patterns select the same stored block of
+// the in-place operand A multiply the same A matrix; a stacked tile takes up to S of them
+// (S = BN / N) and puts their B rows side by side in its BN columns, so the A panel is
+// loaded once for S batches and one MMA of BN columns serves them all.  The stack list is
+// built on the device per group (tc_stack_build): word 0 the number of stacks, then S + 1
+// words per stack: the selected block, then S batch indices (beta), -1 in unused slots
+// (the valid ones first).
+constexpr int kTcMaxStack = 4;
+
+// Sorts the group's T = 2^nbeta batch indices by (selected block, beta) with a bitonic
+// sort in shared memory (deterministic), then cuts each block's run into stacks of S.
+// One block of 1024 threads; dynamic shared memory 8 T bytes.
+__global__ void __launch_bounds__(1024) tc_stack_build(TcGather g, int nbeta, int S, int *out) {
+    extern __shared__ unsigned long long keys[];
+    __shared__ int scan[1024];
+    const int T = 1 << nbeta, nt = blockDim.x, tid = threadIdx.x;
+    for (int b = tid; b < T; b += nt)
+        keys[b] = ((unsigned long long)(unsigned)tc_gather_sel(g, g.closed[b]) << 32) | (unsigned)b;
+    for (int i = tid; i < T * (S + 1); i += nt) out[1 + i] = -1;
+    __syncthreads();
+    for (int k = 2; k <= T; k <<= 1) {
+        for (int j = k >> 1; j > 0; j >>= 1) {
+            for (int i = tid; i < T; i += nt) {
+                const int l = i ^ j;
+                if (l > i) {
+                    const unsigned long long a = keys[i], c = keys[l];
+                    if ((a > c) == ((i & k) == 0)) {
+                        keys[i] = c;
+                        keys[l] = a;
+                    }
+                }
+            }
+            __syncthreads();
+        }
+    }
+    // thread tid walks positions [lo, hi) of the sorted list; a run starts where the block
+    // changes, and a stack at every S-th position of a run
+    const int E = (T + nt - 1) / nt, lo = min(T, tid * E), hi = min(T, lo + E);
+    auto head = [&](int i) { return i == 0 || (keys[i] >> 32) != (keys[i - 1] >> 32); };
+    int last = -1;
+    for (int i = lo; i < hi; i++)
+        if (head(i)) last = i;
+    scan[tid] = last;  // inclusive max-scan: the last run start at or before the chunk's end
+    __syncthreads();
+    for (int d = 1; d < nt; d <<= 1) {
+        const int v = tid >= d ? scan[tid - d] : -1;
+        __syncthreads();
+        scan[tid] = max(scan[tid], v);
+        __syncthreads();
+    }
+    const int run0 = tid > 0 ? scan[tid - 1] : -1;
+    __syncthreads();
+    int starts = 0;
+    last = run0;
+    for (int i = lo; i < hi; i++) {
+        if (head(i)) last = i;
+        starts += (i - last) % S == 0;
+    }
+    scan[tid] = starts;  // inclusive sum-scan of the stack starts
+    __syncthreads();
+    for (int d = 1; d < nt; d <<= 1) {
+        const int v = tid >= d ? scan[tid - d] : 0;
+        __syncthreads();
+        scan[tid] += v;
+        __syncthreads();
+    }
+    int id = scan[tid] - starts - 1;  // stacks started before this chunk, minus one
+    last = run0;
+    for (int i = lo; i < hi; i++) {
+        if (head(i)) last = i;
+        const int pos = (i - last) % S;
+        int *e = out + 1 + (id + (pos == 0)) * (S + 1);
+        if (pos == 0) {
+            id++;
+            e[0] = (int)(keys[i] >> 32);
+        }
+        e[1 + pos] = (int)(keys[i] & 0xffffffffu);
+    }
+    if (tid == nt - 1) out[0] = scan[tid];
 }
 
 struct TcParams {
@@ -72,6 +167,8 @@ struct TcParams {
     long long stall_cycles;  // > 0 (tests only): the MMA warp first waits this long on a
                              // barrier nothing arrives on, so the bounded-wait path runs
     TcGather ga, gb;         // operands read in place through their batch gather
+    const int *stack;        // non-null: stacked tiles over this stack list (tc_stack_build)
+    int stack_S;             // batches per stacked tile (BN >> ln)
     int8_t pos_bat[kMaxBits], pos_m[kMaxBits], pos_n[kMaxBits];
 };
 
@@ -83,6 +180,24 @@ struct TcTile {
     int tn_i, tm_i, bat;
     long long v;
 };
+
+// Stacked tile t: m tiles fastest, then stacks (sorted by block: the stacks of one block
+// run back to back and share its panels in L2), then the non-beta batch bits, then version.
+struct TcStackTile {
+    int tm_i, stack, nonb;
+    long long v;
+};
+__device__ __forceinline__ TcStackTile tc_stack_tile(long long t, long long tiles_m, int n_stacks, int nnb) {
+    TcStackTile r;
+    r.tm_i = (int)(t % tiles_m);
+    long long q = t / tiles_m;
+    r.stack = (int)(q % n_stacks);
+    q /= n_stacks;
+    r.nonb = (int)(q & ((1LL << nnb) - 1));
+    r.v = q >> nnb;
+    return r;
+}
+
 __device__ __forceinline__ TcTile tc_tile(long long t, long long tiles_m, long long tiles_n, int lbat, int group_m) {
     const long long per_bat = tiles_m * tiles_n;
     const long long bv = t / per_bat, tl = t - bv * per_bat;
@@ -255,6 +370,7 @@ __global__ void __launch_bounds__(kTcThreads, 1)
     uint64_t *never = acc_empty + 2;      // test stall: initialised, never arrived on
     uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(never + 1);
     volatile int *abort_flag = reinterpret_cast<volatile int *>(tmem_slot + 1);
+    volatile int *slot_cols = abort_flag + 1;  // [STAGES]: a stacked tile's MMA width
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     // Tiles: (n tile, m tile, batch, version) without folding.  With folding the rows
@@ -267,7 +383,11 @@ __global__ void __launch_bounds__(kTcThreads, 1)
     const long long tiles_n = p.fold == 2 ? (p.nver + vn - 1) / vn : (1LL << (p.ln - ltn));
     const long long tiles_v = p.fold ? 1 : p.nver;
     const long long per_bat = tiles_m * tiles_n;
-    const long long ntiles = per_bat * (1LL << p.lbat) * tiles_v;
+    // stacked: (version, non-beta bits, stack, m tile); the host guarantees one n tile
+    const bool stk = p.stack != nullptr;
+    const int S = p.stack_S, n_stacks = stk ? p.stack[0] : 0;
+    const long long ntiles =
+        stk ? tiles_m * n_stacks * (1LL << p.ga.nnb) * tiles_v : per_bat * (1LL << p.lbat) * tiles_v;
     const int BAT = 1 << p.lbat;
     const int K = 1 << p.lk;
     const int nkb = (K + kTcBK - 1) / kTcBK;
@@ -304,7 +424,7 @@ __global__ void __launch_bounds__(kTcThreads, 1)
         if (lane == 0) {
             long long slot = 0;
             bool ok = true;
-            for (long long t = blockIdx.x; t < ntiles && ok; t += gridDim.x) {
+            for (long long t = blockIdx.x; t < ntiles && ok && !stk; t += gridDim.x) {
                 const TcTile tt = tc_tile(t, tiles_m, tiles_n, p.lbat, p.group_m);
                 const int tn_i = tt.tn_i, tm_i = tt.tm_i, bat = tt.bat, v = (int)tt.v;
                 const int ia = p.fold == 1 ? p.vidx[0] + tm_i * vm : p.vidx[p.fold == 2 ? 0 : v];
@@ -333,6 +453,66 @@ __global__ void __launch_bounds__(kTcThreads, 1)
                     issued = slot + 1;
                 }
             }
+            // stacked tiles: one A panel, then one (1 << ln)-row B box per batch of the stack
+            // (its valid slots come first); the next tile's stack entry is loaded while this
+            // tile's slots are issued, and every slot tells the MMA thread its width
+            auto entry = [&](long long t) {
+                return p.stack + 1 + (long long)tc_stack_tile(t, tiles_m, n_stacks, p.ga.nnb).stack * (S + 1);
+            };
+            int nx[kTcMaxStack + 1];
+            if (stk && blockIdx.x < ntiles) {
+                const int *sb = entry(blockIdx.x);
+#pragma unroll
+                for (int j = 0; j <= kTcMaxStack; j++) nx[j] = j <= S ? sb[j] : -1;
+            }
+            for (long long t = blockIdx.x; t < ntiles && ok && stk; t += gridDim.x) {
+                int e[kTcMaxStack + 1];
+#pragma unroll
+                for (int j = 0; j <= kTcMaxStack; j++) e[j] = nx[j];
+                if (t + gridDim.x < ntiles) {
+                    const int *sb = entry(t + gridDim.x);
+#pragma unroll
+                    for (int j = 0; j <= kTcMaxStack; j++) nx[j] = j <= S ? sb[j] : -1;
+                }
+                const TcStackTile tt = tc_stack_tile(t, tiles_m, n_stacks, p.ga.nnb);
+                const int pza = tt.nonb | (e[0] << p.ga.nnb);  // the block the stack selects
+                const int sza = 1 << (p.ga.nnb + p.ga.nq);
+                int pzb[kTcMaxStack], nbox = 0;
+#pragma unroll
+                for (int j = 0; j < kTcMaxStack; j++) {
+                    pzb[j] = -1;
+                    if (e[1 + j] >= 0) {
+                        const int bat = tc_compose_bat(p.ga, p.lbat, tt.nonb, e[1 + j]);
+                        pzb[j] = p.gb.closed ? tc_gather_plane(p.gb, p.lbat, bat) : bat;
+                        nbox++;
+                    }
+                }
+                const int ia = p.vidx[tt.v], ib = p.vidx[p.nver + tt.v];
+                const int rowA = tt.tm_i * kTcBM;
+                const int szb = p.gb.closed ? 1 << (p.gb.nnb + p.gb.nq) : BAT;
+                const int bbox = (kTcBK * 2) << p.ln;  // bytes per B box
+                for (int kb = 0; kb < nkb; kb++, slot++) {
+                    const int s = (int)(slot % STAGES);
+                    if (slot >= STAGES &&
+                        !mbar_wait(smem_u32(&empty[s]), (uint32_t)(((slot / STAGES) & 1) ^ 1), abort_flag, kLimit)) {
+                        ok = false;
+                        break;
+                    }
+                    slot_cols[s] = nbox << p.ln;  // published by the arrive below
+                    const uint32_t fb = smem_u32(&full[s]);
+                    mbar_expect_tx(fb, (uint32_t)(4 * L::kAPlane + 4 * nbox * bbox));
+                    unsigned char *st = smem + s * L::kStage;
+                    for (int pl = 0; pl < 4; pl++) {
+                        tma_load_4d(smem_u32(st + pl * L::kAPlane), &tmA, kb * kTcBK, rowA, pl * sza + pza, ia, fb);
+#pragma unroll
+                        for (int j = 0; j < kTcMaxStack; j++)
+                            if (pzb[j] >= 0)
+                                tma_load_4d(smem_u32(st + 4 * L::kAPlane + pl * L::kBPlane + j * bbox), &tmB,
+                                            kb * kTcBK, 0, pl * szb + pzb[j], ib, fb);
+                    }
+                    issued = slot + 1;
+                }
+            }
         }
     } else if (warp == 1) {
         if (lane == 0) {
@@ -342,7 +522,7 @@ __global__ void __launch_bounds__(kTcThreads, 1)
             const int8_t pb[12] = {0, 1, 0, 2, 3, 2, 2, 3, 2, 0, 1, 0};
             const int8_t acc[12] = {0, 0, 0, 0, 0, 0, 1, 1, 1, 1, 1, 1};
             const int8_t neg[12] = {0, 0, 0, 1, 1, 1, 0, 0, 0, 0, 0, 0};
-            const uint32_t id_pos = idesc_f16(BN, p.in_fp16, false), id_neg = idesc_f16(BN, p.in_fp16, true);
+            uint32_t id_pos = idesc_f16(BN, p.in_fp16, false), id_neg = idesc_f16(BN, p.in_fp16, true);
             long long slot = 0;
             int it = 0, last_b = -1;
             uint32_t last_par = 0;
@@ -365,6 +545,13 @@ __global__ void __launch_bounds__(kTcThreads, 1)
                         break;
                     }
                     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+                    if (stk && kb == 0) {
+                        // a stacked tile multiplies only its valid batches' columns (the
+                        // valid slots come first): N = count << ln, a multiple of 32
+                        const int n = slot_cols[s];
+                        id_pos = idesc_f16(n, p.in_fp16, false);
+                        id_neg = idesc_f16(n, p.in_fp16, true);
+                    }
                     const uint32_t st = smem_u32(smem + s * L::kStage);
 #pragma unroll
                     for (int kk = 0; kk < kTcBK / 16; kk++) {
@@ -402,7 +589,20 @@ __global__ void __launch_bounds__(kTcThreads, 1)
             const int b = it & 1;
             if (!mbar_wait(smem_u32(&acc_full[b]), (uint32_t)((it >> 1) & 1), abort_flag, kLimit)) break;
             asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-            const TcTile tt = tc_tile(t, tiles_m, tiles_n, p.lbat, p.group_m);
+            TcTile tt;
+            const int *sb = nullptr;  // stacked: this tile's batch indices
+            int nonb = 0;
+            if (stk) {
+                const TcStackTile ts = tc_stack_tile(t, tiles_m, n_stacks, p.ga.nnb);
+                tt.tn_i = 0;
+                tt.tm_i = ts.tm_i;
+                tt.v = ts.v;
+                tt.bat = 0;
+                sb = p.stack + 2 + (long long)ts.stack * (S + 1);  // the stack's batch indices
+                nonb = ts.nonb;
+            } else {
+                tt = tc_tile(t, tiles_m, tiles_n, p.lbat, p.group_m);
+            }
             const int tn_i = tt.tn_i, tm_i = tt.tm_i, bat = tt.bat;
             long long vrow = tt.v;  // this row's version
             long long m;
@@ -413,13 +613,32 @@ __global__ void __launch_bounds__(kTcThreads, 1)
                 m = (long long)tm_i * kTcBM + row;
             }
             const bool row_ok = m < M && vrow < p.nver;
-            const long long cbase = scatter_bits(bat, p.pos_bat, p.lbat) + (row_ok ? scatter_bits(m, p.pos_m, p.lm) : 0);
+            const long long mbase = row_ok ? scatter_bits(m, p.pos_m, p.lm) : 0;
+            long long cbase = scatter_bits(bat, p.pos_bat, p.lbat) + mbase;
             const uint32_t lane_addr = tmem + ((uint32_t)(32 * quarter) << 16) + (uint32_t)(b * 2 * BN);
             for (int c0 = c_begin; c0 < c_end; c0 += 16) {
                 float re[16], im[16];
+                // stacked: columns [j N, (j + 1) N) belong to the stack's batch j (N >= 32);
+                // an empty slot's columns were not computed (warp-uniform skip)
+                const int be = stk ? sb[c0 >> p.ln] : 0;
+                if (be < 0) continue;
                 __syncwarp();
                 tmem_ld16x2(lane_addr + c0, lane_addr + BN + c0, re, im);
                 if (!row_ok) continue;
+                if (stk) {
+                    const long long cb = scatter_bits(tc_compose_bat(p.ga, p.lbat, nonb, be), p.pos_bat, p.lbat) + mbase;
+                    const long long nb = c0 & (N - 1);
+                    void *Cv = static_cast<char *>(p.C) + 8 * vrow * p.c_plane;
+                    const long long hi = cb + scatter_bits(nb >> 4, p.pos_n + 4, p.ln - 4);
+#pragma unroll
+                    for (int j = 0; j < 16; j++) {
+                        const long long off = hi + lo[j];
+                        const float2 x = make_float2(re[j] * p.out_scale, im[j] * p.out_scale);
+                        if (p.out_fmt == OUT_C64) static_cast<float2 *>(Cv)[off] = x;
+                        else store_split(Cv, p.c_plane, off, x, p.out_fmt == OUT_SPLIT_FP16);
+                    }
+                    continue;
+                }
                 if (p.fold == 2) {
                     // columns: version (c0 + j) / N of this tile, n = (c0 + j) % N
 #pragma unroll

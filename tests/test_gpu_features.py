@@ -21,6 +21,7 @@ from paper_2112_15083_gb300 import circuits as cg
 pytestmark = pytest.mark.gpu
 
 TOL_C64 = 1e-4
+TC_IDS = (9128, 9064, 9032, 19128, 19064)  # tensor-core kernels (trace ids)
 
 
 @pytest.fixture(scope="module", autouse=True)
@@ -221,7 +222,7 @@ def long_k_dispatch(tr):
     n = 0
     for s in tr:
         if s["launches"] and min(s["nm"], s["nn"]) <= 3 and max(s["nm"], s["nn"]) <= 5 and s["nk"] >= 10 \
-                and s["kernel"] not in (9128, 9064, 9032):
+                and s["kernel"] not in TC_IDS:
             assert s["kernel"] == 5, s
             n += 1
     return n
@@ -325,8 +326,39 @@ def test_tensor_core_steps_read_gathered_operands_in_place(seed, n_sliced):
     amps = plan.contract(slices, cb)
     tr = plan.trace_read()
     plan.trace(False)
-    tc_in_place = [s for s in tr if s["kernel"] in (9128, 9064, 9032) and s["in_place"] and s["launches"]]
+    tc_in_place = [s for s in tr if s["kernel"] in TC_IDS and s["in_place"] and s["launches"]]
     assert tc_in_place, "no tensor-core step read a gathered operand in place"
     assert all(s["gathers"] == 0 for s in tc_in_place)
     ref = oracle.batch_amplitudes(oracle.simulate(circ), 24, openq, cb)
     assert np.linalg.norm(amps - ref) / np.linalg.norm(ref) <= 1e-3
+
+
+# ------------------------------------------------------------------ stacked tensor-core tiles
+
+def test_stacked_tensor_core_tiles_match_the_oracle():
+    """4x6 grid, 14 cycles, 1024 batches (+5 in a ragged second group): the in-place batch
+    step (10,8,5,7) runs, in turn, every tensor-core variant it has (autotune = k cycles the
+    variants by step), among them the stacked tiles that put 2 or 4 batches reading the same
+    stored block side by side in one 128- or 64-column tile; every amplitude against the
+    oracle's state vector for each."""
+    P = pkg()
+    circ = cg.sycamore_grid(4, 6, 14, seed=0)
+    openq = cg.default_open_qubits(4, 6, 6)
+    C = P.circuit_load(circ.serialize())
+    cb = cg.random_closed_bits(1024 + 5, 18, seed=7)
+    ref = oracle.batch_amplitudes(oracle.simulate(circ), 24, openq, cb)
+    slices = np.arange(1, dtype=np.uint64)
+    seen = set()
+    for k in range(2, 7):
+        plan = P.plan(C, openq, log2_batches=10, order_trials=16, precision=P.tn.PREC_BF16X2, autotune=k)
+        plan.trace(True)
+        amps = plan.contract(slices, cb)
+        tr = plan.trace_read()
+        plan.trace(False)
+        rel = float(np.linalg.norm(amps - ref) / np.linalg.norm(ref))
+        kinds = sorted({s["kernel"] for s in tr if s["kernel"] in TC_IDS and s["in_place"] and s["launches"]})
+        print("autotune %d: in-place tensor-core kernels %s, relative L2 %.2e" % (k, kinds, rel))
+        assert rel <= 1e-3, (k, kinds, rel)
+        seen.update(kinds)
+        del plan
+    assert {19128, 19064} <= seen, "stacked variants never ran: %s" % sorted(seen)
