@@ -91,6 +91,7 @@ struct GemmParams {
     // copy (null: not gathered); closed_bits are the group's batch patterns
     const GatherDesc *gA, *gB;
     const uint64_t *closed_bits;
+    int *err;                 // long-K kernel: set to 1 if a bounded wait gives up
     int8_t pos_bat[kMaxBits], pos_m[kMaxBits], pos_n[kMaxBits];
 };
 
@@ -321,86 +322,203 @@ __global__ void __launch_bounds__(32 * kRowWarps) cgemm_rowstage(GemmParams p) {
     }
 }
 
+// mbarrier primitives (shared-memory barriers with transaction counts).
+__device__ __forceinline__ uint32_t smem_u32(const void *p) {
+    return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+
+__device__ __forceinline__ void mbar_init(uint32_t bar, uint32_t count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(count) : "memory");
+}
+
+__device__ __forceinline__ void mbar_expect_tx(uint32_t bar, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes) : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try(uint32_t bar, uint32_t parity) {
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(bar), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+
+// Bounded wait: gives up after ~limit cycles or when another role has aborted.
+__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, volatile int *abort_flag,
+                                          long long limit) {
+    const long long t0 = clock64();
+    for (int it = 0;; ++it) {
+        if (mbar_try(bar, parity)) return true;
+        if ((it & 63) == 63) {
+            if (*abort_flag) return false;
+            if (clock64() - t0 > limit) {
+                *abort_flag = 1;
+                return false;
+            }
+        }
+    }
+}
+
+// Bounded wait that ignores the abort flag (used to drain work already issued).
+__device__ __forceinline__ bool mbar_drain(uint32_t bar, uint32_t parity, long long limit) {
+    const long long t0 = clock64();
+    for (;;) {
+        if (mbar_try(bar, parity)) return true;
+        if (clock64() - t0 > limit) return false;
+    }
+}
+
+// Bulk copy of `bytes` (a multiple of 16, both addresses 16-byte aligned) global -> shared,
+// completing on mbarrier `bar` as transaction bytes.
+__device__ __forceinline__ void bulk_load(void *dst, const void *src, uint32_t bytes, uint32_t bar) {
+    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                     smem_u32(dst)),
+                 "l"(src), "r"(bytes), "r"(bar)
+                 : "memory");
+}
+
 // Batched products with at most 64 rows and 8 columns and a long K (K >= 1024, complex64
-// operands).  A block of W warps takes W MW rows of one (version, batch) at a time (a
+// operands).  A block of W warps takes R = W MW rows of one (version, batch) at a time (a
 // batch with more rows is split into row blocks); each warp owns MW rows of A and every
-// column.  Per 64-element K block (kSkinnyU blocks
-// per stage), lane l reads
-// elements 2 l and 2 l + 1 of its A rows (16-byte loads, 512 contiguous bytes per row and
-// warp, evict-first) and of the B rows its warp stages, and the block shares the staged B
-// block through double-buffered shared memory (one barrier per block), so each operand
-// element leaves DRAM once.  Each lane accumulates in ascending k and the warp adds its 32
-// lane sums by a fixed xor butterfly.  Gathered operands are read in place, one decode per
-// row and warp.  The lane split of K rounds differently from the kernels that accumulate
-// each output over k in one thread, so it is the only kernel the engine runs for these
-// shapes.
-constexpr int kSkinnyU = 2;  // 64-element K blocks per stage (loads in flight per lane)
+// column.  The block's work is one sequence of stages, each a (unit, K block of 64 U
+// elements) pair, streamed through a ring of ST shared-memory stages by the bulk-copy
+// engine (one contiguous copy per row and stage, issued ST - 1 stages ahead across unit
+// boundaries and completing on the stage's mbarrier), so loads stay in flight while the
+// FMAs run.  In a stage lane l reads elements 2 l and 2 l + 1 of each 64-element block of
+// its warp's A rows; the stage's B rows are shared by the block.  Every wait is bounded:
+// on timeout the block sets *err, lets its copies in flight land (bounded) and returns.
+// Each lane accumulates in ascending k and the warp adds its 32 lane sums by a fixed xor
+// butterfly.  Gathered operands are read in place, one decode per row and warp.  The lane
+// split of K rounds differently from the kernels that accumulate each output over k in
+// one thread, so it is the only kernel the engine runs for these shapes.
+constexpr int kSkinnyU = 2;   // 64-element K blocks per stage
+constexpr int kSkinnyST = 4;  // ring stages
+template <int W, int MW, int N>
+constexpr int skinny_stage_bytes() {
+    return (W * MW + N) * kSkinnyU * 32 * 16;
+}
 template <int W, int MW, int N>
 __global__ void __launch_bounds__(32 * W) cgemm_skinny(GemmParams p) {
-    __shared__ float4 sB[2][kSkinnyU][N][32];
+    extern __shared__ float4 skinny_ring[];
+    __shared__ __align__(8) uint64_t full[kSkinnyST];  // per stage: W arrivals + the bytes
+    __shared__ int abort_flag;
+    constexpr int R = W * MW, U = kSkinnyU, ST = kSkinnyST, NB = (N + W - 1) / W;
+    const long long kLimit = 4000000000LL;
+    constexpr int kStage = (R + N) * U * 32;  // float4 per stage
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    // a block covers W MW rows of one batch: row blocks of the batch, then batches
-    const int row_blocks = (1 << p.lm) / (W * MW);
+    const int row_blocks = (1 << p.lm) / R;
     const long long units = (p.nver << p.lbat) * row_blocks;
-    const int K = 1 << p.lk;
-    for (long long u = blockIdx.x; u < units; u += gridDim.x) {
+    const int nk = (1 << p.lk) / (64 * U);  // stages per unit
+    const long long mine = units > blockIdx.x ? (units - 1 - blockIdx.x) / gridDim.x + 1 : 0;
+    const long long total = mine * nk;
+    // copy side: the row pointers of the unit being issued
+    const float2 *a[MW], *b[NB];
+    long long a_unit = -1;
+    auto unit_of = [&](long long ul, long long &bat, long long &v, int &row0) {
+        const long long u = blockIdx.x + ul * gridDim.x;
         const int rb = (int)(u % row_blocks);
         const long long bv = u / row_blocks;
-        const long long bat = bv & ((1LL << p.lbat) - 1), v = bv >> p.lbat;
-        const int row0 = rb * W * MW + warp * MW;  // this warp's first row of A
-        const float2 *a[MW], *b[(N + W - 1) / W];
+        bat = bv & ((1LL << p.lbat) - 1);
+        v = bv >> p.lbat;
+        row0 = rb * R + warp * MW;  // this warp's first row of A
+    };
+    // copies of stage (unit ul, K block kb) into ring slot `slot`
+    auto issue = [&](long long ul, int kb, int slot) {
+        if (ul != a_unit) {
+            long long bat, v;
+            int row0;
+            unit_of(ul, bat, v, row0);
 #pragma unroll
-        for (int i = 0; i < MW; i++) {
-            const long long e = ((bat << p.lm) | (long long)(row0 + i)) << p.lk;
-            a[i] = p.gA ? reinterpret_cast<const float2 *>(p.gA->src) +
-                              gather_src_warp(*p.gA, e, p.gA->pos_beta[p.gA->lb - 1], p.closed_bits)
-                        : static_cast<const float2 *>(p.ptrA[v]) + e;
-        }
-        // B rows staged by this warp: n = warp, warp + W, ...
-#pragma unroll
-        for (int r = 0; r < (N + W - 1) / W; r++) {
-            const int n = warp + r * W;
-            const long long e = (bat << (p.ln + p.lk)) | ((long long)(n < N ? n : 0) << p.lk);
-            b[r] = p.gB ? reinterpret_cast<const float2 *>(p.gB->src) +
-                              gather_src_warp(*p.gB, e, p.gB->pos_beta[p.gB->lb - 1], p.closed_bits)
-                        : static_cast<const float2 *>(p.ptrB[v]) + e;
-        }
-        float2 acc[MW][N];
-#pragma unroll
-        for (int i = 0; i < MW; i++)
-#pragma unroll
-            for (int n = 0; n < N; n++) acc[i][n] = make_float2(0.f, 0.f);
-        int buf = 0;
-        for (int k0 = 2 * lane; k0 < K; k0 += 64 * kSkinnyU, buf ^= 1) {
-            float4 x[kSkinnyU][MW], y[kSkinnyU][(N + W - 1) / W];
-#pragma unroll
-            for (int u = 0; u < kSkinnyU; u++) {
-#pragma unroll
-                for (int i = 0; i < MW; i++) x[u][i] = __ldcs(reinterpret_cast<const float4 *>(a[i] + k0 + 64 * u));
-#pragma unroll
-                for (int r = 0; r < (N + W - 1) / W; r++)
-                    if (warp + r * W < N) y[u][r] = __ldcs(reinterpret_cast<const float4 *>(b[r] + k0 + 64 * u));
+            for (int i = 0; i < MW; i++) {
+                const long long e = ((bat << p.lm) | (long long)(row0 + i)) << p.lk;
+                a[i] = p.gA ? reinterpret_cast<const float2 *>(p.gA->src) +
+                                  gather_src_warp(*p.gA, e, p.gA->pos_beta[p.gA->lb - 1], p.closed_bits)
+                            : static_cast<const float2 *>(p.ptrA[v]) + e;
             }
 #pragma unroll
-            for (int u = 0; u < kSkinnyU; u++)
-#pragma unroll
-                for (int r = 0; r < (N + W - 1) / W; r++)
-                    if (warp + r * W < N) sB[buf][u][warp + r * W][lane] = y[u][r];
-            // with two buffers one barrier per stage suffices: a warp writes a buffer again
-            // only after every warp has passed the barrier that follows its last reads of it
-            __syncthreads();
-#pragma unroll
-            for (int u = 0; u < kSkinnyU; u++)
-#pragma unroll
-                for (int n = 0; n < N; n++) {
-                    const float4 yb = sB[buf][u][n][lane];
-#pragma unroll
-                    for (int i = 0; i < MW; i++) {
-                        acc[i][n] = cfma(make_float2(x[u][i].x, x[u][i].y), make_float2(yb.x, yb.y), acc[i][n]);
-                        acc[i][n] = cfma(make_float2(x[u][i].z, x[u][i].w), make_float2(yb.z, yb.w), acc[i][n]);
-                    }
-                }
+            for (int r = 0; r < NB; r++) {
+                const int n = warp + r * W;
+                const long long e = (bat << (p.ln + p.lk)) | ((long long)(n < N ? n : 0) << p.lk);
+                b[r] = p.gB ? reinterpret_cast<const float2 *>(p.gB->src) +
+                                  gather_src_warp(*p.gB, e, p.gB->pos_beta[p.gB->lb - 1], p.closed_bits)
+                            : static_cast<const float2 *>(p.ptrB[v]) + e;
+            }
+            a_unit = ul;
         }
+        // lane 0 of each warp: one arrival with the warp's bytes, then its rows' copies
+        if (lane == 0) {
+            float4 *st = skinny_ring + slot * kStage;
+            const uint32_t bar = smem_u32(&full[slot]);
+            int rows = MW;
+#pragma unroll
+            for (int r = 0; r < NB; r++) rows += warp + r * W < N;
+            mbar_expect_tx(bar, (uint32_t)(rows * U * 512));
+            const int k0 = kb * 64 * U;
+#pragma unroll
+            for (int i = 0; i < MW; i++) bulk_load(&st[(warp * MW + i) * U * 32], a[i] + k0, U * 512, bar);
+#pragma unroll
+            for (int r = 0; r < NB; r++)
+                if (warp + r * W < N) bulk_load(&st[(R + warp + r * W) * U * 32], b[r] + k0, U * 512, bar);
+        }
+    };
+    float2 acc[MW][N];
+#pragma unroll
+    for (int i = 0; i < MW; i++)
+#pragma unroll
+        for (int n = 0; n < N; n++) acc[i][n] = make_float2(0.f, 0.f);
+    if (threadIdx.x == 0) {
+        for (int i = 0; i < ST; i++) mbar_init(smem_u32(&full[i]), W);
+        abort_flag = 0;
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    }
+    __syncthreads();
+    // stage counters advance by one (no divisions in the loop): issue side (iul, ikb, islot)
+    // runs ST - 1 stages ahead of the compute side (ul, kb, slot, parity)
+    long long issued = 0, iul = 0;
+    int ikb = 0, islot = 0;
+    auto advance_issue = [&]() {
+        issued++;
+        if (++ikb == nk) { ikb = 0; iul++; }
+        if (++islot == ST) islot = 0;
+    };
+    for (; issued < ST - 1 && issued < total;) {
+        issue(iul, ikb, islot);
+        advance_issue();
+    }
+    long long g = 0, ul = 0;
+    int kb = 0, slot = 0;
+    uint32_t parity = 0;
+    for (; g < total; g++) {
+        __syncthreads();  // every warp is done with the slot the next issue overwrites
+        if (issued < total) {
+            issue(iul, ikb, islot);
+            advance_issue();
+        }
+        mbar_wait(smem_u32(&full[slot]), parity, &abort_flag, kLimit);
+        __syncthreads();  // a timeout anywhere ends the block's loop in every thread
+        if (abort_flag) break;
+        const float4 *st = skinny_ring + slot * kStage;
+        if (++slot == ST) { slot = 0; parity ^= 1u; }
+#pragma unroll
+        for (int u = 0; u < U; u++)
+#pragma unroll
+            for (int n = 0; n < N; n++) {
+                const float4 yb = st[((R + n) * U + u) * 32 + lane];
+#pragma unroll
+                for (int i = 0; i < MW; i++) {
+                    const float4 x = st[((warp * MW + i) * U + u) * 32 + lane];
+                    acc[i][n] = cfma(make_float2(x.x, x.y), make_float2(yb.x, yb.y), acc[i][n]);
+                    acc[i][n] = cfma(make_float2(x.z, x.w), make_float2(yb.z, yb.w), acc[i][n]);
+                }
+            }
+        if (++kb < nk) continue;
+        kb = 0;
+        // the unit's last stage: reduce, store, start the next unit from zero
 #pragma unroll
         for (int off = 16; off > 0; off >>= 1)
 #pragma unroll
@@ -410,17 +528,27 @@ __global__ void __launch_bounds__(32 * W) cgemm_skinny(GemmParams p) {
                     acc[i][n].x += __shfl_xor_sync(0xffffffffu, acc[i][n].x, off);
                     acc[i][n].y += __shfl_xor_sync(0xffffffffu, acc[i][n].y, off);
                 }
+        long long bat, v;
+        int row0;
+        unit_of(ul++, bat, v, row0);
         // every lane holds the totals: lane i N + n stores output (row MW warp + i, column n)
         const long long cb = scatter_bits(bat, p.pos_bat, p.lbat);
 #pragma unroll
         for (int i = 0; i < MW; i++)
 #pragma unroll
-            for (int n = 0; n < N; n++)
+            for (int n = 0; n < N; n++) {
                 if (lane == i * N + n)
                     store_c(p, v, cb + scatter_bits(row0 + i, p.pos_m, p.lm) + scatter_bits(n, p.pos_n, p.ln),
                             acc[i][n]);
-        __syncthreads();  // the staging buffers are reused by the block's next batch
+                acc[i][n] = make_float2(0.f, 0.f);
+            }
     }
+    if (abort_flag && threadIdx.x == 0) {
+        atomicExch(p.err, 1);
+        // let the copies already issued land before the shared memory is released
+        for (long long q = g; q < issued; q++) mbar_drain(smem_u32(&full[q % ST]), (uint32_t)((q / ST) & 1), kLimit);
+    }
+    __syncthreads();
 }
 
 // Batched small products (M, N <= 64, K <= 64): a block stages the operands of 2^lg
