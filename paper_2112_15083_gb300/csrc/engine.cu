@@ -711,7 +711,12 @@ std::vector<int> step_variants(const CNet &cn, size_t si) {
 int default_variant(const CNet &cn, size_t si) {
     const Step &s = cn.steps[si];
     if (skinny_fits(cn, s)) return kVarSkinny;
-    if (!cn.use_tc.empty() && cn.use_tc[si]) return s.nn <= 5 ? kVarTc32 : kVarTc128;
+    if (!cn.use_tc.empty() && cn.use_tc[si]) {
+        // stacked tiles where they fit and the step is large enough to amortise building
+        // the stack list (tens of microseconds)
+        if (stack_fits(cn, si, 128) && s.flops_per_version * (double)cn.cp.nver[s.c] >= 1e9) return kVarTcS128;
+        return s.nn <= 5 ? kVarTc32 : kVarTc128;
+    }
     if (std::min(s.nm, s.nn) == 6 && std::max(s.nm, s.nn) == 6 && small_fits(s, (size_t)cn.elem)) return kVarSmall;
     if (std::min(s.nm, s.nn) <= 5 && s.nk <= 6) return kVarRow;
     // large products: 128 x 32 tiles (the autotuner's choice on GB300 for complex64)
