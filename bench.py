@@ -43,7 +43,10 @@ sys.path.insert(0, ROOT)
 JOB_WORKLOADS = {
     # 40 qubits, 16 cycles, 1/64 of the slices, 100k samples (the largest single-GPU case)
     "grid5x8_m16": dict(rows=5, cols=8, cycles=16, seed=0, n_open=6, log2_batches=12, f=1.0 / 64, N=100000,
-                        alpha=2.0, caps=(30, 29, 28, 27, 26), slice_bytes_max=140e9, budget=150e9, trials=256),
+                        alpha=2.0, caps=(30, 29, 28, 27, 26), slice_bytes_max=140e9, budget=150e9, trials=256,
+                        # per-slice annealing of the size-capped tree: 378.8 against 341.4 samples/s
+                        # unannealed (8000 moves: 344.6, the model misprices small-K FFMA tiles)
+                        anneal=2000),
 }
 # batch-group workloads (one step = one batch group of a sampling job over one slice set)
 WORKLOADS = {
@@ -81,8 +84,9 @@ def parse():
     ap.add_argument("--chunk", type=int, default=8, help="job workloads: at most this many slices per chunk (a power of two)")
     ap.add_argument("--log2-batches", type=int, default=None, help="batches per group = 2^this (default: the workload's)")
     ap.add_argument("--autotune", type=int, default=1, help="kernel autotuning (1) or the fixed shape rules (0)")
-    ap.add_argument("--anneal", type=int, default=0,
-                    help="order search: simulated-annealing moves on the winning tree (tn_plan_opts.anneal_iters)")
+    ap.add_argument("--anneal", type=int, default=None,
+                    help="simulated-annealing moves on the plan's tree (tn_plan_opts.anneal_iters); default: the "
+                         "workload's (2000 for the 40-qubit job, where it is annealed per slice under the size cap)")
     ap.add_argument("--fuse-root", type=int, default=0,
                     help="1: run a row-kernel root step fused with the FP64 slice sum (tn_plan_opts.fuse_root_sum)")
     ap.add_argument("--serve", action="store_true", help="serving run (Poisson request stream) instead of the step bench")
@@ -91,6 +95,8 @@ def parse():
     a = ap.parse_args()
     if a.fidelity is None:
         a.fidelity = JOB_WORKLOADS[a.workload]["f"] if a.workload in JOB_WORKLOADS else 1.0
+    if a.anneal is None:
+        a.anneal = JOB_WORKLOADS[a.workload].get("anneal", 0) if a.workload in JOB_WORKLOADS else 0
     return a
 
 

@@ -1568,7 +1568,14 @@ int tn_plan_build_host(const Merged &mg, const tn_plan_opts &o, const int32_t *o
         int rc = tn_build_amp_network(mg, {}, open, o.log2_batches, net0, closed);
         if (rc) return rc;
         tn_cost_settings(net0, o);
-        if (o.max_log2_tensor > 0) net0.mem_limit_elems = 0;
+        if (o.max_log2_tensor > 0) {
+            net0.mem_limit_elems = 0;
+            // no annealing of the unsliced tree here: it lowers the unsliced cost with wider
+            // tensors, which the size-targeted slicing then pays for with more sliced legs
+            // (on the 40-qubit job 24 instead of 18 legs and 8.5x the work over all slices);
+            // the sliced tree is annealed per slice under the cap below
+            net0.anneal_iters = 0;
+        }
         TreeCost tc0;
         tn_search_tree(net0, o.order_seed, o.order_trials > 0 ? o.order_trials : 64, t0, tc0);
         std::vector<int> picked = o.max_log2_tensor > 0 ? tn_width_slice(net0, t0, o.max_log2_tensor, 62)

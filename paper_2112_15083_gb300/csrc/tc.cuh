@@ -538,8 +538,8 @@ __global__ void __launch_bounds__(kTcThreads, 1)
         int it = 0;
         for (long long t = blockIdx.x; t < ntiles; t += gridDim.x, it++) {
             const int b = it & 1;
-            if (!mbar_wait(smem_u32(&acc_full[b]), (uint32_t)((it >> 1) & 1), abort_flag, kLimit)) break;
-            asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+            // the tile's coordinates and output bases first: their loads and bit scatters
+            // overlap the wait for the accumulator
             TcTile tt;
             const int *sb = nullptr;  // stacked: this tile's batch indices
             int nonb = 0;
@@ -566,18 +566,32 @@ __global__ void __launch_bounds__(kTcThreads, 1)
             const bool row_ok = m < M && vrow < p.nver;
             const long long mbase = row_ok ? scatter_bits(m, p.pos_m, p.lm) : 0;
             long long cbase = scatter_bits(bat, p.pos_bat, p.lbat) + mbase;
+            // stacked: this warp's columns cover the stack's batches j0 and (if BN / 2 > N)
+            // j0 + 1; their indices (-1: empty) and output bases
+            const int j0 = c_begin >> p.ln;
+            int be0 = -1, be1 = -1;
+            long long cb0 = 0, cb1 = 0;
+            if (stk) {
+                be0 = j0 < S ? sb[j0] : -1;
+                be1 = (j0 + 1 < S && ((j0 + 1) << p.ln) < c_end) ? sb[j0 + 1] : -1;
+                if (be0 >= 0) cb0 = scatter_bits(tc_compose_bat(p.ga, p.lbat, nonb, be0), p.pos_bat, p.lbat) + mbase;
+                if (be1 >= 0) cb1 = scatter_bits(tc_compose_bat(p.ga, p.lbat, nonb, be1), p.pos_bat, p.lbat) + mbase;
+            }
+            if (!mbar_wait(smem_u32(&acc_full[b]), (uint32_t)((it >> 1) & 1), abort_flag, kLimit)) break;
+            asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
             const uint32_t lane_addr = tmem + ((uint32_t)(32 * quarter) << 16) + (uint32_t)(b * 2 * BN);
             for (int c0 = c_begin; c0 < c_end; c0 += 16) {
                 float re[16], im[16];
                 // stacked: columns [j N, (j + 1) N) belong to the stack's batch j (N >= 32);
                 // an empty slot's columns were not computed (warp-uniform skip)
-                const int be = stk ? sb[c0 >> p.ln] : 0;
+                const bool first = (c0 >> p.ln) == j0;
+                const int be = stk ? (first ? be0 : be1) : 0;
                 if (be < 0) continue;
                 __syncwarp();
                 tmem_ld16x2(lane_addr + c0, lane_addr + BN + c0, re, im);
                 if (!row_ok) continue;
                 if (stk) {
-                    const long long cb = scatter_bits(tc_compose_bat(p.ga, p.lbat, nonb, be), p.pos_bat, p.lbat) + mbase;
+                    const long long cb = first ? cb0 : cb1;
                     const long long nb = c0 & (N - 1);
                     void *Cv = static_cast<char *>(p.C) + 8 * vrow * p.c_plane;
                     const long long hi = cb + scatter_bits(nb >> 4, p.pos_n + 4, p.ln - 4);

@@ -149,6 +149,20 @@ def test_annealed_plans(emu, seed):
     check(emu, circ, cg.default_open_qubits(3, 5, 6), o, -2, 1, nb=21, seed=seed + 40)
 
 
+def test_size_capped_plan_annealed_per_slice(emu):
+    """A plan sliced down to a tensor-size cap (2^13 elements) whose sliced tree is then
+    annealed per slice under the cap (the sampling job's planning path): at 3x5, 12 cycles
+    (circuit and order seed 3) the annealed tree differs from the unannealed one (9.63e7
+    instead of 9.94e7 FLOPs per slice, 3 sliced legs both ways); its compiled steps,
+    executed on the host, match the oracle on every slice subset."""
+    circ = cg.sycamore_grid(3, 5, 12, seed=3)
+    o = opts(log2_batches=4, n_sliced=0, precision=1)
+    o.max_log2_tensor = 13
+    o.order_seed = 3
+    o.anneal_iters = 20000
+    check(emu, circ, cg.default_open_qubits(3, 5, 6), o, -2, 1, nb=21, seed=5)
+
+
 def test_12q_no_open_qubits(emu):
     """Every qubit closed: one amplitude per batch (the verification workload's plans)."""
     circ = cg.sycamore_grid(3, 4, 8, seed=2)
