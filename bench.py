@@ -60,9 +60,11 @@ METRIC = "samples/s at fixed fidelity"
 # launch from one-pass ncu captures (profiles/), valid for the kernel source it was taken
 # with (sha256 prefix of the named csrc file): (kernel, shape bits) -> (bytes, file, sha)
 MEASURED_TRAFFIC = {
-    # the 40-qubit job's batch step: a quarter-size capture of the same kernel (every
-    # array and tile count a quarter of the launch's), scaled by 4
-    ("tc_cgemm<128,3> stacked", (14, 10, 5, 8)): (13.82e9, "tc.cuh", "3af33f207a404441"),
+    # the 40-qubit job's batch step, from one capture of the same kernel on a case whose
+    # arrays and tile counts are a quarter of (14,10,5,8) and half of (13,10,5,8) (the step
+    # of the annealed plan): 3.458 GB, scaled by 4 and by 2
+    ("tc_cgemm<128,3> stacked", (14, 10, 5, 8)): (13.83e9, "tc.cuh", "fd2822a0b959046e"),
+    ("tc_cgemm<128,3> stacked", (13, 10, 5, 8)): (6.917e9, "tc.cuh", "fd2822a0b959046e"),
 }
 FFMA_PEAK_NOTE = "152 SMs x 128 FP32 lanes x 2 FLOP x 2070 MHz"
 KERNEL_NAMES = {0: "cgemm_row", 1: "cgemm_small", 4: "cgemm_rowstage", 5: "cgemm_skinny"}
@@ -410,8 +412,9 @@ def roofline_of(trace, steps_traced, pk):
         src = os.path.join(ROOT, "paper_2112_15083_gb300", "csrc", rec[1])
         if hashlib.sha256(open(src, "rb").read()).hexdigest()[:16] == rec[2]:
             roof["traffic"] = rec[0]
-            roof["traffic_source"] = ("ncu dram__bytes_read.sum + dram__bytes_write.sum of a quarter-size case of "
-                                      "the same kernel, scaled by 4 (profiles/tc_cgemm_stacked_b4096_m1024_n32_k256.md)")
+            roof["traffic_source"] = ("ncu dram__bytes_read.sum + dram__bytes_write.sum of a smaller case of the "
+                                      "same kernel, scaled by the ratio of their arrays and tiles "
+                                      "(profiles/tc_cgemm_stacked_b4096_m1024_n32_k256.md)")
     return roof
 
 
