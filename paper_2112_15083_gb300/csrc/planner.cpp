@@ -572,10 +572,14 @@ StepEst step_estimate(const Network &net, const Node &a, const Node &b, const No
         // 128-256 x 32 outputs)
         if (nb > 0 && nm + nn <= 14) rate = net.tc_flop_rate * 0.15;
     }
+    // FFMA tiles over K <= 8 write each output after a few multiply-adds: they reach about a
+    // third of the copy bandwidth (measured 1.2-1.7 TB/s on (0,3,25,7) and (0,7,25,3))
+    const bool tc_step = net.tc_flop_rate > 0 && tn_tc_shape(hi, lo, nk);
+    const double bw_step = !tc_step && nk <= 3 && lo >= 4 && C.count() >= 30 ? bw / 3 : bw;
     StepEst e;
     e.flops = fl;
     e.bytes = by + (ga ? 2 * sa : 0) + (gb ? 2 * sb : 0);
-    e.time = std::max(fl / rate, by / bw) + launch + gt;
+    e.time = std::max(fl / rate, by / bw_step) + launch + gt;
     if (net.mem_limit_elems > 0 && by / 8.0 > net.mem_limit_elems) e.time += 1e6 * (by / 8.0 / net.mem_limit_elems);
     // a batch step runs once per group of the job, a batch-independent one once per job
     if (c.beta) e.time *= net.job_groups;

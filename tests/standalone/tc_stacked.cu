@@ -7,7 +7,7 @@
 // ways).  Prints the best of `reps` launches (stack list + tile kernel) and checks six
 // outputs against FP64 sums of the split planes; exits 1 on a mismatch or error.
 // usage: tc_stacked reps M_log2 variant(0 stacked 128, 1 stacked 64, 2 unstacked 64)
-//                   layout(0 n lowest, 1 m lowest) nbeta nq
+//                   layout(0 n lowest, 1 m lowest) nbeta nq nnb(default 2)
 #include <cstdio>
 #include <cstdlib>
 #include <cstring>
@@ -57,9 +57,9 @@ int main(int argc, char **argv) {
     const int lm = argc > 2 ? atoi(argv[2]) : 10;
     const int var = argc > 3 ? atoi(argv[3]) : 0;  // 0 stacked 128, 1 stacked 64, 2 plain 64
     const int nbeta = argc > 5 ? atoi(argv[5]) : 12, nq = argc > 6 ? atoi(argv[6]) : 10;
-    const int nnb = 2, ln = 5, lk = 8;
-    if (reps < 1 || lm < 7 || lm > 12 || var < 0 || var > 2 || nbeta < 1 || nbeta > 14 || nq < 0 || nq > 20) {
-        printf("usage: tc_stacked reps M_log2(7..12) variant(0..2) layout(0|1) nbeta(1..14) nq(0..20)\n");
+    const int nnb = argc > 7 ? atoi(argv[7]) : 2, ln = 5, lk = 8;
+    if (reps < 1 || lm < 7 || lm > 12 || var < 0 || var > 2 || nbeta < 1 || nbeta > 14 || nq < 0 || nq > 20 || nnb < 0 || nnb > 4) {
+        printf("usage: tc_stacked reps M_log2(7..12) variant(0..2) layout(0|1) nbeta(1..14) nq(0..20) nnb(0..4)\n");
         return 2;
     }
     const int lbat = nnb + nbeta, lba = nnb + nq, T = 1 << nbeta;

@@ -62,6 +62,12 @@ def test_tc_batch_step_with_in_place_operand(binaries, variant, layout):
         assert 1024 // (4 if variant == 0 else 2) <= stacks <= 1024
 
 
+def test_tc_batch_step_every_batch_bit_a_batch_index(binaries):
+    # no non-index batch bits (the 40-qubit job's (12,11,5,8) step): 1024 batches of 2048 rows
+    out = run(binaries["tc_stacked"], 2, 11, 0, 1, 10, 8, 0)
+    assert 1024 // 4 <= int(out.split("stacks ")[1].split(",")[0]) <= 1024
+
+
 @pytest.mark.parametrize("variant", [0, 1, 2])
 def test_long_k_kernel_warp_layouts(binaries, variant):
     run(binaries["long_k"], 2, 8, variant)
