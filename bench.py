@@ -3,7 +3,8 @@
 Default workload (grid5x8_m16): the 40-qubit 5x8 ABCD circuit, 16 cycles, 100k samples at
 fidelity f = 1/64 (Alg. 1), batches of 2^6 bitstrings, alpha = 2.  The plan slices legs
 until one slice's tensors fit 2^30 elements; its order search weights the batch steps by
-the job's batch groups.  The sampling job (tn_job_*) splits the retained slices into
+the job's batch groups, and the sliced tree is re-optimised and annealed per slice (2000
+moves) under that cap.  The sampling job (tn_job_*) splits the retained slices into
 chunks; one chunk is contracted for every batch group of the job (its batch-independent
 intermediates once, its batch part once per group of 4096 batches) and added to the
 job's FP64 amplitude sums; a final pass runs the accept / pick step on every batch.
