@@ -229,3 +229,41 @@ def test_job_bench_line_carries_the_contract(monkeypatch):
         assert k in line["e2e"], k
     # e2e: a second job, creation + chunks + final pass projected to all chunks
     assert len(plan.jobs) == 2 and plan.jobs[1].ran == [0, 1]
+
+
+def _step(nbat, nm, nn, nk, kernel, ms, flops, bytes_):
+    return {"nbat": nbat, "nm": nm, "nn": nn, "nk": nk, "nver": 1, "kernel": kernel, "ms": ms, "launches": 1,
+            "flops_per_launch": flops, "bytes_per_launch": bytes_, "gathers": 0, "in_place": 1}
+
+
+def test_roofline_bound_is_the_longer_of_bytes_and_products():
+    """A tensor-core step reports the HBM roofline when its compulsory bytes at the copy
+    bandwidth outlast its tensor-pipe products (three per algorithmic product) at the bf16
+    peak, the tensor roofline otherwise; frac is achieved / peak in the bound's unit."""
+    import bench
+    pk = {"hbm_gbs": 6789.0, "bf16_tflops": 1971.8}
+    # 6.71 GB and 8 x 2^36 = 5.5e11 FLOPs in 2.32 ms: 0.99 ms of bytes against 0.84 ms of
+    # tensor-pipe products
+    r = bench.roofline_of([_step(12, 11, 5, 8, 19128, 2.32, 5.5e11, 6.71e9)], 1, pk)
+    assert r["bound"] == "hbm" and r["unit"] == "GB/s"
+    assert r["achieved"] == pytest.approx(6.71e9 / 2.32e-3 / 1e9)
+    assert r["frac"] == pytest.approx(r["achieved"] / 6789.0)
+    assert r["tensor_pipe_tflops"] == pytest.approx(3 * 5.5e11 / 2.32e-3 / 1e12)
+    # 1.1e15 FLOPs and 70 GB in 2 s: products outlast bytes
+    r = bench.roofline_of([_step(1, 19, 10, 13, 9128, 2000.0, 1.1e15, 7.0e10)], 1, pk)
+    assert r["bound"] == "tensor" and r["unit"] == "TFLOP/s"
+    assert r["frac"] == pytest.approx(1.1e15 / 2.0 / 1e12 / 1971.8)
+
+
+def test_roofline_traffic_only_for_the_measured_kernel_source(monkeypatch):
+    """The measured DRAM traffic of a launch is reported only while the kernel source it
+    was taken with is unchanged (its hash prefix), else traffic stays null."""
+    import bench
+    pk = {"hbm_gbs": 6789.0, "bf16_tflops": 1971.8}
+    step = [_step(12, 11, 5, 8, 19128, 2.32, 5.5e11, 6.71e9)]
+    key = ("tc_cgemm<128,3> stacked", (12, 11, 5, 8))
+    assert key in bench.MEASURED_TRAFFIC
+    r = bench.roofline_of(step, 1, pk)
+    assert r["traffic"] == bench.MEASURED_TRAFFIC[key][0] and "traffic_source" in r
+    monkeypatch.setitem(bench.MEASURED_TRAFFIC, key, (bench.MEASURED_TRAFFIC[key][0], "tc.cuh", "0" * 16))
+    assert bench.roofline_of(step, 1, pk)["traffic"] is None
